@@ -1,0 +1,364 @@
+/*
+ * CPU oracle for the sensor-rendering hot path.  TEST INFRASTRUCTURE ONLY:
+ * only the tests, the package smoke check and the benchmark's CPU-baseline leg
+ * may load this file's library.  It shares no code with the CUDA path.
+ *
+ * What it computes is the plain definition of a rasterised observation
+ * (Sec. 3 "Rendering engine": one pass yields colour, depth and semantic
+ * outputs; Sec. 4 "Sensory input": pinhole colour + idealised depth sensor at
+ * the same pose).  For every pixel centre it takes, over ALL triangles and
+ * all pixels of each triangle's bounding box (no binning, no culling beyond
+ * the rules below), the covering fragment with the largest interpolated
+ * inverse depth, ties to the lower triangle index, and shades that fragment.
+ *
+ * The paper fixes none of the rasterisation rules (it uses an OpenGL
+ * pipeline); every rule below is a stated reading:
+ *   order    : each index triple is rotated cyclically so that its
+ *              lexicographically smallest rotation comes first.
+ *   camera   : unit quaternion (w,x,y,z) -> R (world-from-camera) in double,
+ *              M = [R^T | -R^T pos] rounded once to float; camera looks down
+ *              -Z, +Y up; eye depth d = -z_e (planar depth).
+ *   transform: x_e = fma(M00,x, fma(M01,y, fma(M02,z, M03))) (same for y, z).
+ *   reject   : all three d < near, or all three d > far.
+ *   near clip: Sutherland-Hodgman against d >= near; an edge's endpoints are
+ *              ordered by ascending vertex index; t = (near-d_a)/(d_b-d_a),
+ *              p = fma(t, p_b - p_a, p_a), d := near; fan from first vertex.
+ *   project  : q = 1/d, sx = fma(fx, x_e*q, cx), sy = fma(-fy, y_e*q, cy),
+ *              X = rint(256 sx), Y = rint(256 sy)  (8 sub-pixel bits).
+ *   cull     : A = (X1-X0)(Y2-Y0) - (Y1-Y0)(X2-X0) in int64, keep A < 0
+ *              (front faces are counter-clockwise in the world), then swap
+ *              vertices 1 and 2 so that A > 0.
+ *   coverage : sample (256x+128, 256y+128); edge k opposite vertex k;
+ *              inside iff E_k > 0, or E_k == 0 and edge k is top or left
+ *              (edge i->j is top iff dy == 0 and dx > 0, left iff dy < 0).
+ *   depth    : plane of q over the snapped vertices, relative to vertex 0,
+ *              fp32 op order below; fragment kept iff q > 0 and 1/q <= far.
+ *   key      : ((~bits(q)) << 32) | triangle index; per-pixel minimum.
+ *   shade    : perspective-correct weights E_k * q_k (fp64), bilinear
+ *              clamp-to-edge texture lookup at (u*Wt - 0.5, v*Ht - 0.5), or
+ *              vertex colours; channel = min(255, floor(c + 0.5)).
+ *   outputs  : RGB u8, depth 1/q (float), id = semantic[tri] or tri;
+ *              background RGB 0, depth 0, id 0xFFFFFFFF.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG 1
+#define OR_ERR_OOM 2
+#define OR_ERR_RANGE 3      /* a snapped coordinate left +-2^30 sub-pixels */
+
+static uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/* camera matrix from a pose (x, y, z, qw, qx, qy, qz) */
+int oracle_camera(const float *pose, float *M)
+{
+    double px = pose[0], py = pose[1], pz = pose[2];
+    double w = pose[3], x = pose[4], y = pose[5], z = pose[6];
+    double n2 = ((w * w + x * x) + y * y) + z * z;
+    double n = sqrt(n2);
+    if (!(fabs(n - 1.0) <= 1e-3)) return OR_ERR_ARG;
+    w /= n; x /= n; y /= n; z /= n;
+    double R[3][3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    R[0][1] = 2.0 * (x * y - w * z);
+    R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z);
+    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y);
+    R[2][1] = 2.0 * (y * z + w * x);
+    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+    for (int i = 0; i < 3; i++) {
+        for (int j = 0; j < 3; j++) M[i * 4 + j] = (float)R[j][i];
+        M[i * 4 + 3] = (float)(-((R[0][i] * px + R[1][i] * py) + R[2][i] * pz));
+    }
+    return OR_OK;
+}
+
+typedef struct {
+    float xe, ye, d;        /* eye space, d = -z_e */
+    uint32_t vid;           /* caller's vertex index (clip ordering) */
+    double attr[3];         /* u, v (textured) or r, g, b (vertex colour) */
+} overt;
+
+typedef struct {
+    /* scene */
+    const float *xyz; uint32_t nv;
+    const uint32_t *idx; uint32_t nt;
+    const float *uv; const uint8_t *vrgb;
+    const uint8_t *atlas; uint32_t aw, ah;
+    const uint32_t *sem;
+    /* views */
+    const float *poses; uint32_t n;
+    float fx, fy, cx, cy, znear, zfar;
+    uint32_t W, H;
+    uint8_t *rgb; float *depth; uint32_t *ids; uint32_t *cover;
+    /* work split */
+    uint32_t f0, f1;
+    int status;
+} ojob;
+
+static int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+static int64_t ceildiv(int64_t a, int64_t b) { return -floordiv(-a, b); }
+
+static double texel(const ojob *J, int64_t x, int64_t y, int c)
+{
+    if (x < 0) x = 0;
+    if (x > (int64_t)J->aw - 1) x = J->aw - 1;
+    if (y < 0) y = 0;
+    if (y > (int64_t)J->ah - 1) y = J->ah - 1;
+    return (double)J->atlas[((size_t)y * J->aw + (size_t)x) * 4 + c];
+}
+
+static uint8_t round_channel(double c)
+{
+    double r = floor(c + 0.5);
+    if (r < 0) r = 0;
+    if (r > 255) r = 255;
+    return (uint8_t)r;
+}
+
+/* shade one fragment in fp64: weights E_k * q_k (perspective-correct) */
+static void shade(const ojob *J, int mode, const overt *v[3], const float q[3], const int64_t E[3],
+                  uint8_t out[3])
+{
+    double w0 = (double)E[0] * (double)q[0];
+    double w1 = (double)E[1] * (double)q[1];
+    double w2 = (double)E[2] * (double)q[2];
+    double s = w0 + w1 + w2;
+    double l0 = w0 / s, l1 = w1 / s, l2 = w2 / s;
+    if (mode == 1) {
+        double u = l0 * v[0]->attr[0] + l1 * v[1]->attr[0] + l2 * v[2]->attr[0];
+        double vv = l0 * v[0]->attr[1] + l1 * v[1]->attr[1] + l2 * v[2]->attr[1];
+        double sx = u * J->aw - 0.5, sy = vv * J->ah - 0.5;
+        if (!(sx >= -1.0)) sx = -1.0;
+        if (sx > J->aw) sx = J->aw;
+        if (!(sy >= -1.0)) sy = -1.0;
+        if (sy > J->ah) sy = J->ah;
+        double x0 = floor(sx), y0 = floor(sy);
+        double ax = sx - x0, ay = sy - y0;
+        int64_t ix = (int64_t)x0, iy = (int64_t)y0;
+        for (int c = 0; c < 3; c++) {
+            double c00 = texel(J, ix, iy, c), c10 = texel(J, ix + 1, iy, c);
+            double c01 = texel(J, ix, iy + 1, c), c11 = texel(J, ix + 1, iy + 1, c);
+            double val = (1 - ax) * (1 - ay) * c00 + ax * (1 - ay) * c10 + (1 - ax) * ay * c01 + ax * ay * c11;
+            out[c] = round_channel(val);
+        }
+    } else if (mode == 2) {
+        for (int c = 0; c < 3; c++)
+            out[c] = round_channel(l0 * v[0]->attr[c] + l1 * v[1]->attr[c] + l2 * v[2]->attr[c]);
+    } else {
+        out[0] = out[1] = out[2] = 255;
+    }
+}
+
+static overt clip_point(const overt *p, const overt *r, float znear, int nattr)
+{
+    const overt *a = p, *b = r;
+    if (b->vid < a->vid) { a = r; b = p; }
+    float t = (znear - a->d) / (b->d - a->d);
+    overt o;
+    o.xe = fmaf(t, b->xe - a->xe, a->xe);
+    o.ye = fmaf(t, b->ye - a->ye, a->ye);
+    o.d = znear;
+    o.vid = 0xFFFFFFFFu;
+    for (int k = 0; k < nattr; k++) o.attr[k] = a->attr[k] + (double)t * (b->attr[k] - a->attr[k]);
+    for (int k = nattr; k < 3; k++) o.attr[k] = 0;
+    return o;
+}
+
+static int render_frame(ojob *J, uint32_t f, uint64_t *best)
+{
+    const uint32_t W = J->W, H = J->H;
+    const size_t npx = (size_t)W * H;
+    float M[12];
+    if (oracle_camera(J->poses + 7 * (size_t)f, M) != OR_OK) return OR_ERR_ARG;
+    const int mode = (J->uv && J->atlas) ? 1 : (J->vrgb ? 2 : 0);
+    const int nattr = mode == 1 ? 2 : (mode == 2 ? 3 : 0);
+    uint8_t *rgb = J->rgb + (size_t)f * npx * 3;
+    float *dep = J->depth + (size_t)f * npx;
+    uint32_t *ids = J->ids ? J->ids + (size_t)f * npx : NULL;
+    uint32_t *cov = J->cover ? J->cover + (size_t)f * npx : NULL;
+    for (size_t i = 0; i < npx; i++) best[i] = ~(uint64_t)0;
+    memset(rgb, 0, npx * 3);
+    for (size_t i = 0; i < npx; i++) dep[i] = 0.0f;
+    if (ids) for (size_t i = 0; i < npx; i++) ids[i] = 0xFFFFFFFFu;
+    if (cov) memset(cov, 0, npx * 4);
+
+    for (uint32_t t = 0; t < J->nt; t++) {
+        overt v[3];
+        /* canonical cyclic order: the lexicographically smallest rotation of
+           the index triple comes first (orientation is unchanged) */
+        uint32_t tri[3] = {J->idx[3 * (size_t)t], J->idx[3 * (size_t)t + 1], J->idx[3 * (size_t)t + 2]};
+        int r = 0;
+        for (int c = 1; c < 3; c++) {
+            for (int k = 0; k < 3; k++) {
+                uint32_t a = tri[(c + k) % 3], b = tri[(r + k) % 3];
+                if (a != b) { if (a < b) r = c; break; }
+            }
+        }
+        for (int k = 0; k < 3; k++) {
+            uint32_t vi = tri[(r + k) % 3];
+            float x = J->xyz[3 * (size_t)vi], y = J->xyz[3 * (size_t)vi + 1], z = J->xyz[3 * (size_t)vi + 2];
+            v[k].xe = fmaf(M[0], x, fmaf(M[1], y, fmaf(M[2], z, M[3])));
+            v[k].ye = fmaf(M[4], x, fmaf(M[5], y, fmaf(M[6], z, M[7])));
+            float ze = fmaf(M[8], x, fmaf(M[9], y, fmaf(M[10], z, M[11])));
+            v[k].d = -ze;
+            v[k].vid = vi;
+            for (int c = 0; c < 3; c++) v[k].attr[c] = 0;
+            if (mode == 1) { v[k].attr[0] = J->uv[2 * (size_t)vi]; v[k].attr[1] = J->uv[2 * (size_t)vi + 1]; }
+            if (mode == 2) for (int c = 0; c < 3; c++) v[k].attr[c] = J->vrgb[3 * (size_t)vi + c];
+        }
+        const float zn = J->znear, zf = J->zfar;
+        if (v[0].d < zn && v[1].d < zn && v[2].d < zn) continue;
+        if (v[0].d > zf && v[1].d > zf && v[2].d > zf) continue;
+        overt poly[4];
+        int np = 0;
+        if (v[0].d >= zn && v[1].d >= zn && v[2].d >= zn) {
+            poly[0] = v[0]; poly[1] = v[1]; poly[2] = v[2]; np = 3;
+        } else {
+            for (int k = 0; k < 3; k++) {
+                const overt *a = &v[k], *b = &v[(k + 1) % 3];
+                int ain = a->d >= zn, bin = b->d >= zn;
+                if (ain) poly[np++] = *a;
+                if (ain != bin) poly[np++] = clip_point(a, b, zn, nattr);
+            }
+        }
+        /* project and snap */
+        int32_t X[4], Y[4];
+        float q[4];
+        for (int k = 0; k < np; k++) {
+            q[k] = 1.0f / poly[k].d;
+            float sx = fmaf(J->fx, poly[k].xe * q[k], J->cx);
+            float sy = fmaf(-J->fy, poly[k].ye * q[k], J->cy);
+            float rx = rintf(sx * 256.0f), ry = rintf(sy * 256.0f);
+            if (!(fabsf(rx) < 1073741824.0f) || !(fabsf(ry) < 1073741824.0f)) return OR_ERR_RANGE;
+            X[k] = (int32_t)rx;
+            Y[k] = (int32_t)ry;
+        }
+        for (int fan = 0; fan + 2 < np; fan++) {
+            int i0 = 0, i1 = fan + 1, i2 = fan + 2;
+            int64_t A = (int64_t)(X[i1] - X[i0]) * (Y[i2] - Y[i0]) - (int64_t)(Y[i1] - Y[i0]) * (X[i2] - X[i0]);
+            if (A >= 0) continue;
+            int tmp = i1; i1 = i2; i2 = tmp;      /* orient to positive area */
+            A = -A;
+            const int32_t X0 = X[i0], Y0 = Y[i0], X1 = X[i1], Y1 = Y[i1], X2 = X[i2], Y2 = Y[i2];
+            const float q0 = q[i0], q1 = q[i1], q2 = q[i2];
+            /* plane of q, relative to vertex 0 */
+            const float fA = (float)A;
+            const float dq1 = q1 - q0, dq2 = q2 - q0;
+            const float pa = fmaf(dq1, (float)(Y2 - Y0), -(dq2 * (float)(Y1 - Y0))) / fA;
+            const float pb = fmaf(dq2, (float)(X1 - X0), -(dq1 * (float)(X2 - X0))) / fA;
+            /* top-left flags per edge k (opposite vertex k) */
+            const int32_t ex[3][2] = {{X1, X2}, {X2, X0}, {X0, X1}};
+            const int32_t ey[3][2] = {{Y1, Y2}, {Y2, Y0}, {Y0, Y1}};
+            int tl[3];
+            for (int k = 0; k < 3; k++) {
+                int64_t dx = (int64_t)ex[k][1] - ex[k][0], dy = (int64_t)ey[k][1] - ey[k][0];
+                tl[k] = (dy < 0) || (dy == 0 && dx > 0);
+            }
+            int32_t mnx = X0, mxx = X0, mny = Y0, mxy = Y0;
+            if (X1 < mnx) mnx = X1;
+            if (X2 < mnx) mnx = X2;
+            if (X1 > mxx) mxx = X1;
+            if (X2 > mxx) mxx = X2;
+            if (Y1 < mny) mny = Y1;
+            if (Y2 < mny) mny = Y2;
+            if (Y1 > mxy) mxy = Y1;
+            if (Y2 > mxy) mxy = Y2;
+            int64_t x0 = ceildiv((int64_t)mnx - 128, 256), x1 = floordiv((int64_t)mxx - 128, 256);
+            int64_t y0 = ceildiv((int64_t)mny - 128, 256), y1 = floordiv((int64_t)mxy - 128, 256);
+            if (x0 < 0) x0 = 0;
+            if (y0 < 0) y0 = 0;
+            if (x1 > (int64_t)W - 1) x1 = (int64_t)W - 1;
+            if (y1 > (int64_t)H - 1) y1 = (int64_t)H - 1;
+            const overt *sv[3] = {&poly[i0], &poly[i1], &poly[i2]};
+            const float sq[3] = {q0, q1, q2};
+            for (int64_t py = y0; py <= y1; py++) {
+                for (int64_t px = x0; px <= x1; px++) {
+                    const int64_t Px = 256 * px + 128, Py = 256 * py + 128;
+                    int64_t E[3];
+                    int in = 1;
+                    for (int k = 0; k < 3; k++) {
+                        E[k] = ((int64_t)ex[k][1] - ex[k][0]) * (Py - ey[k][0]) -
+                               ((int64_t)ey[k][1] - ey[k][0]) * (Px - ex[k][0]);
+                        if (!(E[k] > 0 || (E[k] == 0 && tl[k]))) in = 0;
+                    }
+                    if (!in) continue;
+                    const size_t pix = (size_t)py * W + (size_t)px;
+                    if (cov) cov[pix]++;
+                    const float qq = fmaf(pa, (float)(Px - X0), fmaf(pb, (float)(Py - Y0), q0));
+                    if (!(qq > 0.0f)) continue;
+                    const float dd = 1.0f / qq;
+                    if (dd > zf) continue;
+                    const uint64_t key = ((uint64_t)(~f2u(qq)) << 32) | t;
+                    if (key < best[pix]) {
+                        best[pix] = key;
+                        shade(J, mode, sv, sq, E, rgb + 3 * pix);
+                        dep[pix] = dd;
+                        if (ids) ids[pix] = J->sem ? J->sem[t] : t;
+                    }
+                }
+            }
+        }
+    }
+    return OR_OK;
+}
+
+static void *worker(void *arg)
+{
+    ojob *J = (ojob *)arg;
+    uint64_t *best = (uint64_t *)malloc((size_t)J->W * J->H * sizeof(uint64_t));
+    if (!best) { J->status = OR_ERR_OOM; return NULL; }
+    J->status = OR_OK;
+    for (uint32_t f = J->f0; f < J->f1 && J->status == OR_OK; f++) J->status = render_frame(J, f, best);
+    free(best);
+    return NULL;
+}
+
+int oracle_render(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
+                  const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
+                  const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
+                  uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
+                  int nthreads)
+{
+    if (!xyz || !idx || !poses || !intr || !rgb || !depth || n == 0 || W == 0 || H == 0) return OR_ERR_ARG;
+    for (size_t i = 0; i < 3 * (size_t)nt; i++)
+        if (idx[i] >= nv) return OR_ERR_ARG;
+    if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nthreads < 1) nthreads = 1;
+    if ((uint32_t)nthreads > n) nthreads = (int)n;
+    ojob *jobs = (ojob *)calloc((size_t)nthreads, sizeof(ojob));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return OR_ERR_OOM; }
+    for (int i = 0; i < nthreads; i++) {
+        ojob *J = &jobs[i];
+        J->xyz = xyz; J->nv = nv; J->idx = idx; J->nt = nt;
+        J->uv = uv; J->vrgb = vrgb; J->atlas = atlas; J->aw = aw; J->ah = ah; J->sem = sem;
+        J->poses = poses; J->n = n;
+        J->fx = intr[0]; J->fy = intr[1]; J->cx = intr[2]; J->cy = intr[3];
+        J->znear = intr[4]; J->zfar = intr[5];
+        J->W = W; J->H = H; J->rgb = rgb; J->depth = depth; J->ids = ids; J->cover = cover;
+        J->f0 = (uint32_t)((uint64_t)n * i / nthreads);
+        J->f1 = (uint32_t)((uint64_t)n * (i + 1) / nthreads);
+    }
+    int st = OR_OK;
+    if (nthreads == 1) {
+        worker(&jobs[0]);
+        st = jobs[0].status;
+    } else {
+        for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, worker, &jobs[i]);
+        for (int i = 0; i < nthreads; i++) {
+            pthread_join(th[i], NULL);
+            if (jobs[i].status != OR_OK && st == OR_OK) st = jobs[i].status;
+        }
+    }
+    free(jobs);
+    free(th);
+    return st;
+}
