@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: RGB-D frames/s of the sensor-rendering hot path on one B300.
+
+Default workload (N=1): the 1M-triangle synthetic house with a 4096^2 RGBA8
+atlas, 64 agents at random navigable poses, 256x256 RGB + depth — one step
+renders all 64 views in one batched launch. `--mode plain` renders the same
+views one agent per launch. `--impl reference` times the CPU oracle (the
+reference arm: there is no runnable code of the paper).
+
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the
+path has no exchange step); value is the sum of all ranks' frames over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "RGB-D frames/sec (batched vs plain)"
+UNIT = "frames/s"
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6400.0
+
+KERNEL_SOURCES = ["paper_1904_01201_b300/csrc/render.cu", "paper_1904_01201_b300/csrc/hsr_internal.h",
+                  "paper_1904_01201_b300/csrc/kernels/transform.cuh", "paper_1904_01201_b300/csrc/kernels/setup.cuh",
+                  "paper_1904_01201_b300/csrc/kernels/bin.cuh", "paper_1904_01201_b300/csrc/kernels/raster.cuh",
+                  "paper_1904_01201_b300/csrc/kernels/shade.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------- workloads
+def make_workload(name: str, seed: int = 0):
+    from paper_1904_01201_b300 import workloads as wl
+    if name == "house":
+        sc = wl.make_house(seed, 1_000_000, 4096)
+        poses = wl.random_poses(sc, 64, seed)
+        return dict(name="house-1M-atlas4096-64x256", scenes=[sc], soa=np.zeros(64, np.uint32), poses=poses,
+                    W=256, H=256, ids=False, intr=wl.pinhole_90(256, 256))
+    if name == "room":
+        sc = wl.make_room(seed)
+        poses = wl.random_poses(sc, 16, seed)
+        return dict(name="room-10k-vcolor-16x128", scenes=[sc], soa=np.zeros(16, np.uint32), poses=poses,
+                    W=128, H=128, ids=False, intr=wl.pinhole_90(128, 128))
+    if name == "batching":
+        scenes = wl.batching_scenes(seed)
+        split = wl.dirichlet_split(1024, len(scenes), 0.5, seed)
+        soa = np.repeat(np.arange(len(scenes)), split).astype(np.uint32)
+        poses = np.concatenate([wl.random_poses(s, int(k), seed + i) for i, (s, k) in enumerate(zip(scenes, split))])
+        return dict(name="batching-8scenes-1024x128", scenes=scenes, soa=soa, poses=poses, W=128, H=128, ids=False,
+                    intr=wl.pinhole_90(128, 128))
+    if name == "large":
+        sc = wl.make_house(seed + 5, 2_000_000, 8192, semantic=True)
+        poses = wl.random_poses(sc, 256, seed)
+        return dict(name="large-2M-atlas8192-256x512-ids", scenes=[sc], soa=np.zeros(256, np.uint32), poses=poses,
+                    W=512, H=512, ids=True, intr=wl.pinhole_90(512, 512))
+    raise ValueError(name)
+
+
+def algorithmic_bytes_per_view(scene, W, H, ids) -> float:
+    """Per-view algorithmic bytes: the whole mesh is read once per view
+    (indices 12 B/triangle; xyz + uv 20 B/vertex, or xyz + rgb8 15 B), the
+    framebuffer written once (3 B RGB + 4 B depth (+4 B id) per pixel), and
+    one bilinear quad of RGBA8 texels (16 B) per pixel when textured."""
+    T, V = scene.n_tris, scene.n_verts
+    textured = scene.uv is not None and scene.atlas is not None
+    b = 12.0 * T + (20.0 if textured else 15.0) * V + 7.0 * W * H
+    if ids:
+        b += 4.0 * W * H
+    if textured:
+        b += 16.0 * W * H
+    return b
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(workload_name: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"render_kernel_{workload_name}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(wk, n_frames: int, seconds_cap: float = 30.0):
+    """The oracle, as it stands, on a bounded sample of the workload's views."""
+    import oracle
+    cores = os.cpu_count() or 1
+    poses, soa = wk["poses"], wk["soa"]
+    done, t0 = 0, time.perf_counter()
+    i = 0
+    while done < n_frames and time.perf_counter() - t0 < seconds_cap:
+        s = int(soa[i % len(soa)])
+        sel = [j for j in range(i, min(i + cores, len(soa))) if soa[j] == s] or [i % len(soa)]
+        oracle.render(wk["scenes"][s], poses[sel], wk["intr"], wk["W"], wk["H"], nthreads=cores, ids=wk["ids"])
+        done += len(sel)
+        i = (sel[-1] + 1) % len(soa)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of the workload's views rendered by the CPU oracle on {cores} threads in {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args, wk):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    cores = os.cpu_count() or 1
+    n = min(len(wk["soa"]), max(1, cores))
+    for _ in range(args.warmup):
+        oracle.render(wk["scenes"][int(wk["soa"][0])], wk["poses"][:1], wk["intr"], wk["W"], wk["H"], nthreads=1,
+                      ids=wk["ids"])
+    t0 = time.perf_counter()
+    frames = 0
+    for k in range(args.steps):
+        s = int(wk["soa"][0])
+        sel = np.nonzero(wk["soa"] == s)[0][:n]
+        oracle.render(wk["scenes"][s], wk["poses"][sel], wk["intr"], wk["W"], wk["H"], nthreads=cores, ids=wk["ids"])
+        frames += len(sel)
+    dt = time.perf_counter() - t0
+    v = frames / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/int", "data": "synthetic",
+            "config": {"workload": wk["name"], "sample_views_per_step": int(n), "mode": "cpu-oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} views per step of the workload on {cores} threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_gpu(args, wk):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+    from paper_1904_01201_b300 import hsr
+
+    handles = [hsr.SceneHandle(s) for s in wk["scenes"]]
+    n, W, H = len(wk["soa"]), wk["W"], wk["H"]
+    out = hsr.alloc_outputs(n, W, H, ids=wk["ids"], device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    poses, soa = wk["poses"], wk["soa"]
+    multi = len(handles) > 1
+
+    def step_batched():
+        if multi:
+            st = hsr.hsr_render_batch([h.handle for h in handles], soa, poses, wk["intr"], W, H, out["rgb"],
+                                      out["depth"], out.get("ids"), stream)
+        else:
+            st = hsr.hsr_render(handles[0].handle, poses, wk["intr"], W, H, out["rgb"], out["depth"],
+                                out.get("ids"), stream)
+        if st != 0:
+            raise hsr.HsrError(st, "render")
+        return 1
+
+    def step_plain():
+        for i in range(n):
+            h = handles[int(soa[i])]
+            st = hsr.hsr_render(h.handle, poses[i:i + 1], wk["intr"], W, H, out["rgb"][i:i + 1], out["depth"][i:i + 1],
+                                None if "ids" not in out else out["ids"][i:i + 1], stream)
+            if st != 0:
+                raise hsr.HsrError(st, "render")
+        return n
+
+    step = step_plain if args.mode == "plain" else step_batched
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(stepfn, steps, sampler=None):
+        for _ in range(args.warmup):
+            stepfn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches = 0
+        clk = ClockSampler(sampler) if sampler is not False else None
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            launches += stepfn()
+            e.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop() if clk else None
+        barrier()
+        ms = sum(s.elapsed_time(e) for s, e in evs)
+        return ms, launches, clocks
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+
+    ms, launches, clocks = timed(step, args.steps, uuid)
+    local_ms = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    frames = n * args.steps * world
+    value = frames / (ms / 1e3)
+
+    # plain one-agent-per-launch path on the same views, for comparison
+    plain = None
+    if args.mode == "batched" and not args.no_plain:
+        pms, _, _ = timed(step_plain, max(3, args.steps // 10), False)
+        psteps = max(3, args.steps // 10)
+        plain = {"value": n * psteps / (pms / 1e3), "ms_per_step": pms / psteps,
+                 "launches_per_step": n}
+
+    # end to end through the C-ABI with host buffers: host poses in, H2D of
+    # the view descriptors inside the call, D2H of RGB + depth to pinned host memory
+    host_rgb = torch.empty(out["rgb"].shape, dtype=torch.uint8, pin_memory=True)
+    host_depth = torch.empty(out["depth"].shape, dtype=torch.float32, pin_memory=True)
+    for _ in range(args.warmup):
+        step()
+        host_rgb.copy_(out["rgb"], non_blocking=True)
+        host_depth.copy_(out["depth"], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step()
+        host_rgb.copy_(out["rgb"], non_blocking=True)
+        host_depth.copy_(out["depth"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(poses.nbytes),
+           "d2h_bytes_per_step": int(out["rgb"].numel() + 4 * out["depth"].numel())}
+
+    if rank != 0:
+        return None
+    peak, peak_kind = load_peaks()
+    bview = sum(algorithmic_bytes_per_view(wk["scenes"][int(s)], W, H, wk["ids"]) for s in soa) / n
+    kernel_ms_per_launch = local_ms / launches
+    achieved = (bview * n / launches) / (kernel_ms_per_launch / 1e3) / 1e9
+    traffic = recorded_traffic(wk["name"]) if args.mode == "batched" else None
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/int", "data": "synthetic",
+        "config": {"workload": wk["name"], "scenes": len(handles), "tris": [int(s.n_tris) for s in wk["scenes"]],
+                   "agents": n, "width": W, "height": H, "outputs": "rgb+depth" + ("+ids" if wk["ids"] else ""),
+                   "mode": args.mode, "l2": "flushed before every step (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_view": bview, "kernel": "hsr::render_kernel",
+                     "kernel_ms_per_launch": kernel_ms_per_launch},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "kernel_sha": kernel_source_hash(),
+    }
+    if plain:
+        res["plain"] = plain
+        res["batched_over_plain"] = value / plain["value"]
+    if world == 1 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(wk, args.cpu_frames)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hsr", choices=["hsr", "reference"])
+    ap.add_argument("--workload", default="house", choices=["house", "room", "batching", "large"])
+    ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-frames", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wk = make_workload(args.workload, args.seed)
+    res = run_reference(args, wk) if args.impl == "reference" else run_gpu(args, wk)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

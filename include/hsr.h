@@ -1,0 +1,141 @@
+/*
+ * hsr — batched triangle-mesh sensor rendering (colour, depth, semantic ids).
+ *
+ * C-ABI of the rendering hot path described in "Habitat: A Platform for
+ * Embodied AI Research" (arXiv:1904.01201):
+ *   - a scene is loaded once and its resources are shared by every agent that
+ *     renders it (Appendix A, "Memory-efficient management of 3D environment
+ *     resources ... cached and reused");
+ *   - agents carry sensors at a pose and render observations of the scene
+ *     (Appendix A, key abstractions "Agent", "Sensor"; Sec. 4 "Sensory input":
+ *     colour camera and idealised depth sensor at the same pose, 90 degree FOV);
+ *   - colour, depth and semantic outputs come from one pass (Sec. 3 "Rendering
+ *     engine", multi-attachment "uber-shader").
+ *
+ * Conventions used by every call:
+ *   - world is Y-up, metres; a pose is the camera position and a unit
+ *     quaternion (w, x, y, z) rotating camera axes into world axes; the camera
+ *     looks down its -Z axis with +Y up; depth is planar (d = -z_eye).
+ *   - front faces are counter-clockwise seen from their visible side; back
+ *     faces are culled.
+ *   - outputs: RGB uint8 [n][H][W][3], depth float32 [n][H][W] (0 where
+ *     nothing is hit), ids uint32 [n][H][W] (semantic[tri] when the scene has
+ *     a semantic table, else the triangle index; 0xFFFFFFFF where nothing is
+ *     hit). Row 0 is the top of the image.
+ *   - render calls are asynchronous on the caller's CUDA stream (a
+ *     cudaStream_t passed as void*, NULL = legacy default stream). Host input
+ *     arrays (poses) may be reused as soon as the call returns. Output buffers
+ *     are caller-owned device memory and must stay valid until the stream
+ *     reaches the render.
+ *   - every call returns an hsr_status; an error affects only that call.
+ *     Calls are thread-safe for distinct scenes; a scene may be rendered from
+ *     several threads and streams at once, but must not be freed while a
+ *     render that uses it is in flight.
+ */
+#ifndef HSR_H
+#define HSR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HSR_API __attribute__((visibility("default")))
+#else
+#define HSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HSR_OK = 0,
+    HSR_ERR_INVALID_ARG = 1,  /* null pointer, zero count, index >= n_verts,
+                                 non-finite input, non-unit quaternion
+                                 (| |q| - 1 | > 1e-3), width/height outside
+                                 1..4096, bad intrinsics, or a pose/scene whose
+                                 projection could leave +-2^30 sub-pixels      */
+    HSR_ERR_OOM = 2,          /* device or host allocation failed             */
+    HSR_ERR_CUDA = 3,         /* a CUDA runtime call failed                    */
+    HSR_ERR_TIMEOUT = 4,      /* a bounded device wait expired                 */
+    HSR_ERR_OVERFLOW = 5,     /* a fixed-capacity buffer would overflow        */
+    HSR_ERR_NO_DEVICE = 6     /* no CUDA device is visible                     */
+} hsr_status;
+
+typedef struct hsr_scene hsr_scene;          /* opaque, library-owned */
+
+typedef struct {
+    float pos[3];      /* camera position in world metres                  */
+    float quat[4];     /* w, x, y, z: world-from-camera rotation            */
+} hsr_pose;
+
+typedef struct {
+    float fx, fy;      /* focal lengths in pixels (90 deg HFOV: fx = W/2)   */
+    float cx, cy;      /* principal point in pixels (image centre: W/2,H/2) */
+    float znear;       /* near clip distance, metres, > 0                   */
+    float zfar;        /* fragments with depth > zfar are discarded         */
+} hsr_intrinsics;
+
+typedef struct {
+    uint32_t n_tris, n_verts, n_meshlets, n_groups;
+    uint64_t device_bytes;     /* device memory held by the scene           */
+    float aabb_min[3], aabb_max[3];
+} hsr_scene_info;
+
+/*
+ * Load a static triangle mesh into device memory (Appendix A: resources are
+ * loaded once and shared by all agents rendering the scene).
+ *   xyz          host, [n_verts][3] float32 world positions (finite, |v| <= 2^20)
+ *   idx          host, [n_tris][3] uint32 vertex indices (< n_verts)
+ *   uv           host, [n_verts][2] float32 texture coordinates, or NULL
+ *   vert_rgb     host, [n_verts][3] uint8 vertex colours, or NULL
+ *   atlas_rgba8  host, [atlas_h][atlas_w][4] uint8 texture (row 0 is v = 0), or NULL
+ *   tri_semantic host, [n_tris] uint32 semantic ids (!= 0xFFFFFFFF), or NULL
+ * Colour source: atlas+uv if both are given, else vertex colours, else white.
+ * All inputs are copied; the caller may free them on return. On success *out
+ * receives a scene handle owned by the library until hsr_scene_free.
+ * The current CUDA device at load time owns the scene; render on that device.
+ */
+HSR_API int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint32_t n_tris,
+                   const float *uv, const uint8_t *vert_rgb, const uint8_t *atlas_rgba8,
+                   uint32_t atlas_w, uint32_t atlas_h, const uint32_t *tri_semantic,
+                   hsr_scene **out);
+
+/* Release a scene (synchronises the device first). NULL is accepted. */
+HSR_API int hsr_scene_free(hsr_scene *scene);
+
+/* Sizes and device footprint of a loaded scene. */
+HSR_API int hsr_scene_get_info(const hsr_scene *scene, hsr_scene_info *info);
+
+/*
+ * Render n agents of one scene, one observation each (Sec. 4 "Sensory input":
+ * colour + depth at the same pose and intrinsics; Sec. 3: one pass for all
+ * outputs). poses: host [n]. intr: host, shared by all n views.
+ * rgb: device [n][height][width][3]; depth: device [n][height][width];
+ * ids: device [n][height][width] or NULL.
+ */
+HSR_API int hsr_render(const hsr_scene *scene, const hsr_pose *poses, uint32_t n,
+               const hsr_intrinsics *intr, uint32_t width, uint32_t height,
+               uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
+
+/*
+ * Render n agents spread over several resident scenes in one launch (the
+ * batched replacement of the paper's multi-process GPU sharing, Table 1 and
+ * Table 2 "processes"). scenes: host [n_scenes]; scene_of_agent: host [n],
+ * each < n_scenes; outputs as for hsr_render, agent i at frame i.
+ */
+HSR_API int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes,
+                     const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
+                     const hsr_intrinsics *intr, uint32_t width, uint32_t height,
+                     uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
+
+/* Static description of a status code. */
+HSR_API const char *hsr_status_string(int status);
+
+/* Library version, "major.minor.patch". */
+HSR_API const char *hsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSR_H */

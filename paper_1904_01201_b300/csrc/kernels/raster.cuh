@@ -1,0 +1,97 @@
+// K4 — fixed-point edge-function rasteriser with a per-region z-buffer in
+// shared memory.
+//
+// Coverage (reading; the paper's OpenGL rasteriser is not specified): sample
+// at pixel centres (256x+128, 256y+128) in 24.8 fixed point; E_k for the edge
+// opposite vertex k is evaluated exactly in integers; a sample is inside when
+// every E_k > 0, or E_k == 0 on a top or left edge. The depth test keeps, per
+// pixel, the minimum 64-bit key (~bits(q) << 32 | triangle index): largest
+// inverse depth q first, lower triangle index on ties. Because the key is a
+// total order the result does not depend on the order fragments arrive in.
+//
+// Two paths:
+//  * small triangles (<= small_px candidate pixels and a bounding box under
+//    2^15 sub-pixels per axis, so every edge value fits in int32): one thread
+//    walks its own triangle's pixels;
+//  * other triangles are queued per warp in shared memory and rasterised by
+//    the whole warp, lanes spread over an 8x4 pixel footprint, int64 edges.
+// Both merge into the z-buffer with a 64-bit shared-memory atomicMin, skipped
+// when the stored key is already smaller.
+#pragma once
+#include "setup.cuh"
+
+namespace hsr {
+
+// A queued triangle for the warp-cooperative path (48 bytes).
+struct alignas(16) BigTri {
+    int X0, Y0, X1, Y1, X2, Y2;
+    float pa, pb, q0;
+    uint32_t id;
+    short x0, y0, x1, y1;      // candidate pixel range, already clipped to the region
+};
+
+__device__ __forceinline__ unsigned long long depth_key(float q, uint32_t id)
+{
+    return ((unsigned long long)(~__float_as_uint(q)) << 32) | id;
+}
+
+__device__ __forceinline__ void zmin(unsigned long long *z, unsigned long long key)
+{
+    if (key < *z) atomicMin(z, key);
+}
+
+// One thread, one small triangle. Exactness: |X_j - X_i| and |P - X_i| are
+// below 2^15 inside the bounding box, so every product is below 2^30 and every
+// edge value below 2^31.
+__device__ __forceinline__ void raster_small(const Tri2D &t, float pa, float pb, uint32_t id, int x0,
+                                             int x1, int y0, int y1, float q_far, unsigned long long *zbuf,
+                                             int rx0, int ry0, int RW)
+{
+    const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
+    const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
+    const int b2 = edge_bias(t.X0, t.Y0, t.X1, t.Y1);
+    const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
+    const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
+    const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
+    for (int py = y0; py <= y1; ++py) {
+        const int Py = 256 * py + 128;
+        for (int px = x0; px <= x1; ++px) {
+            const int Px = 256 * px + 128;
+            const int e0 = dx0 * (Py - t.Y1) - dy0 * (Px - t.X1);
+            const int e1 = dx1 * (Py - t.Y2) - dy1 * (Px - t.X2);
+            const int e2 = dx2 * (Py - t.Y0) - dy2 * (Px - t.X0);
+            if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
+            const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
+            if (!(q >= q_far)) continue;
+            zmin(zbuf + (py - ry0) * RW + (px - rx0), depth_key(q, id));
+        }
+    }
+}
+
+// The whole warp, one queued triangle.
+__device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float q_far,
+                                                unsigned long long *zbuf, int rx0, int ry0, int RW)
+{
+    const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
+    const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
+    const int b2 = edge_bias(t.X0, t.Y0, t.X1, t.Y1);
+    const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
+    const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
+    const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
+    const int lx = lane & 7, ly = lane >> 3;
+    for (int py = t.y0 + ly; py <= t.y1; py += 4) {
+        const int Py = 256 * py + 128;
+        for (int px = t.x0 + lx; px <= t.x1; px += 8) {
+            const int Px = 256 * px + 128;
+            const long long e0 = (long long)dx0 * (Py - t.Y1) - (long long)dy0 * (Px - t.X1);
+            const long long e1 = (long long)dx1 * (Py - t.Y2) - (long long)dy1 * (Px - t.X2);
+            const long long e2 = (long long)dx2 * (Py - t.Y0) - (long long)dy2 * (Px - t.X0);
+            if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
+            const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0);
+            if (!(q >= q_far)) continue;
+            zmin(zbuf + (py - ry0) * RW + (px - rx0), depth_key(q, t.id));
+        }
+    }
+}
+
+}  // namespace hsr

@@ -1,0 +1,121 @@
+// K2 — triangle setup: trivial reject, near-plane clip, back-face / degenerate
+// cull, orientation, depth plane, and the candidate pixel range.
+//
+// Rules (readings; the paper renders through OpenGL and states none):
+//  * reject when all three d < near or all three d > far;
+//  * Sutherland-Hodgman clip against d >= near; an edge's endpoints are taken
+//    in ascending caller vertex index so shared edges clip to identical points;
+//    t = (near - d_a)/(d_b - d_a), p = fma(t, p_b - p_a, p_a), d := near;
+//    fan triangulation from the first emitted vertex;
+//  * A = (X1-X0)(Y2-Y0) - (Y1-Y0)(X2-X0) in int64; keep A < 0 (front faces are
+//    counter-clockwise in the world; screen y points down), then swap 1 and 2;
+//  * depth plane of q = 1/d relative to vertex 0 (fixed fp32 op order);
+//  * candidate pixels: centres (256x+128, 256y+128) inside the bounding box.
+#pragma once
+#include "transform.cuh"
+
+namespace hsr {
+
+// Vertex entering the near clip. NA attributes travel with it (0 in raster,
+// 2 (u,v) or 3 (r,g,b) when shading).
+template <int NA>
+struct CVert {
+    float xe, ye, d;
+    uint32_t gid;
+    float a[NA > 0 ? NA : 1];
+};
+
+template <int NA>
+__device__ __forceinline__ CVert<NA> clip_edge(const CVert<NA> &p, const CVert<NA> &r, float znear)
+{
+    const bool swap = r.gid < p.gid;
+    const CVert<NA> &a = swap ? r : p;
+    const CVert<NA> &b = swap ? p : r;
+    const float t = __fdiv_rn(__fsub_rn(znear, a.d), __fsub_rn(b.d, a.d));
+    CVert<NA> o;
+    o.xe = __fmaf_rn(t, __fsub_rn(b.xe, a.xe), a.xe);
+    o.ye = __fmaf_rn(t, __fsub_rn(b.ye, a.ye), a.ye);
+    o.d = znear;
+    o.gid = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < NA; k++) o.a[k] = __fmaf_rn(t, __fsub_rn(b.a[k], a.a[k]), a.a[k]);
+    return o;
+}
+
+// Clip a (canonically ordered) triangle with at least one vertex in front of
+// the near plane; returns the polygon size (3 or 4).
+template <int NA>
+__device__ __forceinline__ int clip_near(const CVert<NA> (&v)[3], float znear, CVert<NA> (&out)[4])
+{
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const CVert<NA> &a = v[k];
+        const CVert<NA> &b = v[k == 2 ? 0 : k + 1];
+        const bool ain = a.d >= znear, bin = b.d >= znear;
+        if (ain) out[n++] = a;
+        if (ain != bin) out[n++] = clip_edge<NA>(a, b, znear);
+    }
+    return n;
+}
+
+// A front-facing triangle in oriented (positive-area) order.
+struct Tri2D {
+    int X0, Y0, X1, Y1, X2, Y2;
+    float q0, q1, q2;
+    long long A;           // oriented doubled area, > 0
+};
+
+// Back-face / degenerate cull and orientation. Returns false when culled.
+// Vertex order in: as produced by the clip / fan; out: vertices 1 and 2 swapped.
+__device__ __forceinline__ bool orient_cull(int X0, int Y0, float q0, int X1, int Y1, float q1, int X2,
+                                            int Y2, float q2, Tri2D &t)
+{
+    const long long A = (long long)(X1 - X0) * (long long)(Y2 - Y0) - (long long)(Y1 - Y0) * (long long)(X2 - X0);
+    if (A >= 0) return false;
+    t.X0 = X0; t.Y0 = Y0; t.q0 = q0;
+    t.X1 = X2; t.Y1 = Y2; t.q1 = q2;
+    t.X2 = X1; t.Y2 = Y1; t.q2 = q1;
+    t.A = -A;
+    return true;
+}
+
+// Plane of q over the snapped vertices, relative to vertex 0:
+//   a = fma(dq1, Y2-Y0, -(dq2*(Y1-Y0))) / A,  b = fma(dq2, X1-X0, -(dq1*(X2-X0))) / A.
+__device__ __forceinline__ void depth_plane(const Tri2D &t, float &pa, float &pb)
+{
+    const float fA = __ll2float_rn(t.A);
+    const float dq1 = __fsub_rn(t.q1, t.q0), dq2 = __fsub_rn(t.q2, t.q0);
+    pa = __fdiv_rn(__fmaf_rn(dq1, __int2float_rn(t.Y2 - t.Y0), -__fmul_rn(dq2, __int2float_rn(t.Y1 - t.Y0))), fA);
+    pb = __fdiv_rn(__fmaf_rn(dq2, __int2float_rn(t.X1 - t.X0), -__fmul_rn(dq1, __int2float_rn(t.X2 - t.X0))), fA);
+}
+
+// q at a sample, from its offset (exact integers) to vertex 0.
+__device__ __forceinline__ float plane_q(float pa, float pb, float q0, int dx, int dy)
+{
+    return __fmaf_rn(pa, __int2float_rn(dx), __fmaf_rn(pb, __int2float_rn(dy), q0));
+}
+
+// Top-left bias of edge i->j: 0 if the edge is top (dy == 0, dx > 0) or left
+// (dy < 0), else 1 (a sample exactly on it is outside).
+__device__ __forceinline__ int edge_bias(int Xi, int Yi, int Xj, int Yj)
+{
+    const int dy = Yj - Yi, dx = Xj - Xi;
+    return (dy < 0 || (dy == 0 && dx > 0)) ? 0 : 1;
+}
+
+// Candidate pixel range of the bounding box: centres 256x+128 in [min, max].
+__device__ __forceinline__ void pixel_range(const Tri2D &t, int &x0, int &x1, int &y0, int &y1, int &spanx,
+                                            int &spany)
+{
+    const int mnx = min(t.X0, min(t.X1, t.X2)), mxx = max(t.X0, max(t.X1, t.X2));
+    const int mny = min(t.Y0, min(t.Y1, t.Y2)), mxy = max(t.Y0, max(t.Y1, t.Y2));
+    x0 = (mnx + 127) >> 8;     // ceil((mnx - 128) / 256)
+    x1 = (mxx - 128) >> 8;     // floor((mxx - 128) / 256)
+    y0 = (mny + 127) >> 8;
+    y1 = (mxy - 128) >> 8;
+    spanx = mxx - mnx;
+    spany = mxy - mny;
+}
+
+}  // namespace hsr

@@ -1,0 +1,43 @@
+// K1 — per-(agent, vertex) transform to eye space and projection to 24.8 fixed point.
+//
+// Rule (reading of Sec. 4 "Sensory input": pinhole camera at the agent pose;
+// the paper fixes no arithmetic): x_e = fma(M00,x, fma(M01,y, fma(M02,z, M03)))
+// and likewise y_e, z_e; planar depth d = -z_e; q = 1/d;
+// sx = fma(fx, x_e*q, cx), sy = fma(-fy, y_e*q, cy); X = rint(256 sx), Y = rint(256 sy).
+// Every operation is a correctly rounded single IEEE op (explicit intrinsics,
+// and the file is compiled with --fmad=false), so results are reproducible.
+#pragma once
+#include "../hsr_internal.h"
+
+namespace hsr {
+
+// Per meshlet vertex, cached in shared memory for the warp that owns the meshlet.
+struct alignas(16) EyeVert {
+    float xe, ye, d, q;      // q valid when d >= near
+    int X, Y;                // snapped screen position, valid when d >= near
+    uint32_t gid;            // caller vertex index (near-clip edge ordering)
+    uint32_t pad_;
+};
+
+__device__ __forceinline__ void eye_transform(const float *M, float x, float y, float z,
+                                              float &xe, float &ye, float &d)
+{
+    xe = __fmaf_rn(M[0], x, __fmaf_rn(M[1], y, __fmaf_rn(M[2], z, M[3])));
+    ye = __fmaf_rn(M[4], x, __fmaf_rn(M[5], y, __fmaf_rn(M[6], z, M[7])));
+    const float ze = __fmaf_rn(M[8], x, __fmaf_rn(M[9], y, __fmaf_rn(M[10], z, M[11])));
+    d = -ze;
+}
+
+// Projection and snap of a point with d >= near (> 0). The caller guarantees
+// |256 sx|, |256 sy| < 2^30 (checked per call on the host).
+__device__ __forceinline__ void project_snap(float xe, float ye, float d, float fx, float fy, float cx,
+                                             float cy, float &q, int &X, int &Y)
+{
+    q = __frcp_rn(d);
+    const float sx = __fmaf_rn(fx, __fmul_rn(xe, q), cx);
+    const float sy = __fmaf_rn(-fy, __fmul_rn(ye, q), cy);
+    X = __float2int_rn(__fmul_rn(sx, 256.0f));
+    Y = __float2int_rn(__fmul_rn(sy, 256.0f));
+}
+
+}  // namespace hsr

@@ -1,0 +1,216 @@
+"""Python binding of the hsr C-ABI (include/hsr.h): argument marshalling only.
+
+Every step of rendering runs in the CUDA library ``_lib/libhsr.so``; this
+module only converts numpy / torch arguments to pointers. There is no
+fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhsr.so")
+
+HSR_OK = 0
+HSR_ERR_INVALID_ARG = 1
+HSR_ERR_OOM = 2
+HSR_ERR_CUDA = 3
+HSR_ERR_TIMEOUT = 4
+HSR_ERR_OVERFLOW = 5
+HSR_ERR_NO_DEVICE = 6
+BACKGROUND_ID = 0xFFFFFFFF
+
+
+class hsr_pose(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_float * 3), ("quat", ctypes.c_float * 4)]
+
+
+class hsr_intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("znear", ctypes.c_float), ("zfar", ctypes.c_float)]
+
+
+class hsr_scene_info(ctypes.Structure):
+    _fields_ = [("n_tris", ctypes.c_uint32), ("n_verts", ctypes.c_uint32), ("n_meshlets", ctypes.c_uint32),
+                ("n_groups", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+                ("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3)]
+
+
+class HsrError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {hsr_status_string(status)} ({status})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"hsr CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, U32 = ctypes.c_void_p, ctypes.c_uint32
+    sig = {
+        "hsr_scene_load": ([P, U32, P, U32, P, P, P, U32, U32, P, ctypes.POINTER(P)], ctypes.c_int),
+        "hsr_scene_free": ([P], ctypes.c_int),
+        "hsr_scene_get_info": ([P, ctypes.POINTER(hsr_scene_info)], ctypes.c_int),
+        "hsr_render": ([P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P], ctypes.c_int),
+        "hsr_render_batch": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P],
+                             ctypes.c_int),
+        "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "hsr_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+# -------------------------------------------------------------- raw C-ABI names
+def hsr_status_string(status: int) -> str:
+    return _lib.hsr_status_string(int(status)).decode()
+
+
+def hsr_version() -> str:
+    return _lib.hsr_version().decode()
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def as_intrinsics(intr) -> hsr_intrinsics:
+    a = np.asarray(getattr(intr, "as_array", lambda: intr)(), dtype=np.float32).reshape(6)
+    return hsr_intrinsics(*[float(v) for v in a])
+
+
+def hsr_scene_load(xyz, idx, uv=None, vert_rgb=None, atlas=None, tri_semantic=None):
+    """Load a scene from host arrays; returns an opaque handle (int)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    idx = np.ascontiguousarray(idx, dtype=np.uint32).reshape(-1, 3)
+    uv = None if uv is None else np.ascontiguousarray(uv, dtype=np.float32).reshape(-1, 2)
+    vert_rgb = None if vert_rgb is None else np.ascontiguousarray(vert_rgb, dtype=np.uint8).reshape(-1, 3)
+    aw = ah = 0
+    if atlas is not None:
+        atlas = np.ascontiguousarray(atlas, dtype=np.uint8)
+        ah, aw = atlas.shape[0], atlas.shape[1]
+    sem = None if tri_semantic is None else np.ascontiguousarray(tri_semantic, dtype=np.uint32).reshape(-1)
+    out = ctypes.c_void_p()
+    st = _lib.hsr_scene_load(_np_ptr(xyz), xyz.shape[0], _np_ptr(idx), idx.shape[0], _np_ptr(uv), _np_ptr(vert_rgb),
+                             _np_ptr(atlas), aw, ah, _np_ptr(sem), ctypes.byref(out))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_scene_load")
+    return out.value
+
+
+def hsr_scene_free(handle) -> None:
+    _lib.hsr_scene_free(ctypes.c_void_p(handle))
+
+
+def hsr_scene_get_info(handle) -> hsr_scene_info:
+    info = hsr_scene_info()
+    st = _lib.hsr_scene_get_info(ctypes.c_void_p(handle), ctypes.byref(info))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_scene_get_info")
+    return info
+
+
+def hsr_render(handle, poses, intr, width, height, rgb, depth, ids=None, stream=None) -> int:
+    """Raw render call; outputs are device tensors (or device pointers). Returns the status."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    ci = as_intrinsics(intr)
+    return _lib.hsr_render(ctypes.c_void_p(handle), _np_ptr(poses), poses.shape[0], ctypes.byref(ci), int(width),
+                           int(height), _dev_ptr(rgb), _dev_ptr(depth), _dev_ptr(ids), _stream_ptr(stream))
+
+
+def hsr_render_batch(handles: Sequence[int], scene_of_agent, poses, intr, width, height, rgb, depth, ids=None,
+                     stream=None) -> int:
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    soa = np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+    ci = as_intrinsics(intr)
+    return _lib.hsr_render_batch(arr, len(handles), _np_ptr(soa), _np_ptr(poses), poses.shape[0], ctypes.byref(ci),
+                                 int(width), int(height), _dev_ptr(rgb), _dev_ptr(depth), _dev_ptr(ids),
+                                 _stream_ptr(stream))
+
+
+# -------------------------------------------------------------- conveniences
+class SceneHandle:
+    """Owns a loaded scene; frees it on close() or garbage collection."""
+
+    def __init__(self, scene):
+        self.handle = hsr_scene_load(scene.xyz, scene.idx, scene.uv, scene.vrgb, scene.atlas, scene.sem)
+        self.info = hsr_scene_get_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            hsr_scene_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alloc_outputs(n: int, width: int, height: int, ids: bool = True, device="cuda"):
+    import torch
+    rgb = torch.empty((n, height, width, 3), dtype=torch.uint8, device=device)
+    depth = torch.empty((n, height, width), dtype=torch.float32, device=device)
+    out = {"rgb": rgb, "depth": depth}
+    if ids:
+        out["ids"] = torch.empty((n, height, width), dtype=torch.int32, device=device)
+    return out
+
+
+def render(scene: SceneHandle, poses, intr, width: int, height: int, ids: bool = True, out=None, stream=None):
+    """Render poses [N,7] of one scene into (new or given) device tensors."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    out = out or alloc_outputs(poses.shape[0], width, height, ids)
+    st = hsr_render(scene.handle, poses, intr, width, height, out["rgb"], out["depth"], out.get("ids"), stream)
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_render")
+    return out
+
+
+def render_batch(scenes: Sequence[SceneHandle], scene_of_agent, poses, intr, width: int, height: int,
+                 ids: bool = True, out=None, stream=None):
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    out = out or alloc_outputs(poses.shape[0], width, height, ids)
+    st = hsr_render_batch([s.handle for s in scenes], scene_of_agent, poses, intr, width, height, out["rgb"],
+                          out["depth"], out.get("ids"), stream)
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_render_batch")
+    return out
+
+
+def ids_u32(t):
+    """View an int32 id tensor as uint32 numpy."""
+    return t.cpu().numpy().view(np.uint32)
