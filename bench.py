@@ -332,7 +332,8 @@ def run_gpu(args, wk):
     peak, peak_kind = load_peaks()
     bview = sum(algorithmic_bytes_per_view(wk["scenes"][int(s)], W, H, wk["ids"]) for s in soa) / n
     kernel_ms_per_launch = local_ms / launches
-    achieved = (bview * n / launches) / (kernel_ms_per_launch / 1e3) / 1e9
+    bytes_per_launch = bview * n * args.steps / launches
+    achieved = bytes_per_launch / (kernel_ms_per_launch / 1e3) / 1e9
     traffic = recorded_traffic(wk["name"]) if args.mode == "batched" else None
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -344,7 +345,8 @@ def run_gpu(args, wk):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_view": bview, "kernel": "hsr::render_kernel",
+                     "algorithmic_bytes_per_view": bview, "views_per_launch": n * args.steps / launches,
+                     "kernel": "hsr render call (cull + raster + shade kernels)",
                      "kernel_ms_per_launch": kernel_ms_per_launch},
         "e2e": e2e,
         "gpu_launches": launches,
@@ -371,10 +373,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--agents", type=int, default=0, help="render only the first N agents (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     wk = make_workload(args.workload, args.seed)
+    if args.agents:
+        k = min(args.agents, len(wk["soa"]))
+        wk["soa"], wk["poses"] = wk["soa"][:k], wk["poses"][:k]
+        wk["name"] += f"-first{k}"
     res = run_reference(args, wk) if args.impl == "reference" else run_gpu(args, wk)
     if res is not None:
         print(json.dumps(res), flush=True)

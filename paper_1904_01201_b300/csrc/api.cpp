@@ -1,6 +1,6 @@
 // C-ABI of the sensor-rendering library (include/hsr.h): argument checking,
 // scene loading (device-resident meshlet layout), per-view camera setup on the
-// host, and launch of the fused render kernel.
+// host, and launch of the cull / raster / shade kernels.
 #include "../../include/hsr.h"
 
 #include <algorithm>
@@ -166,23 +166,36 @@ struct Staging {
 };
 thread_local Staging g_staging;
 
-LaunchCfg default_cfg(uint32_t width, uint32_t height)
-{
-    LaunchCfg c;
-    c.region_w = std::min<uint32_t>(64, width);
-    c.region_h = std::min<uint32_t>(64, height);
-    return c;
-}
+// World-space culling planes of a view (n . p + off >= 0 inside), double
+// precision from the float matrix: the image borders pushed out by
+// kPlaneMarginPx pixels, and the near / far planes pushed out by
+// kPlaneMarginDepth metres, so culling only removes geometry that cannot
+// produce a sample.
+constexpr double kPlaneMarginPx = 2.0;
+constexpr double kPlaneMarginDepth = 1e-4;
+constexpr uint64_t kMaxScratchBytes = 2ull << 30;
 
-int sm_count()
+void view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32_t H, float planes[24])
 {
-    static int cached = -1;
-    if (cached < 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    const double m = kPlaneMarginPx;
+    const double fx = in.fx, fy = in.fy, cx = in.cx, cy = in.cy;
+    const double ne[6][3] = {{fx, 0, -(cx + m)},
+                             {-fx, 0, -((double)W + m - cx)},
+                             {0, -fy, -(cy + m)},
+                             {0, fy, -((double)H + m - cy)},
+                             {0, 0, -1},
+                             {0, 0, 1}};
+    const double oe[6] = {0, 0, 0, 0, -((double)in.znear - kPlaneMarginDepth), (double)in.zfar + kPlaneMarginDepth};
+    for (int k = 0; k < 6; k++) {
+        for (int j = 0; j < 3; j++) {
+            double n = 0;
+            for (int i = 0; i < 3; i++) n += (double)M[i * 4 + j] * ne[k][i];
+            planes[4 * k + j] = (float)n;
+        }
+        double off = oe[k];
+        for (int i = 0; i < 3; i++) off += (double)M[i * 4 + 3] * ne[k][i];
+        planes[4 * k + 3] = (float)off;
     }
-    return cached;
 }
 
 // Shared body of hsr_render / hsr_render_batch.
@@ -197,11 +210,53 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         if (!scenes[i]) return HSR_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
-    // host: per-view camera setup (a1)
-    const size_t scene_bytes = sizeof(SceneDev) * n_scenes;
-    const size_t head = 256;
-    const size_t views_off = head + ((scene_bytes + 255) / 256) * 256;
-    const size_t total = views_off + sizeof(View) * (size_t)n;
+    // scratch: z-buffer (8 B / pixel / view) + worst-case visible-meshlet list
+    // (8 B per meshlet per view); large calls are split into halves
+    uint64_t list_entries = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const uint32_t s = scene_of_agent ? scene_of_agent[i] : 0u;
+        if (s >= n_scenes) return HSR_ERR_INVALID_ARG;
+        list_entries += scenes[s]->dev.n_meshlets;
+    }
+    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 8ull;
+    if (scratch > kMaxScratchBytes && n > 1) {
+        const uint32_t h = n / 2;
+        const size_t px = (size_t)width * height;
+        int st = render_views(scenes, n_scenes, scene_of_agent, poses, h, intr, width, height, rgb, depth, ids,
+                              stream_ptr, cfg_in);
+        if (st != HSR_OK) return st;
+        return render_views(scenes, n_scenes, scene_of_agent ? scene_of_agent + h : nullptr, poses + h, n - h, intr,
+                            width, height, rgb + 3 * px * h, depth + px * h, ids ? ids + px * h : nullptr, stream_ptr,
+                            cfg_in);
+    }
+
+    // views sorted by scene (stable), grouped into slots
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; i++) order[i] = i;
+    if (scene_of_agent)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return scene_of_agent[a] < scene_of_agent[b]; });
+    std::vector<uint32_t> slot_scene, slot_view_base, slot_item_base;
+    uint64_t items = 0;
+    for (uint32_t k = 0; k < n; k++) {
+        const uint32_t s = scene_of_agent ? scene_of_agent[order[k]] : 0u;
+        if (slot_scene.empty() || slot_scene.back() != s) {
+            slot_scene.push_back(s);
+            slot_view_base.push_back(k);
+            slot_item_base.push_back((uint32_t)items);
+        }
+        items += scenes[s]->dev.n_groups;
+    }
+    if (items >= 0xFFFFFFF0ull || list_entries >= 0xFFFFFFF0ull) return HSR_ERR_INVALID_ARG;
+    slot_item_base.push_back((uint32_t)items);
+    const uint32_t n_slots = (uint32_t)slot_scene.size();
+
+    // host staging: [counters | scenes | slot arrays | views]
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t off_scenes = 256;
+    const size_t off_slots = off_scenes + al(sizeof(SceneDev) * n_scenes);
+    const size_t off_views = off_slots + al(sizeof(uint32_t) * (3 * (size_t)n_slots + 1));
+    const size_t total = off_views + sizeof(View) * (size_t)n;
     Staging &st = g_staging;
     if (st.pending) {
         if (cudaEventSynchronize(st.done) != cudaSuccess) return HSR_ERR_CUDA;
@@ -217,31 +272,43 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     }
     if (!st.done && cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) return HSR_ERR_CUDA;
     auto *hbuf = static_cast<unsigned char *>(st.host);
-    std::memset(hbuf, 0, head);
-    SceneDev *hs = reinterpret_cast<SceneDev *>(hbuf + head);
+    std::memset(hbuf, 0, off_scenes);
+    SceneDev *hs = reinterpret_cast<SceneDev *>(hbuf + off_scenes);
     for (uint32_t i = 0; i < n_scenes; i++) hs[i] = scenes[i]->dev;
-    View *hv = reinterpret_cast<View *>(hbuf + views_off);
-    for (uint32_t i = 0; i < n; i++) {
+    uint32_t *hslot = reinterpret_cast<uint32_t *>(hbuf + off_slots);
+    for (uint32_t k = 0; k <= n_slots; k++) hslot[k] = slot_item_base[k];
+    for (uint32_t k = 0; k < n_slots; k++) hslot[n_slots + 1 + k] = slot_view_base[k];
+    for (uint32_t k = 0; k < n_slots; k++) hslot[2 * n_slots + 1 + k] = slot_scene[k];
+    View *hv = reinterpret_cast<View *>(hbuf + off_views);
+    for (uint32_t k = 0; k < n; k++) {
+        const uint32_t i = order[k];
         const uint32_t sidx = scene_of_agent ? scene_of_agent[i] : 0u;
-        if (sidx >= n_scenes) return HSR_ERR_INVALID_ARG;
-        View &v = hv[i];
+        View &v = hv[k];
         std::memset(&v, 0, sizeof(View));
+        // a1: camera setup
         if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
         if (!snap_in_range(scenes[sidx], poses[i], *intr)) return HSR_ERR_INVALID_ARG;
+        view_planes(v.M, *intr, width, height, v.planes);
         v.scene = sidx;
         v.frame = i;
     }
 
-    LaunchCfg cfg = cfg_in ? *cfg_in : default_cfg(width, height);
-    cfg.region_w = std::min(cfg.region_w, width);
-    cfg.region_h = std::min(cfg.region_h, height);
-
-    void *dbuf = nullptr;
+    LaunchCfg cfg = cfg_in ? *cfg_in : LaunchCfg{};
+    const size_t zbytes = (size_t)n * width * height * sizeof(unsigned long long);
+    const size_t lbytes = (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2);
+    void *dbuf = nullptr, *zbuf = nullptr;
     cudaError_t e = cudaMallocAsync(&dbuf, total, stream);
     if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMallocAsync(&zbuf, zbytes + lbytes, stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(dbuf, stream);
+        return cuda_status(e);
+    }
     e = cudaMemcpyAsync(dbuf, hbuf, total, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(zbuf, 0xFF, zbytes, stream);
     if (e != cudaSuccess) {
+        cudaFreeAsync(zbuf, stream);
         cudaFreeAsync(dbuf, stream);
         return HSR_ERR_CUDA;
     }
@@ -249,29 +316,34 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
 
     Params p{};
     auto *dchar = static_cast<unsigned char *>(dbuf);
-    p.work_counter = cfg.persistent ? reinterpret_cast<uint32_t *>(dchar) : nullptr;
-    p.scenes = reinterpret_cast<const SceneDev *>(dchar + head);
-    p.views = reinterpret_cast<const View *>(dchar + views_off);
+    const uint32_t *dslot = reinterpret_cast<const uint32_t *>(dchar + off_slots);
+    p.vis_count = reinterpret_cast<uint32_t *>(dchar);
+    p.vis = reinterpret_cast<uint2 *>(static_cast<unsigned char *>(zbuf) + zbytes);
+    p.vis_cap = (uint32_t)list_entries;
+    p.scenes = reinterpret_cast<const SceneDev *>(dchar + off_scenes);
+    p.views = reinterpret_cast<const View *>(dchar + off_views);
+    p.slot_item_base = dslot;
+    p.slot_view_base = dslot + n_slots + 1;
+    p.slot_scene = dslot + 2 * n_slots + 1;
+    p.n_slots = n_slots;
+    p.zbuf = static_cast<unsigned long long *>(zbuf);
     p.rgb = rgb;
     p.depth = depth;
     p.ids = ids;
     p.n_views = n;
     p.width = width;
     p.height = height;
+    p.total_items = (uint32_t)items;
     p.fx = intr->fx; p.fy = intr->fy; p.cx = intr->cx; p.cy = intr->cy;
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = far_threshold(intr->zfar);
-    p.region_w = cfg.region_w;
-    p.region_h = cfg.region_h;
-    p.regions_x = (width + cfg.region_w - 1) / cfg.region_w;
-    p.regions_y = (height + cfg.region_h - 1) / cfg.region_h;
-    p.n_items = n * p.regions_x * p.regions_y;
     p.small_px = cfg.small_px;
-    (void)sm_count;
+    p.chunk = cfg.chunk;
     e = launch_render(p, cfg, stream);
-    cudaError_t ef = cudaFreeAsync(dbuf, stream);
+    cudaError_t e1 = cudaFreeAsync(zbuf, stream);
+    cudaError_t e2 = cudaFreeAsync(dbuf, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    if (ef != cudaSuccess) return HSR_ERR_CUDA;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return HSR_ERR_CUDA;
     return HSR_OK;
 }
 

@@ -47,10 +47,12 @@ struct SceneDev {
     int pad_;
 };
 
-// One rendered view: world-to-eye matrix (rows of a 3x4), its scene and the
-// output frame it writes.
+// One rendered view: world-to-eye matrix (rows of a 3x4), the six world-space
+// frustum planes used for culling (n . p + off >= 0 inside), its scene, and
+// the output frame it writes.
 struct alignas(16) View {
     float M[12];
+    float planes[24];
     uint32_t scene;
     uint32_t frame;
     uint32_t pad_[2];
@@ -58,29 +60,37 @@ struct alignas(16) View {
 
 struct Params {
     const SceneDev *scenes;    // device array
-    const View *views;         // device array, n_views
+    const View *views;         // device array, n_views (sorted by scene)
+    unsigned long long *zbuf;  // [n_views][H][W] 64-bit keys, preset to ~0
     uint8_t *rgb;
     float *depth;
     uint32_t *ids;             // may be null
-    uint32_t *work_counter;    // persistent mode: items past gridDim.x; null: one item per CTA
+    uint2 *vis;                // visible (view, meshlet) pairs written by the cull kernel
+    uint32_t *vis_count;       // number of pairs in `vis` (preset to 0)
+    uint32_t vis_cap;          // capacity of `vis`
+    // Views are sorted by scene; slot k covers views [slot_view_base[k], ...)
+    // of scene slot_scene[k] and work items [slot_item_base[k], slot_item_base[k+1]),
+    // item = slot_item_base[k] + (view - slot_view_base[k]) * n_groups + group.
+    const uint32_t *slot_item_base;   // n_slots + 1
+    const uint32_t *slot_view_base;   // n_slots
+    const uint32_t *slot_scene;       // n_slots
+    uint32_t n_slots;
     uint32_t n_views, width, height;
+    uint32_t total_items;      // sum over views of their scene's group count
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar
-    uint32_t region_w, region_h, regions_x, regions_y;
-    uint32_t n_items;          // n_views * regions_x * regions_y
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels
+    uint32_t chunk;            // consecutive visible pairs a raster warp takes per step
 };
 
 // Launch configuration chosen by the host (autotuned).
 struct LaunchCfg {
-    uint32_t region_w = 64, region_h = 64;
     uint32_t small_px = 16;
-    uint32_t ctas_per_sm = 2;
-    bool persistent = true;
+    uint32_t chunk = 4;
+    uint32_t raster_ctas_per_sm = 3;
 };
 
-// Launches the fused render kernel; returns a cudaError_t.
+// Launches the cull, raster and shade kernels on `stream`.
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream);
-size_t render_smem_bytes(const LaunchCfg &cfg);
 
 }  // namespace hsr

@@ -1,22 +1,21 @@
-// K4 — fixed-point edge-function rasteriser with a per-region z-buffer in
-// shared memory.
+// K4 — fixed-point edge-function rasteriser with an order-independent
+// 64-bit z-buffer per view.
 //
 // Coverage (reading; the paper's OpenGL rasteriser is not specified): sample
 // at pixel centres (256x+128, 256y+128) in 24.8 fixed point; E_k for the edge
-// opposite vertex k is evaluated exactly in integers; a sample is inside when
-// every E_k > 0, or E_k == 0 on a top or left edge. The depth test keeps, per
-// pixel, the minimum 64-bit key (~bits(q) << 32 | triangle index): largest
-// inverse depth q first, lower triangle index on ties. Because the key is a
-// total order the result does not depend on the order fragments arrive in.
+// opposite vertex k is exact in integers; a sample is inside when every
+// E_k > 0, or E_k == 0 on a top or left edge. The depth test keeps, per pixel,
+// the minimum key (~bits(q) << 32 | triangle index): largest inverse depth q
+// first, lower triangle index on ties. The key is a total order, so the
+// result does not depend on the order fragments arrive in; each fragment is
+// merged with one 64-bit atomic minimum (a fire-and-forget reduction in L2).
 //
 // Two paths:
-//  * small triangles (<= small_px candidate pixels and a bounding box under
-//    2^15 sub-pixels per axis, so every edge value fits in int32): one thread
-//    walks its own triangle's pixels;
+//  * small triangles (<= small_px candidate pixels, bounding box under 2^15
+//    sub-pixels per axis so every edge value fits in int32): one thread walks
+//    its own triangle's pixels;
 //  * other triangles are queued per warp in shared memory and rasterised by
 //    the whole warp, lanes spread over an 8x4 pixel footprint, int64 edges.
-// Both merge into the z-buffer with a 64-bit shared-memory atomicMin, skipped
-// when the stored key is already smaller.
 #pragma once
 #include "setup.cuh"
 
@@ -27,7 +26,7 @@ struct alignas(16) BigTri {
     int X0, Y0, X1, Y1, X2, Y2;
     float pa, pb, q0;
     uint32_t id;
-    short x0, y0, x1, y1;      // candidate pixel range, already clipped to the region
+    unsigned short x0, y0, x1, y1;      // candidate pixel range, clipped to the image
 };
 
 __device__ __forceinline__ unsigned long long depth_key(float q, uint32_t id)
@@ -37,15 +36,14 @@ __device__ __forceinline__ unsigned long long depth_key(float q, uint32_t id)
 
 __device__ __forceinline__ void zmin(unsigned long long *z, unsigned long long key)
 {
-    if (key < *z) atomicMin(z, key);
+    atomicMin(z, key);
 }
 
 // One thread, one small triangle. Exactness: |X_j - X_i| and |P - X_i| are
-// below 2^15 inside the bounding box, so every product is below 2^30 and every
-// edge value below 2^31.
-__device__ __forceinline__ void raster_small(const Tri2D &t, float pa, float pb, uint32_t id, int x0,
-                                             int x1, int y0, int y1, float q_far, unsigned long long *zbuf,
-                                             int rx0, int ry0, int RW)
+// below 2^15 inside the bounding box, so every product is below 2^30 and
+// every edge value below 2^31.
+__device__ __forceinline__ void raster_small(const Tri2D &t, float pa, float pb, uint32_t id, int x0, int x1,
+                                             int y0, int y1, float q_far, unsigned long long *zbuf, int W)
 {
     const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
     const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
@@ -63,14 +61,14 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, float pa, float pb,
             if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
             const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
             if (!(q >= q_far)) continue;
-            zmin(zbuf + (py - ry0) * RW + (px - rx0), depth_key(q, id));
+            zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
         }
     }
 }
 
 // The whole warp, one queued triangle.
-__device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float q_far,
-                                                unsigned long long *zbuf, int rx0, int ry0, int RW)
+__device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float q_far, unsigned long long *zbuf,
+                                                int W)
 {
     const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
     const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
@@ -79,9 +77,9 @@ __device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float
     const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
     const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
     const int lx = lane & 7, ly = lane >> 3;
-    for (int py = t.y0 + ly; py <= t.y1; py += 4) {
+    for (int py = (int)t.y0 + ly; py <= (int)t.y1; py += 4) {
         const int Py = 256 * py + 128;
-        for (int px = t.x0 + lx; px <= t.x1; px += 8) {
+        for (int px = (int)t.x0 + lx; px <= (int)t.x1; px += 8) {
             const int Px = 256 * px + 128;
             const long long e0 = (long long)dx0 * (Py - t.Y1) - (long long)dy0 * (Px - t.X1);
             const long long e1 = (long long)dx1 * (Py - t.Y2) - (long long)dy1 * (Px - t.X2);
@@ -89,7 +87,7 @@ __device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float
             if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
             const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0);
             if (!(q >= q_far)) continue;
-            zmin(zbuf + (py - ry0) * RW + (px - rx0), depth_key(q, t.id));
+            zmin(zbuf + (size_t)py * W + px, depth_key(q, t.id));
         }
     }
 }

@@ -1,8 +1,8 @@
-// K5 — resolve and shade (deferred): for each pixel of the region, decode the
-// winning key, rebuild that triangle's setup exactly as the rasteriser did,
-// find the (sub-)triangle that produced the fragment, and write the three
-// sensor outputs of the single pass (Sec. 3 "Rendering engine": colour, depth
-// and semantic outputs together).
+// K5 — resolve and shade (deferred): each pixel's winning key names the
+// triangle and its inverse depth; the triangle's setup is rebuilt exactly as
+// the rasteriser built it, and the three sensor outputs of the single pass are
+// produced (Sec. 3 "Rendering engine": colour, depth and semantic outputs
+// together).
 //
 // Readings: perspective-correct weights w_k = E_k(P) * q_k normalised;
 // texture lookups are bilinear, clamp-to-edge, at (u*Wt - 0.5, v*Ht - 0.5)
@@ -14,12 +14,6 @@
 namespace hsr {
 
 constexpr uint32_t kBackgroundId = 0xFFFFFFFFu;
-
-struct ShadeOut {
-    uint32_t rgb;      // r | g << 8 | b << 16
-    float depth;
-    uint32_t id;
-};
 
 __device__ __forceinline__ uint32_t round_channel(float c)
 {
@@ -41,7 +35,7 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
     const uint32_t c00 = __ldg(S.atlas + (size_t)y0 * W + x0), c10 = __ldg(S.atlas + (size_t)y0 * W + x1);
     const uint32_t c01 = __ldg(S.atlas + (size_t)y1 * W + x0), c11 = __ldg(S.atlas + (size_t)y1 * W + x1);
-    const float gx = 1.0f - ax, gy = 1.0f - ay;
+    const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
     uint32_t out = 0;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -54,13 +48,10 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     return out;
 }
 
-// Rebuild triangle `tri` with NA attributes, find the sub-triangle whose
-// fragment at (Px, Py) has inverse depth qk, and interpolate its attributes.
+// Vertices of a triangle with NA attributes, in eye space.
 template <int NA>
-__device__ __forceinline__ bool refind_fragment(const SceneDev &S, const float *M, const Params &p,
-                                                const uint4 &T, int Px, int Py, float qk, float (&attr)[3])
+__device__ __forceinline__ void load_tri(const SceneDev &S, const float *M, const uint4 &T, CVert<NA> (&v)[3])
 {
-    CVert<NA> v[3];
     const uint32_t gi[3] = {T.x, T.y, T.z};
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -78,14 +69,70 @@ __device__ __forceinline__ bool refind_fragment(const SceneDev &S, const float *
             v[k].a[NA > 2 ? 2 : 0] = (float)((c >> 16) & 255u);
         }
     }
-    CVert<NA> poly[4];
-    int np;
-    if (v[0].d >= p.znear && v[1].d >= p.znear && v[2].d >= p.znear) {
-        poly[0] = v[0]; poly[1] = v[1]; poly[2] = v[2];
-        np = 3;
-    } else {
-        np = clip_near<NA>(v, p.znear, poly);
+}
+
+// Perspective-correct attribute interpolation at P over an oriented triangle
+// whose attributes are a0 (vertex 0), a1 (vertex 1), a2 (vertex 2).
+template <int NA>
+__device__ __forceinline__ void interp(const Tri2D &t, int Px, int Py, const float *a0, const float *a1,
+                                       const float *a2, float (&attr)[3])
+{
+    const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
+    const long long e1 = (long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2);
+    const long long e2 = (long long)(t.X1 - t.X0) * (Py - t.Y0) - (long long)(t.Y1 - t.Y0) * (Px - t.X0);
+    const float w0 = __fmul_rn(__ll2float_rn(e0), t.q0);
+    const float w1 = __fmul_rn(__ll2float_rn(e1), t.q1);
+    const float w2 = __fmul_rn(__ll2float_rn(e2), t.q2);
+    const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
+    const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
+#pragma unroll
+    for (int c = 0; c < NA; c++) attr[c] = __fmaf_rn(l0, a0[c], __fmaf_rn(l1, a1[c], __fmul_rn(l2, a2[c])));
+}
+
+// Setup of the last triangle a thread shaded (neighbouring pixels often share it).
+template <int NA>
+struct ShadeTri {
+    uint32_t tri = 0xFFFFFFFFu;
+    bool clipped = false;
+    Tri2D t;                            // oriented (unclipped case)
+    float a[3][NA > 0 ? NA : 1];        // attributes in oriented order
+    uint4 T;
+};
+
+template <int NA>
+__device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev &S, const float *M,
+                                                const Params &p, uint32_t tri)
+{
+    st.tri = tri;
+    st.T = __ldg(S.tri + tri);
+    CVert<NA> v[3];
+    load_tri<NA>(S, M, st.T, v);
+    st.clipped = !(v[0].d >= p.znear && v[1].d >= p.znear && v[2].d >= p.znear);
+    if (st.clipped) return;
+    int X[3], Y[3];
+    float q[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) project_snap(v[k].xe, v[k].ye, v[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
+    // a winning fragment exists, so the triangle is front facing: orient_cull succeeds
+    orient_cull(X[0], Y[0], q[0], X[1], Y[1], q[1], X[2], Y[2], q[2], st.t);
+#pragma unroll
+    for (int c = 0; c < NA; c++) {
+        st.a[0][c] = v[0].a[c];
+        st.a[1][c] = v[2].a[c];
+        st.a[2][c] = v[1].a[c];
     }
+}
+
+// Near-clipped triangle: rebuild the clipped polygon and find the fan
+// sub-triangle whose fragment at P has inverse depth qk.
+template <int NA>
+__device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M, const Params &p, const uint4 &T,
+                                              int Px, int Py, float qk, float (&attr)[3])
+{
+    CVert<NA> v[3];
+    load_tri<NA>(S, M, T, v);
+    CVert<NA> poly[4];
+    const int np = clip_near<NA>(v, p.znear, poly);
     int X[4], Y[4];
     float q[4];
     for (int k = 0; k < np; k++) project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
@@ -104,47 +151,45 @@ __device__ __forceinline__ bool refind_fragment(const SceneDev &S, const float *
         const float qq = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
         if (__float_as_uint(qq) != __float_as_uint(qk)) continue;
         // oriented order is (poly 0, poly f+2, poly f+1)
-        const float w0 = __fmul_rn(__ll2float_rn(e0), t.q0);
-        const float w1 = __fmul_rn(__ll2float_rn(e1), t.q1);
-        const float w2 = __fmul_rn(__ll2float_rn(e2), t.q2);
-        const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
-        const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
-#pragma unroll
-        for (int c = 0; c < NA; c++)
-            attr[c] = __fmaf_rn(l0, poly[0].a[c], __fmaf_rn(l1, poly[f + 2].a[c], __fmul_rn(l2, poly[f + 1].a[c])));
+        interp<NA>(t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a, attr);
         return true;
     }
     return false;
 }
 
-__device__ __forceinline__ ShadeOut shade_pixel(const SceneDev &S, const float *M, const Params &p, int px,
-                                                int py, unsigned long long key)
+template <int NA>
+__device__ __forceinline__ uint32_t shade_colour(const SceneDev &S, const float (&a)[3])
 {
-    ShadeOut o;
+    if (NA == 2) return sample_bilinear(S, a[0], a[1]);
+    if (NA == 3) return round_channel(a[0]) | (round_channel(a[1]) << 8) | (round_channel(a[2]) << 16);
+    return 0xFFFFFFu;
+}
+
+// Shade one pixel given its key; `st` caches the last triangle's setup.
+template <int NA>
+__device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S, const float *M, const Params &p,
+                                            int px, int py, unsigned long long key, uint32_t &rgb, float &depth,
+                                            uint32_t &id)
+{
     if (key == ~0ull) {
-        o.rgb = 0;
-        o.depth = 0.0f;
-        o.id = kBackgroundId;
-        return o;
+        rgb = 0;
+        depth = 0.0f;
+        id = kBackgroundId;
+        return;
     }
     const uint32_t tri = (uint32_t)key;
     const float qk = __uint_as_float(~(uint32_t)(key >> 32));
-    o.depth = __frcp_rn(qk);
-    const uint4 T = __ldg(S.tri + tri);
-    o.id = T.w;
+    depth = __frcp_rn(qk);
+    if (tri != st.tri) build_shade_tri<NA>(st, S, M, p, tri);
+    id = st.T.w;
     const int Px = 256 * px + 128, Py = 256 * py + 128;
     float a[3] = {0.f, 0.f, 0.f};
-    if (S.color_mode == kColorTexture) {
-        o.rgb = refind_fragment<2>(S, M, p, T, Px, Py, qk, a) ? sample_bilinear(S, a[0], a[1]) : 0u;
-    } else if (S.color_mode == kColorVertex) {
-        if (refind_fragment<3>(S, M, p, T, Px, Py, qk, a))
-            o.rgb = round_channel(a[0]) | (round_channel(a[1]) << 8) | (round_channel(a[2]) << 16);
-        else
-            o.rgb = 0;
+    if (!st.clipped) {
+        interp<NA>(st.t, Px, Py, st.a[0], st.a[1], st.a[2], a);
+        rgb = shade_colour<NA>(S, a);
     } else {
-        o.rgb = 0xFFFFFFu;
+        rgb = shade_clipped<NA>(S, M, p, st.T, Px, Py, qk, a) ? shade_colour<NA>(S, a) : 0u;
     }
-    return o;
 }
 
 }  // namespace hsr

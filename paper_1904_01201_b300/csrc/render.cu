@@ -1,14 +1,22 @@
-// Fused render kernel: one CTA per (view, screen region) work item, all five
-// stages in one launch so no intermediate ever leaves the SM:
-//   K3 bin   — groups / meshlets culled against the region frustum (bin.cuh)
-//   K1       — meshlet vertices transformed and snapped into a per-warp
-//              shared-memory cache (transform.cuh)
-//   K2       — per-triangle reject / near clip / cull / depth plane (setup.cuh)
-//   K4       — per-thread or per-warp fixed-point raster into the region's
-//              shared-memory z-buffer (raster.cuh)
-//   K5       — deferred resolve + shade + store of the region (shade.cuh)
-// In persistent mode a grid of (#SM x CTAs/SM) CTAs pulls further work items
-// from a global counter; otherwise each CTA renders exactly one item.
+// Render kernels.
+//
+// cull_kernel (K3): one warp per (view, meshlet group) work item; the group
+//   and then its meshlets are tested against the view frustum and the visible
+//   (view, meshlet) pairs are appended to a compact list (bin.cuh).
+// raster_kernel: warps take equal shares of the visible pairs (grid-stride,
+//   `chunk` consecutive pairs at a time). For each pair:
+//   K1 — transform + snap the meshlet's vertices into a per-warp
+//        shared-memory cache (transform.cuh)
+//   K2 — per-lane triangle reject / near clip / cull / depth plane (setup.cuh)
+//   K4 — per-thread raster of small triangles, warp-cooperative raster of the
+//        rest, into the view's 64-bit z-buffer (raster.cuh)
+// shade_kernel (K5): one CTA row per view; each thread resolves four
+//   consecutive pixels of a row (shade.cuh) and writes RGB / depth / id with
+//   vector stores when the row layout allows it.
+// Work items are ordered scene-major then view-major, so a scene's geometry
+// stays hot in L2 while its views are in flight.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "hsr_internal.h"
@@ -20,65 +28,109 @@
 
 namespace hsr {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-constexpr int kGroupChunk = 64;
-constexpr int kMlistCap = kGroupChunk * kGroupMeshlets;
+constexpr int kRasterWarps = 8;
+constexpr int kRasterThreads = kRasterWarps * 32;
 constexpr int kBigCap = 2 * kMeshletTris;        // a lane emits at most two sub-triangles
+constexpr int kShadeThreads = 256;
 
-// Shared-memory layout (every section starts on a 128-byte boundary):
-//   z-buffer [RW*RH] u64 | vertex caches [warps][64] | big-triangle queues [warps][64] | meshlet queue
-__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
-constexpr size_t kVcacheBytes = align128((size_t)kWarps * kMeshletVerts * sizeof(EyeVert));
-constexpr size_t kBigqBytes = align128((size_t)kWarps * kBigCap * sizeof(BigTri));
-constexpr size_t kMlistBytes = align128((size_t)kMlistCap * sizeof(uint32_t));
-
-__host__ __device__ inline size_t zbuf_bytes(uint32_t rw, uint32_t rh)
-{
-    return align128((size_t)rw * rh * sizeof(unsigned long long));
-}
-
-size_t render_smem_bytes(const LaunchCfg &c)
-{
-    return zbuf_bytes(c.region_w, c.region_h) + kVcacheBytes + kBigqBytes + kMlistBytes;
-}
-
-// Per-lane sub-triangle after setup (at most two per source triangle).
-struct SubTri {
-    Tri2D t;
-    float pa, pb;
-    int x0, x1, y0, y1;
-    bool small;
+// --------------------------------------------------------------------- cull
+// Decode a (view, group) work item: views are sorted by scene, slot k holds
+// the items of one scene's views.
+struct ItemDecoder {
+    int s = -1;
+    uint32_t lo = 0, hi = 0, G = 1, vbase = 0, scene = 0;
+    __device__ __forceinline__ void locate(const Params &p, uint32_t item)
+    {
+        if (s >= 0 && item >= lo && item < hi) return;
+        int k = 0;
+        while (p.slot_item_base[k + 1] <= item) k++;
+        s = k;
+        lo = p.slot_item_base[k];
+        hi = p.slot_item_base[k + 1];
+        vbase = p.slot_view_base[k];
+        scene = p.slot_scene[k];
+        G = p.scenes[scene].n_groups;
+    }
 };
 
-__device__ __forceinline__ bool finish_setup(SubTri &s, const Params &p, int rx0, int ry0, int rx1, int ry1)
+__global__ void __launch_bounds__(256) cull_kernel(const Params p)
 {
-    int spanx, spany;
-    pixel_range(s.t, s.x0, s.x1, s.y0, s.y1, spanx, spany);
-    s.x0 = max(s.x0, rx0);
-    s.y0 = max(s.y0, ry0);
-    s.x1 = min(s.x1, rx1 - 1);
-    s.y1 = min(s.y1, ry1 - 1);
-    if (s.x0 > s.x1 || s.y0 > s.y1) return false;      // no sample of this region
-    depth_plane(s.t, s.pa, s.pb);
-    const int npx = (s.x1 - s.x0 + 1) * (s.y1 - s.y0 + 1);
-    s.small = spanx < 32768 && spany < 32768 && npx <= (int)p.small_px;
-    return true;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    ItemDecoder dec;
+    for (uint32_t item = warp_id; item < p.total_items; item += n_warps) {
+        dec.locate(p, item);
+        const uint32_t local = item - dec.lo;
+        const uint32_t vi = dec.vbase + local / dec.G, g = local % dec.G;
+        const SceneDev &S = p.scenes[dec.scene];
+        const float *pl = p.views[vi].planes;
+        const Group grp = S.groups[g];
+        if (!aabb_visible(pl, grp.bmin, grp.bmax)) continue;
+        const uint32_t m = grp.m0 + lane;
+        bool vis = false;
+        if (m < grp.m1) {
+            const Meshlet ml = S.meshlets[m];
+            vis = aabb_visible(pl, ml.bmin, ml.bmax);
+        }
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, vis);
+        if (!mask) continue;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(p.vis_count, (uint32_t)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        const uint32_t slot = base + __popc(mask & ((1u << lane) - 1u));
+        if (vis && slot < p.vis_cap) p.vis[slot] = make_uint2(vi, m);
+    }
 }
 
-__device__ __forceinline__ void process_meshlet(const SceneDev &S, const float *M, const Params &p,
-                                                uint32_t m, EyeVert *vc, BigTri *bigq,
-                                                unsigned long long *zbuf, int rx0, int ry0, int rx1, int ry1,
-                                                int RW, int lane)
+// --------------------------------------------------------------------- raster
+struct WarpCtx {
+    // view-dependent, warp-uniform
+    unsigned long long *zbuf;
+    const Meshlet *meshlets;
+    const float4 *mvert;
+    const uint2 *mtri;
+};
+
+// Emit one front-facing (sub-)triangle: clip its pixel range to the image,
+// raster it here when small, else queue it for the warp.
+__device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Params &p, unsigned long long *zbuf,
+                                         BigTri *bigq, uint32_t *bign)
 {
-    const Meshlet ml = S.meshlets[m];
-    const uint32_t vend = S.meshlets[m + 1].vbase, tend = S.meshlets[m + 1].tbase;
+    int x0, x1, y0, y1, spanx, spany;
+    pixel_range(t, x0, x1, y0, y1, spanx, spany);
+    x0 = max(x0, 0);
+    y0 = max(y0, 0);
+    x1 = min(x1, (int)p.width - 1);
+    y1 = min(y1, (int)p.height - 1);
+    if (x0 > x1 || y0 > y1) return;            // no sample on screen
+    float pa, pb;
+    depth_plane(t, pa, pb);
+    const int npx = (x1 - x0 + 1) * (y1 - y0 + 1);
+    if (spanx < 32768 && spany < 32768 && npx <= (int)p.small_px) {
+        raster_small(t, pa, pb, id, x0, x1, y0, y1, p.q_far, zbuf, (int)p.width);
+        return;
+    }
+    const uint32_t slot = atomicAdd(bign, 1u);
+    BigTri r;
+    r.X0 = t.X0; r.Y0 = t.Y0; r.X1 = t.X1; r.Y1 = t.Y1; r.X2 = t.X2; r.Y2 = t.Y2;
+    r.pa = pa; r.pb = pb; r.q0 = t.q0; r.id = id;
+    r.x0 = (unsigned short)x0; r.x1 = (unsigned short)x1;
+    r.y0 = (unsigned short)y0; r.y1 = (unsigned short)y1;
+    bigq[slot] = r;
+}
+
+__device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M, const Params &p, uint32_t m,
+                                                EyeVert *vc, BigTri *bigq, uint32_t *bign, int lane)
+{
+    const Meshlet ml = c.meshlets[m];
+    const uint32_t vend = c.meshlets[m + 1].vbase, tend = c.meshlets[m + 1].tbase;
     const int nv = (int)(vend - ml.vbase), nt = (int)(tend - ml.tbase);
     const float zn = p.znear, zf = p.zfar;
 
     // K1: transform + snap this meshlet's vertices
     for (int v = lane; v < nv; v += 32) {
-        const float4 P = __ldg(S.mvert + ml.vbase + v);
+        const float4 P = __ldg(c.mvert + ml.vbase + v);
         EyeVert e;
         eye_transform(M, P.x, P.y, P.z, e.xe, e.ye, e.d);
         e.gid = __float_as_uint(P.w);
@@ -92,186 +144,178 @@ __device__ __forceinline__ void process_meshlet(const SceneDev &S, const float *
     }
     __syncwarp();
 
-    // K2: one triangle per lane -> up to two front-facing sub-triangles
-    SubTri st[2];
-    int nst = 0;
-    uint32_t id = 0;
+    // K2 + K4: one triangle per lane
     if (lane < nt) {
-        const uint2 mt = __ldg(S.mtri + ml.tbase + lane);
-        const EyeVert a = vc[mt.x & 255u], b = vc[(mt.x >> 8) & 255u], c = vc[(mt.x >> 16) & 255u];
-        id = mt.y;
-        const bool all_near = a.d < zn && b.d < zn && c.d < zn;
-        const bool all_far = a.d > zf && b.d > zf && c.d > zf;
+        const uint2 mt = __ldg(c.mtri + ml.tbase + lane);
+        const EyeVert a = vc[mt.x & 255u], b = vc[(mt.x >> 8) & 255u], cc = vc[(mt.x >> 16) & 255u];
+        const uint32_t id = mt.y;
+        const bool all_near = a.d < zn && b.d < zn && cc.d < zn;
+        const bool all_far = a.d > zf && b.d > zf && cc.d > zf;
         if (!all_near && !all_far) {
-            if (a.d >= zn && b.d >= zn && c.d >= zn) {
-                if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, c.X, c.Y, c.q, st[0].t) &&
-                    finish_setup(st[0], p, rx0, ry0, rx1, ry1))
-                    nst = 1;
+            Tri2D t;
+            if (a.d >= zn && b.d >= zn && cc.d >= zn) {
+                if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, cc.X, cc.Y, cc.q, t)) emit_tri(t, id, p, c.zbuf, bigq, bign);
             } else {
                 CVert<0> v[3];
                 v[0].xe = a.xe; v[0].ye = a.ye; v[0].d = a.d; v[0].gid = a.gid;
                 v[1].xe = b.xe; v[1].ye = b.ye; v[1].d = b.d; v[1].gid = b.gid;
-                v[2].xe = c.xe; v[2].ye = c.ye; v[2].d = c.d; v[2].gid = c.gid;
+                v[2].xe = cc.xe; v[2].ye = cc.ye; v[2].d = cc.d; v[2].gid = cc.gid;
                 CVert<0> poly[4];
                 const int np = clip_near<0>(v, zn, poly);
                 int X[4], Y[4];
                 float q[4];
                 for (int k = 0; k < np; k++)
                     project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
-                for (int f = 0; f + 2 < np; f++) {
-                    SubTri &s = st[nst];
-                    if (orient_cull(X[0], Y[0], q[0], X[f + 1], Y[f + 1], q[f + 1], X[f + 2], Y[f + 2], q[f + 2], s.t) &&
-                        finish_setup(s, p, rx0, ry0, rx1, ry1))
-                        nst++;
-                }
+                for (int f = 0; f + 2 < np; f++)
+                    if (orient_cull(X[0], Y[0], q[0], X[f + 1], Y[f + 1], q[f + 1], X[f + 2], Y[f + 2], q[f + 2], t))
+                        emit_tri(t, id, p, c.zbuf, bigq, bign);
             }
         }
     }
-
-    // K4: small triangles per thread; the rest through the warp queue
-    int qn = 0;
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const bool have = k < nst;
-        const bool small = have && st[k].small;
-        const bool big = have && !st[k].small;
-        if (small)
-            raster_small(st[k].t, st[k].pa, st[k].pb, id, st[k].x0, st[k].x1, st[k].y0, st[k].y1, p.q_far, zbuf,
-                         rx0, ry0, RW);
-        const unsigned bm = __ballot_sync(0xFFFFFFFFu, big);
-        if (big) {
-            BigTri r;
-            r.X0 = st[k].t.X0; r.Y0 = st[k].t.Y0;
-            r.X1 = st[k].t.X1; r.Y1 = st[k].t.Y1;
-            r.X2 = st[k].t.X2; r.Y2 = st[k].t.Y2;
-            r.pa = st[k].pa; r.pb = st[k].pb; r.q0 = st[k].t.q0;
-            r.id = id;
-            r.x0 = (short)st[k].x0; r.x1 = (short)st[k].x1;
-            r.y0 = (short)st[k].y0; r.y1 = (short)st[k].y1;
-            bigq[qn + __popc(bm & ((1u << lane) - 1u))] = r;
-        }
-        qn += __popc(bm);
-    }
     __syncwarp();
-    for (int r = 0; r < qn; r++) raster_big_warp(bigq[r], lane, p.q_far, zbuf, rx0, ry0, RW);
+    const uint32_t nb = *bign;
+    for (uint32_t r = 0; r < nb; r++) raster_big_warp(bigq[r], lane, p.q_far, c.zbuf, (int)p.width);
+    __syncwarp();
+    if (lane == 0) *bign = 0;
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kThreads, 2) render_kernel(const Params p)
+__global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int RW = (int)p.region_w, RH = (int)p.region_h;
-    unsigned long long *zbuf = reinterpret_cast<unsigned long long *>(smem);
-    const size_t zb = zbuf_bytes(p.region_w, p.region_h);
-    EyeVert *vcache = reinterpret_cast<EyeVert *>(smem + zb);
-    BigTri *bigq = reinterpret_cast<BigTri *>(smem + zb + kVcacheBytes);
-    uint32_t *mlist = reinterpret_cast<uint32_t *>(smem + zb + kVcacheBytes + kBigqBytes);
-
-    __shared__ float sM[12];
-    __shared__ Plane sPlanes[6];
-    __shared__ SceneDev sS;
-    __shared__ uint32_t s_item, s_mcount, s_mnext;
+    __shared__ EyeVert s_vc[kRasterWarps][kMeshletVerts];
+    __shared__ BigTri s_big[kRasterWarps][kBigCap];
+    __shared__ float s_view[kRasterWarps][12];
+    __shared__ uint32_t s_bign[kRasterWarps];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    EyeVert *myvc = vcache + warp * kMeshletVerts;
-    BigTri *mybig = bigq + warp * kBigCap;
-    const uint32_t nreg = p.regions_x * p.regions_y;
-
-    uint32_t item = blockIdx.x;
-    while (item < p.n_items) {
-        const uint32_t vi = item / nreg, ri = item % nreg;
-        const int rx0 = (int)(ri % p.regions_x) * RW, ry0 = (int)(ri / p.regions_x) * RH;
-        const int rx1 = min(rx0 + RW, (int)p.width), ry1 = min(ry0 + RH, (int)p.height);
-        const View &V = p.views[vi];
-        if (threadIdx.x < 12) sM[threadIdx.x] = V.M[threadIdx.x];
-        if (threadIdx.x == 0) {
-            sS = p.scenes[V.scene];
-            s_mcount = 0;
-            s_mnext = 0;
-        }
-        for (int i = threadIdx.x; i < RW * RH; i += kThreads) zbuf[i] = ~0ull;
-        __syncthreads();
-        if (threadIdx.x < 6) sPlanes[threadIdx.x] = region_plane(threadIdx.x, sM, p, rx0, ry0, rx1, ry1);
-        __syncthreads();
-
-        const uint32_t ngroups = sS.n_groups;
-        for (uint32_t g0 = 0; g0 < ngroups; g0 += kGroupChunk) {
-            // K3: bin groups -> meshlets of this chunk to the region
-            for (uint32_t gi = warp; gi < (uint32_t)kGroupChunk && g0 + gi < ngroups; gi += kWarps) {
-                const Group g = sS.groups[g0 + gi];
-                if (!aabb_visible(sPlanes, g.bmin, g.bmax)) continue;
-                const uint32_t m = g.m0 + lane;
-                bool vis = false;
-                if (m < g.m1) {
-                    const Meshlet ml = sS.meshlets[m];
-                    vis = aabb_visible(sPlanes, ml.bmin, ml.bmax);
+    float *vw = s_view[warp];
+    if (lane == 0) s_bign[warp] = 0;
+    __syncwarp();
+    const uint32_t count = min(*p.vis_count, p.vis_cap);
+    const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    WarpCtx c{};
+    uint32_t cur_view = 0xFFFFFFFFu, cur_scene = 0xFFFFFFFFu;
+    for (uint32_t e0 = warp_id * p.chunk; e0 < count; e0 += n_warps * p.chunk) {
+        const uint32_t e1 = min(e0 + p.chunk, count);
+        for (uint32_t e = e0; e < e1; e++) {
+            const uint2 pr = p.vis[e];
+            const uint32_t vi = pr.x;
+            if (vi != cur_view) {
+                cur_view = vi;
+                const View &V = p.views[vi];
+                __syncwarp();
+                if (lane < 12) vw[lane] = V.M[lane];
+                c.zbuf = p.zbuf + (size_t)vi * p.width * p.height;
+                if (V.scene != cur_scene) {
+                    cur_scene = V.scene;
+                    const SceneDev &S = p.scenes[cur_scene];
+                    c.meshlets = S.meshlets;
+                    c.mvert = S.mvert;
+                    c.mtri = S.mtri;
                 }
-                const unsigned mask = __ballot_sync(0xFFFFFFFFu, vis);
-                uint32_t base = 0;
-                if (lane == 0 && mask) base = atomicAdd(&s_mcount, (uint32_t)__popc(mask));
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                if (vis) mlist[base + __popc(mask & ((1u << lane) - 1u))] = m;
+                __syncwarp();
             }
-            __syncthreads();
-            const uint32_t mcount = s_mcount;
-            for (;;) {
-                uint32_t k = 0;
-                if (lane == 0) k = atomicAdd(&s_mnext, 1u);
-                k = __shfl_sync(0xFFFFFFFFu, k, 0);
-                if (k >= mcount) break;
-                process_meshlet(sS, sM, p, mlist[k], myvc, mybig, zbuf, rx0, ry0, rx1, ry1, RW, lane);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                s_mcount = 0;
-                s_mnext = 0;
-            }
-            __syncthreads();
+            process_meshlet(c, vw, p, pr.y, s_vc[warp], s_big[warp], &s_bign[warp], lane);
         }
-
-        // K5: resolve, shade, store
-        const uint32_t frame = V.frame;
-        const size_t fbase = (size_t)frame * p.width * p.height;
-        for (int i = threadIdx.x; i < RW * RH; i += kThreads) {
-            const int lx = i % RW, ly = i / RW;
-            const int px = rx0 + lx, py = ry0 + ly;
-            if (px >= rx1 || py >= ry1) continue;
-            const ShadeOut o = shade_pixel(sS, sM, p, px, py, zbuf[i]);
-            const size_t pi = fbase + (size_t)py * p.width + px;
-            p.rgb[3 * pi + 0] = (uint8_t)(o.rgb & 255u);
-            p.rgb[3 * pi + 1] = (uint8_t)((o.rgb >> 8) & 255u);
-            p.rgb[3 * pi + 2] = (uint8_t)((o.rgb >> 16) & 255u);
-            p.depth[pi] = o.depth;
-            if (p.ids) p.ids[pi] = o.id;
-        }
-        if (!p.work_counter) break;
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = gridDim.x + atomicAdd(p.work_counter, 1u);
-        __syncthreads();
-        item = s_item;
     }
 }
 
+// --------------------------------------------------------------------- shade
+template <int NA>
+__device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
+                                           uint32_t frame)
+{
+    const uint32_t W = p.width, H = p.height;
+    const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
+    const unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
+    const size_t fbase = (size_t)frame * W * H;
+    const bool vec = (W % 4 == 0) && (((uintptr_t)p.rgb & 3) == 0) && (((uintptr_t)p.depth & 15) == 0) &&
+                     (((uintptr_t)p.ids & 15) == 0);
+    ShadeTri<NA> st;
+    for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < quads; qi += gridDim.x * blockDim.x) {
+        const uint32_t y = qi / qpr, x0 = (qi % qpr) * 4;
+        const uint32_t n = min(4u, W - x0);
+        const size_t pi = (size_t)y * W + x0;
+        unsigned long long key[4];
+        if (vec) {
+            const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(zb + pi);
+            const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(zb + pi + 2);
+            key[0] = k01.x; key[1] = k01.y; key[2] = k23.x; key[3] = k23.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
+        }
+        uint32_t rgb[4], id[4];
+        float dep[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k]);
+        const size_t o = fbase + pi;
+        if (vec) {
+            // four packed 24-bit RGB values -> three little-endian words
+            uint32_t *r32 = reinterpret_cast<uint32_t *>(p.rgb + 3 * o);
+            r32[0] = rgb[0] | (rgb[1] << 24);
+            r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
+            r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
+            *reinterpret_cast<float4 *>(p.depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
+            if (p.ids) *reinterpret_cast<uint4 *>(p.ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
+        } else {
+            for (uint32_t k = 0; k < n; k++) {
+                p.rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
+                p.rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
+                p.rgb[3 * (o + k) + 2] = (uint8_t)((rgb[k] >> 16) & 255u);
+                p.depth[o + k] = dep[k];
+                if (p.ids) p.ids[o + k] = id[k];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, uint32_t view0)
+{
+    __shared__ float sM[12];
+    __shared__ SceneDev sS;
+    __shared__ uint32_t s_frame;
+    const uint32_t vi = view0 + blockIdx.y;
+    if (threadIdx.x < 12) sM[threadIdx.x] = p.views[vi].M[threadIdx.x];
+    if (threadIdx.x == 0) {
+        sS = p.scenes[p.views[vi].scene];
+        s_frame = p.views[vi].frame;
+    }
+    __syncthreads();
+    if (sS.color_mode == kColorTexture)
+        shade_rows<2>(p, sS, sM, vi, s_frame);
+    else if (sS.color_mode == kColorVertex)
+        shade_rows<3>(p, sS, sM, vi, s_frame);
+    else
+        shade_rows<0>(p, sS, sM, vi, s_frame);
+}
+
+// --------------------------------------------------------------------- launch
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream)
 {
-    const size_t smem = render_smem_bytes(cfg);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (p.total_items > 0) {
+        const uint32_t cull_blocks = std::min<uint32_t>((p.total_items + 7) / 8, (uint32_t)sms * 8);
+        cull_kernel<<<cull_blocks, 256, 0, stream>>>(p);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, 0, stream>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    uint32_t grid = p.n_items;
-    if (p.work_counter) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const uint32_t cap = (uint32_t)sms * cfg.ctas_per_sm;
-        if (grid > cap) grid = cap;
+    const uint32_t quads = ((p.width + 3) / 4) * p.height;
+    const uint32_t bx = std::min<uint32_t>((quads + kShadeThreads - 1) / kShadeThreads, 1024);
+    for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
+        const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
+        shade_kernel<<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    if (grid == 0) return cudaSuccess;
-    render_kernel<<<grid, kThreads, smem, stream>>>(p);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace hsr
