@@ -128,6 +128,29 @@ HSR_API int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes,
                      const hsr_intrinsics *intr, uint32_t width, uint32_t height,
                      uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
 
+/*
+ * Allocation-free variant of hsr_render (the paper has no counterpart; this is
+ * a library-integration feature). Same arguments, outputs and results as
+ * hsr_render, but no memory is allocated on the call path: its scratch (view
+ * descriptors, z-buffer, visible-meshlet list) is one fixed 32 MiB array in
+ * device memory, present on every GPU that loads the library until the
+ * process exits. For callers that cannot let a library allocate: processes
+ * whose framework already holds the device memory in its own pool, loops that
+ * cannot afford an allocator call, and hosts that route every allocation
+ * through their own allocator.
+ *   - A call needing more than 32 MiB of scratch (about 8 B per output pixel
+ *     per view + 8 B per meshlet per view + 160 B per view) returns
+ *     HSR_ERR_OVERFLOW; split such batches or use hsr_render.
+ *   - All calls share the array and it keeps the last call's contents (each
+ *     call re-initialises what it needs). Calls whose work overlaps on the
+ *     GPU race and corrupt each other's images: order them on one stream.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture on that device.
+ */
+HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose *poses, uint32_t n,
+                       const hsr_intrinsics *intr, uint32_t width, uint32_t height,
+                       uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
+
 /* Static description of a status code. */
 HSR_API const char *hsr_status_string(int status);
 

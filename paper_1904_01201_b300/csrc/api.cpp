@@ -349,6 +349,22 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
 
 }  // namespace
 
+// Host helpers shared with other translation units of the library.
+namespace hsr {
+bool host_camera_matrix(const hsr_pose &pose, float M[12]) { return camera_matrix(pose, M); }
+bool host_intrinsics_ok(const hsr_intrinsics *in) { return intrinsics_ok(in); }
+float host_far_threshold(float zfar) { return far_threshold(zfar); }
+void host_view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32_t H, float planes[24])
+{
+    view_planes(M, in, W, H, planes);
+}
+bool host_snap_in_range(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in)
+{
+    return snap_in_range(s, pose, in);
+}
+const SceneDev &host_scene_dev(const hsr_scene *s) { return s->dev; }
+}  // namespace hsr
+
 extern "C" {
 
 const char *hsr_version(void) { return "0.1.0"; }

@@ -1,0 +1,149 @@
+// hsr_render_noalloc: a variant of hsr_render that performs no memory
+// allocation of any kind on the call path.
+//
+// Some callers cannot let a library allocate: a training process whose
+// framework has already reserved (nearly) all device memory in its own
+// caching pool, where an extra cudaMalloc would fail or fragment that pool;
+// latency-critical loops where an allocator call may block or synchronise the
+// device; and hosts that require every device allocation to go through their
+// own allocator. For them, the scratch this render needs (per-view
+// descriptors, the 64-bit z-buffer and the visible-meshlet list) lives in one
+// fixed array in device memory, created when the library is loaded, rather
+// than in buffers obtained per call.
+//
+// Limits and rules (also stated in include/hsr.h):
+//  * the array holds kNoAllocScratchBytes = 32 MiB; a call needing more
+//    (about 8 bytes per output pixel per view plus 8 bytes per meshlet per
+//    view, plus 160 bytes per view) is rejected with HSR_ERR_OVERFLOW;
+//  * the host-side descriptors are staged in a fixed 1 MiB host buffer
+//    (at most ~6500 views per call);
+//  * every GPU that loads the library keeps the 32 MiB array until the
+//    process exits;
+//  * all calls share the array: two calls whose work overlaps on the GPU
+//    (different streams, or different host threads without ordering) race
+//    and give wrong images. Serialise them on one stream.
+//  * the first call on each device looks up the array's device address with
+//    cudaGetSymbolAddress (with that device current); make that first call
+//    before any stream capture on that device.
+#include <cstring>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hsr.h"
+#include "hsr_internal.h"
+
+namespace hsr {
+
+bool host_camera_matrix(const hsr_pose &pose, float M[12]);
+bool host_intrinsics_ok(const hsr_intrinsics *in);
+float host_far_threshold(float zfar);
+void host_view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32_t H, float planes[24]);
+bool host_snap_in_range(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in);
+const SceneDev &host_scene_dev(const hsr_scene *s);
+
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;
+constexpr size_t kNoAllocHostBytes = 1ull << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+// The fixed device scratch. In host code this name is only a stand-in for the
+// symbol: its device address must come from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev_ptr[kNoAllocMaxDevices] = {};
+alignas(256) unsigned char g_noalloc_host[kNoAllocHostBytes];
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+}  // namespace hsr
+
+using namespace hsr;
+
+extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose *poses, uint32_t n,
+                                          const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb,
+                                          float *depth, uint32_t *ids, void *cuda_stream)
+{
+    if (!scene || !poses || n == 0 || !rgb || !depth) return HSR_ERR_INVALID_ARG;
+    if (width == 0 || height == 0 || width > 4096 || height > 4096) return HSR_ERR_INVALID_ARG;
+    if (!host_intrinsics_ok(intr)) return HSR_ERR_INVALID_ARG;
+    const SceneDev &sd = host_scene_dev(scene);
+
+    // layout of the scratch array: [counters | scene | slot | views | z-buffer | visible list]
+    const size_t off_scene = 256;
+    const size_t off_slots = off_scene + align256(sizeof(SceneDev));
+    const size_t off_views = off_slots + 256;
+    const size_t desc_bytes = off_views + (size_t)n * sizeof(View);
+    const size_t off_z = align256(desc_bytes);
+    const uint64_t zbytes = (uint64_t)n * width * height * sizeof(unsigned long long);
+    const uint64_t list_entries = (uint64_t)n * sd.n_meshlets;
+    const uint64_t items = (uint64_t)n * sd.n_groups;
+    const uint64_t need = (uint64_t)off_z + zbytes + list_entries * sizeof(uint2);
+    if (need > kNoAllocScratchBytes || desc_bytes > kNoAllocHostBytes) return HSR_ERR_OVERFLOW;
+    if (items >= 0xFFFFFFF0ull) return HSR_ERR_OVERFLOW;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HSR_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return HSR_ERR_INVALID_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_dev_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return HSR_ERR_CUDA;
+        g_noalloc_dev_ptr[dev] = ptr;
+    }
+    unsigned char *d = static_cast<unsigned char *>(g_noalloc_dev_ptr[dev]);
+
+    // host descriptors (counters start at zero)
+    unsigned char *h = g_noalloc_host;
+    std::memset(h, 0, off_views);
+    std::memcpy(h + off_scene, &sd, sizeof(SceneDev));
+    uint32_t *slot = reinterpret_cast<uint32_t *>(h + off_slots);
+    slot[0] = 0;                    // slot_item_base[0]
+    slot[1] = (uint32_t)items;      // slot_item_base[1]
+    slot[2] = 0;                    // slot_view_base[0]
+    slot[3] = 0;                    // slot_scene[0]
+    View *hv = reinterpret_cast<View *>(h + off_views);
+    for (uint32_t i = 0; i < n; i++) {
+        View &v = hv[i];
+        std::memset(&v, 0, sizeof(View));
+        if (!host_camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
+        if (!host_snap_in_range(scene, poses[i], *intr)) return HSR_ERR_INVALID_ARG;
+        host_view_planes(v.M, *intr, width, height, v.planes);
+        v.scene = 0;
+        v.frame = i;
+    }
+    // Pageable source: the copy has consumed `h` when this call returns.
+    if (cudaMemcpyAsync(d, h, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HSR_ERR_CUDA;
+    if (cudaMemsetAsync(d + off_z, 0xFF, (size_t)zbytes, stream) != cudaSuccess) return HSR_ERR_CUDA;
+
+    Params p{};
+    p.vis_count = reinterpret_cast<uint32_t *>(d);
+    p.scenes = reinterpret_cast<const SceneDev *>(d + off_scene);
+    const uint32_t *dslot = reinterpret_cast<const uint32_t *>(d + off_slots);
+    p.slot_item_base = dslot;
+    p.slot_view_base = dslot + 2;
+    p.slot_scene = dslot + 3;
+    p.n_slots = 1;
+    p.views = reinterpret_cast<const View *>(d + off_views);
+    p.zbuf = reinterpret_cast<unsigned long long *>(d + off_z);
+    p.vis = reinterpret_cast<uint2 *>(d + off_z + zbytes);
+    p.vis_cap = (uint32_t)list_entries;
+    p.rgb = rgb;
+    p.depth = depth;
+    p.ids = ids;
+    p.n_views = n;
+    p.width = width;
+    p.height = height;
+    p.total_items = (uint32_t)items;
+    p.fx = intr->fx; p.fy = intr->fy; p.cx = intr->cx; p.cy = intr->cy;
+    p.znear = intr->znear; p.zfar = intr->zfar;
+    p.q_far = host_far_threshold(intr->zfar);
+    const LaunchCfg cfg{};
+    p.small_px = cfg.small_px;
+    p.chunk = cfg.chunk;
+    return launch_render(p, cfg, stream) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+}

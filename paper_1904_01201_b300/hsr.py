@@ -58,6 +58,7 @@ def _load():
         "hsr_render": ([P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P], ctypes.c_int),
         "hsr_render_batch": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P],
                              ctypes.c_int),
+        "hsr_render_noalloc": ([P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P], ctypes.c_int),
         "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "hsr_version": ([], ctypes.c_char_p),
     }
@@ -147,6 +148,15 @@ def hsr_render(handle, poses, intr, width, height, rgb, depth, ids=None, stream=
     ci = as_intrinsics(intr)
     return _lib.hsr_render(ctypes.c_void_p(handle), _np_ptr(poses), poses.shape[0], ctypes.byref(ci), int(width),
                            int(height), _dev_ptr(rgb), _dev_ptr(depth), _dev_ptr(ids), _stream_ptr(stream))
+
+
+def hsr_render_noalloc(handle, poses, intr, width, height, rgb, depth, ids=None, stream=None) -> int:
+    """Allocation-free variant of hsr_render (fixed device scratch; see include/hsr.h). Returns the status."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    ci = as_intrinsics(intr)
+    return _lib.hsr_render_noalloc(ctypes.c_void_p(handle), _np_ptr(poses), poses.shape[0], ctypes.byref(ci),
+                                   int(width), int(height), _dev_ptr(rgb), _dev_ptr(depth), _dev_ptr(ids),
+                                   _stream_ptr(stream))
 
 
 def hsr_render_batch(handles: Sequence[int], scene_of_agent, poses, intr, width, height, rgb, depth, ids=None,
