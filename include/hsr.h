@@ -129,6 +129,17 @@ HSR_API int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes,
                      uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
 
 /*
+ * Diagnostic stage timing (measurement support, not part of the method).
+ * While enabled, every render call records CUDA events on its stream around
+ * its three stages; hsr_get_stage_timing waits for the last call's events and
+ * writes ms[0] = cull, ms[1] = raster, ms[2] = shade, ms[3] = all three
+ * (milliseconds). It returns HSR_ERR_INVALID_ARG if no call was timed since
+ * timing was enabled. The event set is global: use from one thread at a time.
+ */
+HSR_API int hsr_set_stage_timing(int enable);
+HSR_API int hsr_get_stage_timing(float *ms);
+
+/*
  * Allocation-free variant of hsr_render (the paper has no counterpart; this is
  * a library-integration feature). Same arguments, outputs and results as
  * hsr_render, but no memory is allocated on the call path: its scratch (view

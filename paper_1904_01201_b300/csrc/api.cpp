@@ -619,6 +619,19 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
     return HSR_OK;
 }
 
+int hsr_set_stage_timing(int enable)
+{
+    return stage_timing_enable(enable != 0) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+}
+
+int hsr_get_stage_timing(float *ms)
+{
+    if (!ms) return HSR_ERR_INVALID_ARG;
+    const cudaError_t e = stage_timing_read(ms);
+    if (e == cudaErrorNotReady) return HSR_ERR_INVALID_ARG;
+    return e == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+}
+
 int hsr_scene_free(hsr_scene *scene)
 {
     free_scene(scene);

@@ -93,4 +93,8 @@ struct LaunchCfg {
 // Launches the cull, raster and shade kernels on `stream`.
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream);
 
+// Stage timing (diagnostic): events around cull / raster / shade.
+cudaError_t stage_timing_enable(bool on);
+cudaError_t stage_timing_read(float ms[4]);
+
 }  // namespace hsr

@@ -291,6 +291,57 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
         shade_rows<0>(p, sS, sM, vi, s_frame);
 }
 
+// --------------------------------------------------------------------- stage timing
+// Diagnostic: CUDA events recorded around each stage of every launch while
+// enabled (one set of events per process; meant for single-threaded use).
+namespace {
+bool g_timing = false;
+int g_timing_dev = -1;
+cudaEvent_t g_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+bool g_ev_recorded = false;
+}  // namespace
+
+cudaError_t stage_timing_enable(bool on)
+{
+    if (on) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (g_timing_dev != dev) {
+            for (auto &ev : g_ev)
+                if (ev) {
+                    cudaEventDestroy(ev);
+                    ev = nullptr;
+                }
+            for (auto &ev : g_ev) {
+                e = cudaEventCreate(&ev);
+                if (e != cudaSuccess) return e;
+            }
+            g_timing_dev = dev;
+        }
+    }
+    g_timing = on;
+    g_ev_recorded = false;
+    return cudaSuccess;
+}
+
+cudaError_t stage_timing_read(float ms[4])
+{
+    if (!g_ev_recorded) return cudaErrorNotReady;
+    cudaError_t e = cudaEventSynchronize(g_ev[3]);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < 3; k++) {
+        e = cudaEventElapsedTime(&ms[k], g_ev[k], g_ev[k + 1]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaEventElapsedTime(&ms[3], g_ev[0], g_ev[3]);
+}
+
+static inline void mark(int k, cudaStream_t stream)
+{
+    if (g_timing) cudaEventRecord(g_ev[k], stream);
+}
+
 // --------------------------------------------------------------------- launch
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream)
 {
@@ -298,15 +349,20 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    mark(0, stream);
     if (p.total_items > 0) {
         const uint32_t cull_blocks = std::min<uint32_t>((p.total_items + 7) / 8, (uint32_t)sms * 8);
         cull_kernel<<<cull_blocks, 256, 0, stream>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        mark(1, stream);
         raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, 0, stream>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+    } else {
+        mark(1, stream);
     }
+    mark(2, stream);
     const uint32_t quads = ((p.width + 3) / 4) * p.height;
     const uint32_t bx = std::min<uint32_t>((quads + kShadeThreads - 1) / kShadeThreads, 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
@@ -315,6 +371,8 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    mark(3, stream);
+    if (g_timing) g_ev_recorded = true;
     return cudaSuccess;
 }
 

@@ -59,6 +59,8 @@ def _load():
         "hsr_render_batch": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P],
                              ctypes.c_int),
         "hsr_render_noalloc": ([P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P], ctypes.c_int),
+        "hsr_set_stage_timing": ([ctypes.c_int], ctypes.c_int),
+        "hsr_get_stage_timing": ([P], ctypes.c_int),
         "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "hsr_version": ([], ctypes.c_char_p),
     }
@@ -79,6 +81,21 @@ def library():
 # -------------------------------------------------------------- raw C-ABI names
 def hsr_status_string(status: int) -> str:
     return _lib.hsr_status_string(int(status)).decode()
+
+
+def hsr_set_stage_timing(enable: bool) -> None:
+    st = _lib.hsr_set_stage_timing(1 if enable else 0)
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_set_stage_timing")
+
+
+def hsr_get_stage_timing():
+    """Stage durations (ms) of the last timed render call: cull, raster, shade, total."""
+    ms = np.zeros(4, dtype=np.float32)
+    st = _lib.hsr_get_stage_timing(_np_ptr(ms))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_get_stage_timing")
+    return {"cull": float(ms[0]), "raster": float(ms[1]), "shade": float(ms[2]), "total": float(ms[3])}
 
 
 def hsr_version() -> str:
