@@ -337,8 +337,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     p.fx = intr->fx; p.fy = intr->fy; p.cx = intr->cx; p.cy = intr->cy;
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = far_threshold(intr->zfar);
-    p.small_px = cfg.small_px;
-    p.chunk = cfg.chunk;
+    p.small_px = std::min<uint32_t>(cfg.small_px, 32);
+    p.chunk = std::max<uint32_t>(cfg.chunk, 1);
     e = launch_render(p, cfg, stream);
     cudaError_t e1 = cudaFreeAsync(zbuf, stream);
     cudaError_t e2 = cudaFreeAsync(dbuf, stream);

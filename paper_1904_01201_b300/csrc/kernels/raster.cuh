@@ -11,7 +11,7 @@
 // merged with one 64-bit atomic minimum (a fire-and-forget reduction in L2).
 //
 // Two paths:
-//  * small triangles (<= small_px candidate pixels, bounding box under 2^15
+//  * small triangles (<= small_px <= 32 candidate pixels, bounding box under 2^15
 //    sub-pixels per axis so every edge value fits in int32): one thread walks
 //    its own triangle's pixels;
 //  * other triangles are queued per warp in shared memory and rasterised by
@@ -39,11 +39,13 @@ __device__ __forceinline__ void zmin(unsigned long long *z, unsigned long long k
     atomicMin(z, key);
 }
 
-// One thread, one small triangle. Exactness: |X_j - X_i| and |P - X_i| are
-// below 2^15 inside the bounding box, so every product is below 2^30 and
-// every edge value below 2^31.
-__device__ __forceinline__ void raster_small(const Tri2D &t, float pa, float pb, uint32_t id, int x0, int x1,
-                                             int y0, int y1, float q_far, unsigned long long *zbuf, int W)
+// One thread, one small triangle (at most 32 candidate pixels). Coverage is
+// found first; the depth plane (two divisions) is only built when at least
+// one sample is covered. Exactness: |X_j - X_i| and |P - X_i| are below 2^15
+// inside the bounding box, so every product is below 2^30 and every edge
+// value below 2^31.
+__device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0, int x1, int y0, int y1,
+                                             float q_far, unsigned long long *zbuf, int W)
 {
     const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
     const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
@@ -51,18 +53,30 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, float pa, float pb,
     const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
     const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
     const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
+    const int w = x1 - x0 + 1;
+    uint32_t mask = 0;
+    int k = 0;
     for (int py = y0; py <= y1; ++py) {
         const int Py = 256 * py + 128;
-        for (int px = x0; px <= x1; ++px) {
+        for (int px = x0; px <= x1; ++px, ++k) {
             const int Px = 256 * px + 128;
             const int e0 = dx0 * (Py - t.Y1) - dy0 * (Px - t.X1);
             const int e1 = dx1 * (Py - t.Y2) - dy1 * (Px - t.X2);
             const int e2 = dx2 * (Py - t.Y0) - dy2 * (Px - t.X0);
-            if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
-            const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
-            if (!(q >= q_far)) continue;
-            zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
+            if (((e0 - b0) | (e1 - b1) | (e2 - b2)) >= 0) mask |= 1u << k;
         }
+    }
+    if (!mask) return;
+    float pa, pb;
+    depth_plane(t, pa, pb);
+    while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int px = x0 + b % w, py = y0 + b / w;
+        const int Px = 256 * px + 128, Py = 256 * py + 128;
+        const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
+        if (!(q >= q_far)) continue;
+        zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
     }
 }
 

@@ -11,11 +11,17 @@
 
 namespace hsr {
 
-// Per meshlet vertex, cached in shared memory for the warp that owns the meshlet.
-struct alignas(16) EyeVert {
-    float xe, ye, d, q;      // q valid when d >= near
-    int X, Y;                // snapped screen position, valid when d >= near
-    uint32_t gid;            // caller vertex index (near-clip edge ordering)
+// Per meshlet vertex, cached in shared memory for the warp that owns the
+// meshlet, split so that the common path reads one 16-byte record:
+//   hot  — snapped X, Y and q (valid when d >= near), and d;
+//   cold — eye-space x, y and the caller vertex index (near-clip path only).
+struct alignas(16) EyeHot {
+    int X, Y;
+    float q, d;
+};
+struct alignas(16) EyeCold {
+    float xe, ye;
+    uint32_t gid;
     uint32_t pad_;
 };
 

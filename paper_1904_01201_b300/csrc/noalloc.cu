@@ -143,7 +143,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = host_far_threshold(intr->zfar);
     const LaunchCfg cfg{};
-    p.small_px = cfg.small_px;
-    p.chunk = cfg.chunk;
+    p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
+    p.chunk = cfg.chunk > 0 ? cfg.chunk : 1;
     return launch_render(p, cfg, stream) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
 }

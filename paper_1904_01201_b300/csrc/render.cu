@@ -104,13 +104,13 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     x1 = min(x1, (int)p.width - 1);
     y1 = min(y1, (int)p.height - 1);
     if (x0 > x1 || y0 > y1) return;            // no sample on screen
-    float pa, pb;
-    depth_plane(t, pa, pb);
     const int npx = (x1 - x0 + 1) * (y1 - y0 + 1);
     if (spanx < 32768 && spany < 32768 && npx <= (int)p.small_px) {
-        raster_small(t, pa, pb, id, x0, x1, y0, y1, p.q_far, zbuf, (int)p.width);
+        raster_small(t, id, x0, x1, y0, y1, p.q_far, zbuf, (int)p.width);
         return;
     }
+    float pa, pb;
+    depth_plane(t, pa, pb);
     const uint32_t slot = atomicAdd(bign, 1u);
     BigTri r;
     r.X0 = t.X0; r.Y0 = t.Y0; r.X1 = t.X1; r.Y1 = t.Y1; r.X2 = t.X2; r.Y2 = t.Y2;
@@ -121,7 +121,7 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
 }
 
 __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M, const Params &p, uint32_t m,
-                                                EyeVert *vc, BigTri *bigq, uint32_t *bign, int lane)
+                                                EyeHot *vh, EyeCold *vcold, BigTri *bigq, uint32_t *bign, int lane)
 {
     const Meshlet ml = c.meshlets[m];
     const uint32_t vend = c.meshlets[m + 1].vbase, tend = c.meshlets[m + 1].tbase;
@@ -131,23 +131,27 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
     // K1: transform + snap this meshlet's vertices
     for (int v = lane; v < nv; v += 32) {
         const float4 P = __ldg(c.mvert + ml.vbase + v);
-        EyeVert e;
-        eye_transform(M, P.x, P.y, P.z, e.xe, e.ye, e.d);
-        e.gid = __float_as_uint(P.w);
-        if (e.d >= zn) {
-            project_snap(e.xe, e.ye, e.d, p.fx, p.fy, p.cx, p.cy, e.q, e.X, e.Y);
+        EyeHot h;
+        EyeCold cd;
+        eye_transform(M, P.x, P.y, P.z, cd.xe, cd.ye, h.d);
+        cd.gid = __float_as_uint(P.w);
+        cd.pad_ = 0;
+        if (h.d >= zn) {
+            project_snap(cd.xe, cd.ye, h.d, p.fx, p.fy, p.cx, p.cy, h.q, h.X, h.Y);
         } else {
-            e.q = 0.f;
-            e.X = e.Y = 0;
+            h.q = 0.f;
+            h.X = h.Y = 0;
         }
-        vc[v] = e;
+        vh[v] = h;
+        vcold[v] = cd;
     }
     __syncwarp();
 
     // K2 + K4: one triangle per lane
     if (lane < nt) {
         const uint2 mt = __ldg(c.mtri + ml.tbase + lane);
-        const EyeVert a = vc[mt.x & 255u], b = vc[(mt.x >> 8) & 255u], cc = vc[(mt.x >> 16) & 255u];
+        const uint32_t ia = mt.x & 255u, ib = (mt.x >> 8) & 255u, ic = (mt.x >> 16) & 255u;
+        const EyeHot a = vh[ia], b = vh[ib], cc = vh[ic];
         const uint32_t id = mt.y;
         const bool all_near = a.d < zn && b.d < zn && cc.d < zn;
         const bool all_far = a.d > zf && b.d > zf && cc.d > zf;
@@ -156,10 +160,11 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
             if (a.d >= zn && b.d >= zn && cc.d >= zn) {
                 if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, cc.X, cc.Y, cc.q, t)) emit_tri(t, id, p, c.zbuf, bigq, bign);
             } else {
+                const EyeCold ca = vcold[ia], cb = vcold[ib], ccc = vcold[ic];
                 CVert<0> v[3];
-                v[0].xe = a.xe; v[0].ye = a.ye; v[0].d = a.d; v[0].gid = a.gid;
-                v[1].xe = b.xe; v[1].ye = b.ye; v[1].d = b.d; v[1].gid = b.gid;
-                v[2].xe = cc.xe; v[2].ye = cc.ye; v[2].d = cc.d; v[2].gid = cc.gid;
+                v[0].xe = ca.xe; v[0].ye = ca.ye; v[0].d = a.d; v[0].gid = ca.gid;
+                v[1].xe = cb.xe; v[1].ye = cb.ye; v[1].d = b.d; v[1].gid = cb.gid;
+                v[2].xe = ccc.xe; v[2].ye = ccc.ye; v[2].d = cc.d; v[2].gid = ccc.gid;
                 CVert<0> poly[4];
                 const int np = clip_near<0>(v, zn, poly);
                 int X[4], Y[4];
@@ -182,7 +187,8 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
 
 __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p)
 {
-    __shared__ EyeVert s_vc[kRasterWarps][kMeshletVerts];
+    __shared__ EyeHot s_vh[kRasterWarps][kMeshletVerts];
+    __shared__ EyeCold s_vcold[kRasterWarps][kMeshletVerts];
     __shared__ BigTri s_big[kRasterWarps][kBigCap];
     __shared__ float s_view[kRasterWarps][12];
     __shared__ uint32_t s_bign[kRasterWarps];
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
                 }
                 __syncwarp();
             }
-            process_meshlet(c, vw, p, pr.y, s_vc[warp], s_big[warp], &s_bign[warp], lane);
+            process_meshlet(c, vw, p, pr.y, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
         }
     }
 }
