@@ -144,10 +144,16 @@ def load_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def raster_bytes_per_view(scene) -> float:
+    """Algorithmic bytes of the raster stage per view: the mesh read once
+    (a 12-byte index triple per triangle, 12 bytes of xyz per vertex)."""
+    return 12.0 * scene.n_tris + 12.0 * scene.n_verts
+
+
 def recorded_traffic(workload_name: str):
-    """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"render_kernel_{workload_name}.txt")
+    """dram bytes per raster launch from a committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"raster_kernel_{workload_name}.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -299,6 +305,20 @@ def run_gpu(args, wk):
     frames = n * args.steps * world
     value = frames / (ms / 1e3)
 
+    # per-stage device times (CUDA events recorded by the library around each
+    # kernel on this stream), over separate steps after the timed region
+    hsr.hsr_set_stage_timing(True)
+    stage_steps = max(3, min(args.steps, 20))
+    acc = {"cull": 0.0, "raster": 0.0, "shade": 0.0, "total": 0.0}
+    for _ in range(stage_steps):
+        flush.zero_()
+        step_batched() if args.mode == "batched" else step_plain()
+        t = hsr.hsr_get_stage_timing()
+        for k in acc:
+            acc[k] += t[k]
+    hsr.hsr_set_stage_timing(False)
+    stages = {k: v / stage_steps for k, v in acc.items()}
+
     # plain one-agent-per-launch path on the same views, for comparison
     plain = None
     if args.mode == "batched" and not args.no_plain:
@@ -331,9 +351,14 @@ def run_gpu(args, wk):
         return None
     peak, peak_kind = load_peaks()
     bview = sum(algorithmic_bytes_per_view(wk["scenes"][int(s)], W, H, wk["ids"]) for s in soa) / n
+    views_per_launch = n * args.steps / launches
     kernel_ms_per_launch = local_ms / launches
-    bytes_per_launch = bview * n * args.steps / launches
-    achieved = bytes_per_launch / (kernel_ms_per_launch / 1e3) / 1e9
+    path_achieved = bview * views_per_launch / (kernel_ms_per_launch / 1e3) / 1e9
+    # dominant kernel: the raster stage (one launch per render call; in plain
+    # mode the stage timing covers the last single-view call)
+    rview = sum(raster_bytes_per_view(wk["scenes"][int(s)]) for s in soa) / n
+    raster_views = n if args.mode == "batched" else 1
+    raster_achieved = rview * raster_views / (stages["raster"] / 1e3) / 1e9
     traffic = recorded_traffic(wk["name"]) if args.mode == "batched" else None
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -343,13 +368,19 @@ def run_gpu(args, wk):
                    "agents": n, "width": W, "height": H, "outputs": "rgb+depth" + ("+ids" if wk["ids"] else ""),
                    "mode": args.mode, "l2": "flushed before every step (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_view": bview, "views_per_launch": n * args.steps / launches,
-                     "kernel": "hsr render call (cull + raster + shade kernels)",
-                     "kernel_ms_per_launch": kernel_ms_per_launch},
+        "roofline": {"bound": "hbm", "achieved": raster_achieved, "peak": peak, "unit": "GB/s",
+                     "frac": raster_achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "hsr::raster_kernel", "kernel_ms_per_launch": stages["raster"],
+                     "algorithmic_bytes_per_view": rview, "views_per_launch": raster_views},
+        "roofline_path": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
+                          "frac": path_achieved / peak, "peak_kind": peak_kind,
+                          "what": "whole render call (cull + raster + shade) per step",
+                          "algorithmic_bytes_per_view": bview, "views_per_launch": views_per_launch,
+                          "ms_per_launch": kernel_ms_per_launch},
+        "stages_ms": stages,
         "e2e": e2e,
-        "gpu_launches": launches,
+        "gpu_launches": 3 * launches,          # cull + raster + shade per render call
+        "render_calls": launches,
         "clocks": clocks,
         "kernel_sha": kernel_source_hash(),
     }
