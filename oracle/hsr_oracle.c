@@ -32,7 +32,8 @@
  *              inside iff E_k > 0, or E_k == 0 and edge k is top or left
  *              (edge i->j is top iff dy == 0 and dx > 0, left iff dy < 0).
  *   depth    : plane of q over the snapped vertices, relative to vertex 0,
- *              fp32 op order below; fragment kept iff q > 0 and 1/q <= far.
+ *              fp32 op order below, clamped to [min q_i, max q_i] of the
+ *              (sub-)triangle's vertices; fragment kept iff 1/q <= far.
  *   key      : ((~bits(q)) << 32) | triangle index; per-pixel minimum.
  *   shade    : perspective-correct weights E_k * q_k (fp64), bilinear
  *              clamp-to-edge texture lookup at (u*Wt - 0.5, v*Ht - 0.5), or
@@ -250,6 +251,7 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
             const int32_t X0 = X[i0], Y0 = Y[i0], X1 = X[i1], Y1 = Y[i1], X2 = X[i2], Y2 = Y[i2];
             const float q0 = q[i0], q1 = q[i1], q2 = q[i2];
             /* plane of q, relative to vertex 0 */
+            const float qlo = fminf(q0, fminf(q1, q2)), qhi = fmaxf(q0, fmaxf(q1, q2));
             const float fA = (float)A;
             const float dq1 = q1 - q0, dq2 = q2 - q0;
             const float pa = fmaf(dq1, (float)(Y2 - Y0), -(dq2 * (float)(Y1 - Y0))) / fA;
@@ -292,7 +294,10 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
                     if (!in) continue;
                     const size_t pix = (size_t)py * W + (size_t)px;
                     if (cov) cov[pix]++;
-                    const float qq = fmaf(pa, (float)(Px - X0), fmaf(pb, (float)(Py - Y0), q0));
+                    float qq = fmaf(pa, (float)(Px - X0), fmaf(pb, (float)(Py - Y0), q0));
+                    /* interior points lie between the vertices' depths: clamp the
+                       rounded plane value to the vertices' range of q */
+                    qq = fminf(fmaxf(qq, qlo), qhi);
                     if (!(qq > 0.0f)) continue;
                     const float dd = 1.0f / qq;
                     if (dd > zf) continue;

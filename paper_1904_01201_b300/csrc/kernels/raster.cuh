@@ -21,10 +21,10 @@
 
 namespace hsr {
 
-// A queued triangle for the warp-cooperative path (48 bytes).
+// A queued triangle for the warp-cooperative path (64 bytes).
 struct alignas(16) BigTri {
     int X0, Y0, X1, Y1, X2, Y2;
-    float pa, pb, q0;
+    float pa, pb, q0, qlo, qhi;
     uint32_t id;
     unsigned short x0, y0, x1, y1;      // candidate pixel range, clipped to the image
 };
@@ -69,12 +69,13 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0
     if (!mask) return;
     float pa, pb;
     depth_plane(t, pa, pb);
+    const float qlo = tri_qlo(t), qhi = tri_qhi(t);
     while (mask) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
         const int px = x0 + b % w, py = y0 + b / w;
         const int Px = 256 * px + 128, Py = 256 * py + 128;
-        const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
+        const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0, qlo, qhi);
         if (!(q >= q_far)) continue;
         zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
     }
@@ -99,7 +100,7 @@ __device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float
             const long long e1 = (long long)dx1 * (Py - t.Y2) - (long long)dy1 * (Px - t.X2);
             const long long e2 = (long long)dx2 * (Py - t.Y0) - (long long)dy2 * (Px - t.X0);
             if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
-            const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0);
+            const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0, t.qlo, t.qhi);
             if (!(q >= q_far)) continue;
             zmin(zbuf + (size_t)py * W + px, depth_key(q, t.id));
         }

@@ -9,7 +9,8 @@
 //    fan triangulation from the first emitted vertex;
 //  * A = (X1-X0)(Y2-Y0) - (Y1-Y0)(X2-X0) in int64; keep A < 0 (front faces are
 //    counter-clockwise in the world; screen y points down), then swap 1 and 2;
-//  * depth plane of q = 1/d relative to vertex 0 (fixed fp32 op order);
+//  * depth plane of q = 1/d relative to vertex 0 (fixed fp32 op order),
+//    clamped to the vertices' range of q;
 //  * candidate pixels: centres (256x+128, 256y+128) inside the bounding box.
 #pragma once
 #include "transform.cuh"
@@ -90,11 +91,17 @@ __device__ __forceinline__ void depth_plane(const Tri2D &t, float &pa, float &pb
     pb = __fdiv_rn(__fmaf_rn(dq2, __int2float_rn(t.X1 - t.X0), -__fmul_rn(dq1, __int2float_rn(t.X2 - t.X0))), fA);
 }
 
-// q at a sample, from its offset (exact integers) to vertex 0.
-__device__ __forceinline__ float plane_q(float pa, float pb, float q0, int dx, int dy)
+// q at a sample, from its offset (exact integers) to vertex 0, clamped to the
+// range [qlo, qhi] of the triangle's vertex values (interior points lie
+// between the vertices' depths; the clamp keeps that true under rounding).
+__device__ __forceinline__ float plane_q(float pa, float pb, float q0, int dx, int dy, float qlo, float qhi)
 {
-    return __fmaf_rn(pa, __int2float_rn(dx), __fmaf_rn(pb, __int2float_rn(dy), q0));
+    const float q = __fmaf_rn(pa, __int2float_rn(dx), __fmaf_rn(pb, __int2float_rn(dy), q0));
+    return fminf(fmaxf(q, qlo), qhi);
 }
+
+__device__ __forceinline__ float tri_qlo(const Tri2D &t) { return fminf(t.q0, fminf(t.q1, t.q2)); }
+__device__ __forceinline__ float tri_qhi(const Tri2D &t) { return fmaxf(t.q0, fmaxf(t.q1, t.q2)); }
 
 // Top-left bias of edge i->j: 0 if the edge is top (dy == 0, dx > 0) or left
 // (dy < 0), else 1 (a sample exactly on it is outside).

@@ -148,7 +148,7 @@ __device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M,
         if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
         float pa, pb;
         depth_plane(t, pa, pb);
-        const float qq = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0);
+        const float qq = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0, tri_qlo(t), tri_qhi(t));
         if (__float_as_uint(qq) != __float_as_uint(qk)) continue;
         // oriented order is (poly 0, poly f+2, poly f+1)
         interp<NA>(t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a, attr);

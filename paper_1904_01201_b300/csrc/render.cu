@@ -114,7 +114,7 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     const uint32_t slot = atomicAdd(bign, 1u);
     BigTri r;
     r.X0 = t.X0; r.Y0 = t.Y0; r.X1 = t.X1; r.Y1 = t.Y1; r.X2 = t.X2; r.Y2 = t.Y2;
-    r.pa = pa; r.pb = pb; r.q0 = t.q0; r.id = id;
+    r.pa = pa; r.pb = pb; r.q0 = t.q0; r.qlo = tri_qlo(t); r.qhi = tri_qhi(t); r.id = id;
     r.x0 = (unsigned short)x0; r.x1 = (unsigned short)x1;
     r.y0 = (unsigned short)y0; r.y1 = (unsigned short)y1;
     bigq[slot] = r;
@@ -187,9 +187,12 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
 
 __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p)
 {
-    __shared__ EyeHot s_vh[kRasterWarps][kMeshletVerts];
-    __shared__ EyeCold s_vcold[kRasterWarps][kMeshletVerts];
-    __shared__ BigTri s_big[kRasterWarps][kBigCap];
+    // dynamic shared memory: per warp a hot and a cold vertex cache and a
+    // big-triangle queue (raster_smem_bytes)
+    extern __shared__ __align__(16) unsigned char smem[];
+    EyeHot(*s_vh)[kMeshletVerts] = reinterpret_cast<EyeHot(*)[kMeshletVerts]>(smem);
+    EyeCold(*s_vcold)[kMeshletVerts] = reinterpret_cast<EyeCold(*)[kMeshletVerts]>(s_vh + kRasterWarps);
+    BigTri(*s_big)[kBigCap] = reinterpret_cast<BigTri(*)[kBigCap]>(s_vcold + kRasterWarps);
     __shared__ float s_view[kRasterWarps][12];
     __shared__ uint32_t s_bign[kRasterWarps];
 
@@ -362,7 +365,15 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         mark(1, stream);
-        raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, 0, stream>>>(p);
+        constexpr size_t smem = kRasterWarps * kMeshletVerts * (sizeof(EyeHot) + sizeof(EyeCold)) +
+                                kRasterWarps * kBigCap * sizeof(BigTri);
+        static int attr_dev = -1;
+        if (attr_dev != dev) {
+            e = cudaFuncSetAttribute(raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_dev = dev;
+        }
+        raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, smem, stream>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     } else {

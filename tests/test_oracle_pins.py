@@ -466,3 +466,29 @@ def test_equal_depth_ties_go_to_lower_index(oracle_mod):
     assert hit.sum() > 20
     assert np.all(out["ids"][0][hit] == 0)
     assert np.all(out["cover"][0][hit] == 3)
+
+
+def test_depth_within_winning_triangle_vertex_range(oracle_mod):
+    # Every point of a triangle lies between its vertices' depths; long thin
+    # slivers with strong depth variation are where rounding of the plane
+    # evaluation would otherwise step outside that range.
+    rng = np.random.default_rng(1)
+    W, H = 512, 320
+    intr = Intrinsics(256.0, 256.0, 256.0, 160.0, 0.05, 100.0)
+    violations = 0
+    for trial in range(12):
+        tris = []
+        for _ in range(200):
+            a = rng.uniform([-3, -2, -1.0], [3, 2, -0.3])
+            b = rng.uniform([-3, -2, -60.0], [3, 2, -20.0])
+            c = a + (b - a) * rng.uniform(0.2, 0.8) + rng.normal(scale=1e-4, size=3)
+            tris.append(np.array([a, b, c]))
+        sc = scene_from_tris(tris)
+        o = oracle_mod.render(sc, identity_pose()[None], intr, W, H)
+        ids, dep = o["ids"][0], o["depth"][0]
+        hit = ids != BG
+        d = -sc.xyz[sc.idx.astype(np.int64)][:, :, 2].astype(np.float64)     # vertex depths (identity camera)
+        lo, hi = d.min(1)[ids[hit]], d.max(1)[ids[hit]]
+        dd = dep[hit].astype(np.float64)
+        violations += int(((dd < lo * (1 - 1e-6)) | (dd > hi * (1 + 1e-6))).sum())
+    assert violations == 0
