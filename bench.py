@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "RGB-D frames/sec (batched vs plain)"
+# kernels per render call: cull, 3 raster phases, 2 hierarchical-z builds, shade
+KERNELS_PER_CALL = 7
 UNIT = "frames/s"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6400.0
@@ -379,7 +381,7 @@ def run_gpu(args, wk):
                           "ms_per_launch": kernel_ms_per_launch},
         "stages_ms": stages,
         "e2e": e2e,
-        "gpu_launches": 3 * launches,          # cull + raster + shade per render call
+        "gpu_launches": KERNELS_PER_CALL * launches,
         "render_calls": launches,
         "clocks": clocks,
         "kernel_sha": kernel_source_hash(),

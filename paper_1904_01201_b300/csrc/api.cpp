@@ -218,7 +218,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         if (s >= n_scenes) return HSR_ERR_INVALID_ARG;
         list_entries += scenes[s]->dev.n_meshlets;
     }
-    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 8ull;
+    const uint64_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
+    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 8ull + (uint64_t)n * hiz_w * hiz_h * 4ull;
     if (scratch > kMaxScratchBytes && n > 1) {
         const uint32_t h = n / 2;
         const size_t px = (size_t)width * height;
@@ -289,6 +290,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
         if (!snap_in_range(scenes[sidx], poses[i], *intr)) return HSR_ERR_INVALID_ARG;
         view_planes(v.M, *intr, width, height, v.planes);
+        for (int k = 0; k < 3; k++) v.pos[k] = poses[i].pos[k];
         v.scene = sidx;
         v.frame = i;
     }
@@ -296,10 +298,11 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     LaunchCfg cfg = cfg_in ? *cfg_in : LaunchCfg{};
     const size_t zbytes = (size_t)n * width * height * sizeof(unsigned long long);
     const size_t lbytes = (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2);
+    const size_t hbytes = (size_t)n * hiz_w * hiz_h * sizeof(uint32_t);
     void *dbuf = nullptr, *zbuf = nullptr;
     cudaError_t e = cudaMallocAsync(&dbuf, total, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMallocAsync(&zbuf, zbytes + lbytes, stream);
+    e = cudaMallocAsync(&zbuf, zbytes + lbytes + hbytes, stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(dbuf, stream);
         return cuda_status(e);
@@ -339,6 +342,12 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     p.q_far = far_threshold(intr->zfar);
     p.small_px = std::min<uint32_t>(cfg.small_px, 32);
     p.chunk = std::max<uint32_t>(cfg.chunk, 1);
+    p.hiz = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes);
+    p.hiz_w = (uint32_t)hiz_w;
+    p.hiz_h = (uint32_t)hiz_h;
+    p.n_phases = std::min<uint32_t>(std::max<uint32_t>(cfg.n_phases, 1u), 3u);
+    p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
+    p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
     e = launch_render(p, cfg, stream);
     cudaError_t e1 = cudaFreeAsync(zbuf, stream);
     cudaError_t e2 = cudaFreeAsync(dbuf, stream);
@@ -519,6 +528,7 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         }
         flush();
         const uint32_t n_meshlets = (uint32_t)meshlets.size();
+        if (n_meshlets > kMeshletMask) throw std::bad_alloc();   // visible-list entries hold 28-bit meshlet ids
         Meshlet sentinel{};
         sentinel.vbase = (uint32_t)mvert.size();
         sentinel.tbase = (uint32_t)mtri.size();

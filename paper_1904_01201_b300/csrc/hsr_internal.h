@@ -53,9 +53,10 @@ struct SceneDev {
 struct alignas(16) View {
     float M[12];
     float planes[24];
+    float pos[3];              // camera position (distance bands of the occlusion phases)
     uint32_t scene;
     uint32_t frame;
-    uint32_t pad_[2];
+    uint32_t pad_[3];
 };
 
 struct Params {
@@ -65,7 +66,7 @@ struct Params {
     uint8_t *rgb;
     float *depth;
     uint32_t *ids;             // may be null
-    uint2 *vis;                // visible (view, meshlet) pairs written by the cull kernel
+    uint2 *vis;                // visible (view, meshlet | phase << 28) pairs written by the cull kernel
     uint32_t *vis_count;       // number of pairs in `vis` (preset to 0)
     uint32_t vis_cap;          // capacity of `vis`
     // Views are sorted by scene; slot k covers views [slot_view_base[k], ...)
@@ -81,13 +82,26 @@ struct Params {
     float q_far;               // smallest float q with 1/q <= zfar
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels
     uint32_t chunk;            // consecutive visible pairs a raster warp takes per step
+    // occlusion phases: a visible meshlet at distance r from the camera goes
+    // to phase (r > phase_r[0]) + (r > phase_r[1]), limited to n_phases - 1;
+    // phases after the first skip meshlets the hierarchical z-buffer proves hidden
+    uint32_t n_phases;         // 1 (no occlusion culling) .. 3
+    float phase_r2[2];         // squared band radii, metres^2
+    uint32_t *hiz;             // [n_views][hiz_h][hiz_w]: max key >> 32 over each 8x8 tile
+    uint32_t hiz_w, hiz_h;
 };
+
+constexpr int kHizTile = 8;
+constexpr uint32_t kPhaseShift = 28;
+constexpr uint32_t kMeshletMask = (1u << kPhaseShift) - 1u;
 
 // Launch configuration chosen by the host (autotuned).
 struct LaunchCfg {
     uint32_t small_px = 16;
     uint32_t chunk = 4;
     uint32_t raster_ctas_per_sm = 3;
+    uint32_t n_phases = 3;
+    float phase_r[2] = {3.0f, 7.0f};
 };
 
 // Launches the cull, raster and shade kernels on `stream`.

@@ -7,14 +7,15 @@
 // latency-critical loops where an allocator call may block or synchronise the
 // device; and hosts that require every device allocation to go through their
 // own allocator. For them, the scratch this render needs (per-view
-// descriptors, the 64-bit z-buffer and the visible-meshlet list) lives in one
+// descriptors, the 64-bit z-buffer, the visible-meshlet list and the
+// per-tile occlusion buffer) lives in one
 // fixed array in device memory, created when the library is loaded, rather
 // than in buffers obtained per call.
 //
 // Limits and rules (also stated in include/hsr.h):
 //  * the array holds kNoAllocScratchBytes = 32 MiB; a call needing more
 //    (about 8 bytes per output pixel per view plus 8 bytes per meshlet per
-//    view, plus 160 bytes per view) is rejected with HSR_ERR_OVERFLOW;
+//    view, plus 176 bytes per view) is rejected with HSR_ERR_OVERFLOW;
 //  * the host-side descriptors are staged in a fixed 1 MiB host buffer
 //    (at most ~6500 views per call);
 //  * every GPU that loads the library keeps the 32 MiB array until the
@@ -71,7 +72,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     if (!host_intrinsics_ok(intr)) return HSR_ERR_INVALID_ARG;
     const SceneDev &sd = host_scene_dev(scene);
 
-    // layout of the scratch array: [counters | scene | slot | views | z-buffer | visible list]
+    // layout of the scratch array: [counters | scene | slot | views | z-buffer | visible list | tile z]
     const size_t off_scene = 256;
     const size_t off_slots = off_scene + align256(sizeof(SceneDev));
     const size_t off_views = off_slots + 256;
@@ -80,7 +81,9 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     const uint64_t zbytes = (uint64_t)n * width * height * sizeof(unsigned long long);
     const uint64_t list_entries = (uint64_t)n * sd.n_meshlets;
     const uint64_t items = (uint64_t)n * sd.n_groups;
-    const uint64_t need = (uint64_t)off_z + zbytes + list_entries * sizeof(uint2);
+    const uint32_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
+    const uint64_t hbytes = (uint64_t)n * hiz_w * hiz_h * sizeof(uint32_t);
+    const uint64_t need = (uint64_t)off_z + zbytes + list_entries * sizeof(uint2) + hbytes;
     if (need > kNoAllocScratchBytes || desc_bytes > kNoAllocHostBytes) return HSR_ERR_OVERFLOW;
     if (items >= 0xFFFFFFF0ull) return HSR_ERR_OVERFLOW;
 
@@ -113,6 +116,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
         if (!host_camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
         if (!host_snap_in_range(scene, poses[i], *intr)) return HSR_ERR_INVALID_ARG;
         host_view_planes(v.M, *intr, width, height, v.planes);
+        for (int k = 0; k < 3; k++) v.pos[k] = poses[i].pos[k];
         v.scene = 0;
         v.frame = i;
     }
@@ -145,5 +149,11 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     const LaunchCfg cfg{};
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? cfg.chunk : 1;
+    p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + list_entries * sizeof(uint2));
+    p.hiz_w = hiz_w;
+    p.hiz_h = hiz_h;
+    p.n_phases = cfg.n_phases;
+    p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
+    p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
     return launch_render(p, cfg, stream) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
 }

@@ -3,13 +3,16 @@
 // cull_kernel (K3): one warp per (view, meshlet group) work item; the group
 //   and then its meshlets are tested against the view frustum and the visible
 //   (view, meshlet) pairs are appended to a compact list (bin.cuh).
-// raster_kernel: warps take equal shares of the visible pairs (grid-stride,
-//   `chunk` consecutive pairs at a time). For each pair:
+// raster_kernel: one launch per occlusion phase; warps take equal shares of
+//   the visible pairs (grid-stride, `chunk` consecutive pairs at a time), keep
+//   the pairs of their phase, skip meshlets the hierarchical z-buffer proves
+//   hidden (phases after the first), and for each remaining pair:
 //   K1 — transform + snap the meshlet's vertices into a per-warp
 //        shared-memory cache (transform.cuh)
 //   K2 — per-lane triangle reject / near clip / cull / depth plane (setup.cuh)
 //   K4 — per-thread raster of small triangles, warp-cooperative raster of the
 //        rest, into the view's 64-bit z-buffer (raster.cuh)
+// hiz_kernel: between phases, the farthest stored key of every 8x8 tile.
 // shade_kernel (K5): one CTA row per view; each thread resolves four
 //   consecutive pixels of a row (shade.cuh) and writes RGB / depth / id with
 //   vector stores when the row layout allows it.
@@ -69,9 +72,19 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         if (!aabb_visible(pl, grp.bmin, grp.bmax)) continue;
         const uint32_t m = grp.m0 + lane;
         bool vis = false;
+        uint32_t phase = 0;
         if (m < grp.m1) {
             const Meshlet ml = S.meshlets[m];
             vis = aabb_visible(pl, ml.bmin, ml.bmax);
+            // distance band of the box from the camera -> occlusion phase
+            const float *cp = p.views[vi].pos;
+            float d2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float dk = fmaxf(fmaxf(ml.bmin[k] - cp[k], cp[k] - ml.bmax[k]), 0.f);
+                d2 = __fmaf_rn(dk, dk, d2);
+            }
+            phase = (p.n_phases > 1 && d2 > p.phase_r2[0]) + (p.n_phases > 2 && d2 > p.phase_r2[1]);
         }
         const unsigned mask = __ballot_sync(0xFFFFFFFFu, vis);
         if (!mask) continue;
@@ -79,7 +92,7 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         if (lane == 0) base = atomicAdd(p.vis_count, (uint32_t)__popc(mask));
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         const uint32_t slot = base + __popc(mask & ((1u << lane) - 1u));
-        if (vis && slot < p.vis_cap) p.vis[slot] = make_uint2(vi, m);
+        if (vis && slot < p.vis_cap) p.vis[slot] = make_uint2(vi, m | (phase << kPhaseShift));
     }
 }
 
@@ -185,7 +198,86 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p)
+// Conservative occlusion test of a meshlet against the hierarchical z-buffer
+// of phases already rasterised (whole warp). Every fragment of the meshlet has
+// inverse depth at most 1/d_min of its (inflated) box, because interpolated q
+// is clamped to the vertices' range; if every 8x8 tile under the box's
+// projected rectangle already stores keys strictly nearer than that bound,
+// none of its fragments can win any pixel, and skipping it changes nothing.
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ bool meshlet_occluded(const Meshlet &ml, const float *M, const Params &p,
+                                                 const uint32_t *hiz_v, int lane)
+{
+    float d = 3.0e38f, xe = 0.f, ye = 0.f;
+    if (lane < 8) {
+        const float x = (lane & 1) ? ml.bmax[0] : ml.bmin[0];
+        const float y = (lane & 2) ? ml.bmax[1] : ml.bmin[1];
+        const float z = (lane & 4) ? ml.bmax[2] : ml.bmin[2];
+        eye_transform(M, x, y, z, xe, ye, d);
+    }
+    const float dmin = warp_min(d);
+    if (!(dmin > p.znear + 1e-3f)) return false;        // box reaches the near plane: keep
+    float sx0 = 3.0e38f, sx1 = -3.0e38f, sy0 = 3.0e38f, sy1 = -3.0e38f;
+    if (lane < 8) {
+        const float r = __frcp_rn(d);
+        const float sx = __fmaf_rn(p.fx, __fmul_rn(xe, r), p.cx);
+        const float sy = __fmaf_rn(-p.fy, __fmul_rn(ye, r), p.cy);
+        sx0 = sx1 = sx;
+        sy0 = sy1 = sy;
+    }
+    sx0 = warp_min(sx0);
+    sx1 = warp_max(sx1);
+    sy0 = warp_min(sy0);
+    sy1 = warp_max(sy1);
+    const float Wf = (float)p.width, Hf = (float)p.height;
+    const int x0 = (int)fminf(fmaxf(floorf(sx0 - 1.f), 0.f), Wf - 1.f);
+    const int x1 = (int)fminf(fmaxf(ceilf(sx1 + 1.f), 0.f), Wf - 1.f);
+    const int y0 = (int)fminf(fmaxf(floorf(sy0 - 1.f), 0.f), Hf - 1.f);
+    const int y1 = (int)fminf(fmaxf(ceilf(sy1 + 1.f), 0.f), Hf - 1.f);
+    const int tx0 = x0 / kHizTile, tx1 = x1 / kHizTile, ty0 = y0 / kHizTile, ty1 = y1 / kHizTile;
+    const int ntx = tx1 - tx0 + 1, n = ntx * (ty1 - ty0 + 1);
+    if (n > 1024) return false;
+    const uint32_t hb = ~__float_as_uint(__frcp_rn(dmin * (1.0f - 1e-5f)));
+    bool occ = true;
+    for (int i = lane; i < n; i += 32) {
+        const int tx = tx0 + i % ntx, ty = ty0 + i / ntx;
+        if (hiz_v[ty * p.hiz_w + tx] >= hb) occ = false;
+    }
+    return __all_sync(0xFFFFFFFFu, occ);
+}
+
+// Hierarchical z: per 8x8 tile of each view, the largest stored key >> 32
+// (the farthest fragment, or background = 0xFFFFFFFF).
+__global__ void __launch_bounds__(256) hiz_kernel(const Params p)
+{
+    const uint32_t per_view = p.hiz_w * p.hiz_h;
+    const uint32_t total = p.n_views * per_view;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const uint32_t v = t / per_view, r = t % per_view;
+        const uint32_t ty = r / p.hiz_w, tx = r % p.hiz_w;
+        const unsigned long long *zb = p.zbuf + (size_t)v * p.width * p.height;
+        const uint32_t x0 = tx * kHizTile, y0 = ty * kHizTile;
+        const uint32_t x1 = min(x0 + kHizTile, p.width), y1 = min(y0 + kHizTile, p.height);
+        uint32_t mx = 0;
+        for (uint32_t y = y0; y < y1; y++)
+            for (uint32_t x = x0; x < x1; x++) mx = max(mx, (uint32_t)(zb[(size_t)y * p.width + x] >> 32));
+        p.hiz[t] = mx;
+    }
+}
+
+__global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p, uint32_t phase)
 {
     // dynamic shared memory: per warp a hot and a cold vertex cache and a
     // big-triangle queue (raster_smem_bytes)
@@ -209,7 +301,9 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
         const uint32_t e1 = min(e0 + p.chunk, count);
         for (uint32_t e = e0; e < e1; e++) {
             const uint2 pr = p.vis[e];
+            if ((pr.y >> kPhaseShift) != phase) continue;
             const uint32_t vi = pr.x;
+            const uint32_t m = pr.y & kMeshletMask;
             if (vi != cur_view) {
                 cur_view = vi;
                 const View &V = p.views[vi];
@@ -225,7 +319,10 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
                 }
                 __syncwarp();
             }
-            process_meshlet(c, vw, p, pr.y, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
+            if (phase > 0 &&
+                meshlet_occluded(c.meshlets[m], vw, p, p.hiz + (size_t)vi * p.hiz_w * p.hiz_h, lane))
+                continue;
+            process_meshlet(c, vw, p, m, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
         }
     }
 }
@@ -373,9 +470,18 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
             if (e != cudaSuccess) return e;
             attr_dev = dev;
         }
-        raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, smem, stream>>>(p);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        const uint32_t hiz_tiles = p.n_views * p.hiz_w * p.hiz_h;
+        const uint32_t hiz_blocks = std::min<uint32_t>((hiz_tiles + 255) / 256, (uint32_t)sms * 16);
+        for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
+            if (ph > 0) {
+                hiz_kernel<<<hiz_blocks, 256, 0, stream>>>(p);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
+            raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, smem, stream>>>(p, ph);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     } else {
         mark(1, stream);
     }
