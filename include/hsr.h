@@ -140,6 +140,17 @@ HSR_API int hsr_set_stage_timing(int enable);
 HSR_API int hsr_get_stage_timing(float *ms);
 
 /*
+ * Diagnostic work counters (measurement support, not part of the method).
+ * While enabled, render calls count, per occlusion phase, the visible
+ * (view, meshlet) pairs rasterised and the meshlets skipped as hidden;
+ * hsr_get_stage_stats synchronises the device and writes counts[0..2] = pairs
+ * per phase, counts[3..5] = skipped per phase, for the last call. Enabling
+ * allocates 32 bytes of device memory once. Use from one thread at a time.
+ */
+HSR_API int hsr_set_stage_stats(int enable);
+HSR_API int hsr_get_stage_stats(uint32_t *counts);
+
+/*
  * Allocation-free variant of hsr_render (the paper has no counterpart; this is
  * a library-integration feature). Same arguments, outputs and results as
  * hsr_render, but no memory is allocated on the call path: its scratch (view

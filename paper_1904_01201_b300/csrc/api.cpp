@@ -346,6 +346,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     p.hiz_w = (uint32_t)hiz_w;
     p.hiz_h = (uint32_t)hiz_h;
     p.n_phases = std::min<uint32_t>(std::max<uint32_t>(cfg.n_phases, 1u), 3u);
+    p.stats = stage_stats_buffer();
     p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
     p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
     e = launch_render(p, cfg, stream);
@@ -638,6 +639,19 @@ int hsr_get_stage_timing(float *ms)
 {
     if (!ms) return HSR_ERR_INVALID_ARG;
     const cudaError_t e = stage_timing_read(ms);
+    if (e == cudaErrorNotReady) return HSR_ERR_INVALID_ARG;
+    return e == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+}
+
+int hsr_set_stage_stats(int enable)
+{
+    return stage_stats_enable(enable != 0) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+}
+
+int hsr_get_stage_stats(uint32_t *counts)
+{
+    if (!counts) return HSR_ERR_INVALID_ARG;
+    const cudaError_t e = stage_stats_read(counts);
     if (e == cudaErrorNotReady) return HSR_ERR_INVALID_ARG;
     return e == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
 }

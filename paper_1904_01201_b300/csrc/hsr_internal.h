@@ -88,6 +88,7 @@ struct Params {
     uint32_t n_phases;         // 1 (no occlusion culling) .. 3
     float phase_r2[2];         // squared band radii, metres^2
     uint32_t *hiz;             // [n_views][hiz_h][hiz_w]: max key >> 32 over each 8x8 tile
+    uint32_t *stats;           // diagnostic counters or null: [0..2] pairs per phase, [3..5] skipped per phase
     uint32_t hiz_w, hiz_h;
 };
 
@@ -110,5 +111,10 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
 // Stage timing (diagnostic): events around cull / raster / shade.
 cudaError_t stage_timing_enable(bool on);
 cudaError_t stage_timing_read(float ms[4]);
+
+// Diagnostic counters of the last render call (null when disabled).
+uint32_t *stage_stats_buffer();
+cudaError_t stage_stats_enable(bool on);
+cudaError_t stage_stats_read(uint32_t out[6]);
 
 }  // namespace hsr

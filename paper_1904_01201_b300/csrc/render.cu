@@ -319,9 +319,12 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
                 }
                 __syncwarp();
             }
+            if (p.stats && lane == 0) atomicAdd(p.stats + phase, 1u);
             if (phase > 0 &&
-                meshlet_occluded(c.meshlets[m], vw, p, p.hiz + (size_t)vi * p.hiz_w * p.hiz_h, lane))
+                meshlet_occluded(c.meshlets[m], vw, p, p.hiz + (size_t)vi * p.hiz_w * p.hiz_h, lane)) {
+                if (p.stats && lane == 0) atomicAdd(p.stats + 3 + phase, 1u);
                 continue;
+            }
             process_meshlet(c, vw, p, m, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
         }
     }
@@ -443,6 +446,31 @@ cudaError_t stage_timing_read(float ms[4])
     return cudaEventElapsedTime(&ms[3], g_ev[0], g_ev[3]);
 }
 
+namespace {
+uint32_t *g_stats = nullptr;      // device counters (6 words), allocated when enabled
+bool g_stats_on = false;
+}  // namespace
+
+uint32_t *stage_stats_buffer() { return g_stats_on ? g_stats : nullptr; }
+
+cudaError_t stage_stats_enable(bool on)
+{
+    if (on && !g_stats) {
+        cudaError_t e = cudaMalloc(&g_stats, 8 * sizeof(uint32_t));
+        if (e != cudaSuccess) return e;
+    }
+    g_stats_on = on;
+    return cudaSuccess;
+}
+
+cudaError_t stage_stats_read(uint32_t out[6])
+{
+    if (!g_stats) return cudaErrorNotReady;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(out, g_stats, 6 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+}
+
 static inline void mark(int k, cudaStream_t stream)
 {
     if (g_timing) cudaEventRecord(g_ev[k], stream);
@@ -456,6 +484,10 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     mark(0, stream);
+    if (p.stats) {
+        e = cudaMemsetAsync(p.stats, 0, 6 * sizeof(uint32_t), stream);
+        if (e != cudaSuccess) return e;
+    }
     if (p.total_items > 0) {
         const uint32_t cull_blocks = std::min<uint32_t>((p.total_items + 7) / 8, (uint32_t)sms * 8);
         cull_kernel<<<cull_blocks, 256, 0, stream>>>(p);

@@ -61,6 +61,8 @@ def _load():
         "hsr_render_noalloc": ([P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P], ctypes.c_int),
         "hsr_set_stage_timing": ([ctypes.c_int], ctypes.c_int),
         "hsr_get_stage_timing": ([P], ctypes.c_int),
+        "hsr_set_stage_stats": ([ctypes.c_int], ctypes.c_int),
+        "hsr_get_stage_stats": ([P], ctypes.c_int),
         "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "hsr_version": ([], ctypes.c_char_p),
     }
@@ -96,6 +98,21 @@ def hsr_get_stage_timing():
     if st != HSR_OK:
         raise HsrError(st, "hsr_get_stage_timing")
     return {"cull": float(ms[0]), "raster": float(ms[1]), "shade": float(ms[2]), "total": float(ms[3])}
+
+
+def hsr_set_stage_stats(enable: bool) -> None:
+    st = _lib.hsr_set_stage_stats(1 if enable else 0)
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_set_stage_stats")
+
+
+def hsr_get_stage_stats():
+    """Work counters of the last render call: pairs and skipped meshlets per occlusion phase."""
+    c = np.zeros(6, dtype=np.uint32)
+    st = _lib.hsr_get_stage_stats(_np_ptr(c))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_get_stage_stats")
+    return {"pairs": [int(v) for v in c[:3]], "skipped": [int(v) for v in c[3:]]}
 
 
 def hsr_version() -> str:
