@@ -161,7 +161,7 @@ HSR_API int hsr_get_stage_stats(uint32_t *counts);
  * cannot afford an allocator call, and hosts that route every allocation
  * through their own allocator.
  *   - A call needing more than 32 MiB of scratch (about 8 B per output pixel
- *     per view + 8 B per meshlet per view + 176 B per view) returns
+ *     per view + 16 B per meshlet per view + 176 B per view) returns
  *     HSR_ERR_OVERFLOW; split such batches or use hsr_render.
  *   - All calls share the array and it keeps the last call's contents (each
  *     call re-initialises what it needs). Calls whose work overlaps on the

@@ -219,7 +219,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         list_entries += scenes[s]->dev.n_meshlets;
     }
     const uint64_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
-    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 8ull + (uint64_t)n * hiz_w * hiz_h * 4ull;
+    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 16ull + (uint64_t)n * hiz_w * hiz_h * 4ull;
     if (scratch > kMaxScratchBytes && n > 1) {
         const uint32_t h = n / 2;
         const size_t px = (size_t)width * height;
@@ -297,7 +297,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
 
     LaunchCfg cfg = cfg_in ? *cfg_in : LaunchCfg{};
     const size_t zbytes = (size_t)n * width * height * sizeof(unsigned long long);
-    const size_t lbytes = (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2);
+    const size_t lbytes = 2 * (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2);
     const size_t hbytes = (size_t)n * hiz_w * hiz_h * sizeof(uint32_t);
     void *dbuf = nullptr, *zbuf = nullptr;
     cudaError_t e = cudaMallocAsync(&dbuf, total, stream);
@@ -322,7 +322,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     const uint32_t *dslot = reinterpret_cast<const uint32_t *>(dchar + off_slots);
     p.vis_count = reinterpret_cast<uint32_t *>(dchar);
     p.vis = reinterpret_cast<uint2 *>(static_cast<unsigned char *>(zbuf) + zbytes);
-    p.vis_cap = (uint32_t)list_entries;
+    p.vis_cap = (uint32_t)std::max<uint64_t>(list_entries, 1);
     p.scenes = reinterpret_cast<const SceneDev *>(dchar + off_scenes);
     p.views = reinterpret_cast<const View *>(dchar + off_views);
     p.slot_item_base = dslot;
@@ -341,7 +341,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = far_threshold(intr->zfar);
     p.small_px = std::min<uint32_t>(cfg.small_px, 32);
-    p.chunk = std::max<uint32_t>(cfg.chunk, 1);
+    p.chunk = std::min<uint32_t>(std::max<uint32_t>(cfg.chunk, 1), 32);
     p.hiz = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes);
     p.hiz_w = (uint32_t)hiz_w;
     p.hiz_h = (uint32_t)hiz_h;
@@ -529,7 +529,7 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         }
         flush();
         const uint32_t n_meshlets = (uint32_t)meshlets.size();
-        if (n_meshlets > kMeshletMask) throw std::bad_alloc();   // visible-list entries hold 28-bit meshlet ids
+        if (n_meshlets > kMaxMeshlets) throw std::bad_alloc();
         Meshlet sentinel{};
         sentinel.vbase = (uint32_t)mvert.size();
         sentinel.tbase = (uint32_t)mtri.size();

@@ -66,9 +66,13 @@ struct Params {
     uint8_t *rgb;
     float *depth;
     uint32_t *ids;             // may be null
-    uint2 *vis;                // visible (view, meshlet | phase << 28) pairs written by the cull kernel
-    uint32_t *vis_count;       // number of pairs in `vis` (preset to 0)
-    uint32_t vis_cap;          // capacity of `vis`
+    // Visible (view, meshlet) pairs written by the cull kernel, one list per
+    // occlusion phase in a buffer of 2 * vis_cap entries: phase 0 grows up
+    // from vis[0], phase 2 grows down from vis[vis_cap - 1], phase 1 grows up
+    // from vis[vis_cap] (vis_cap = worst case, every meshlet in every view).
+    uint2 *vis;
+    uint32_t *vis_count;       // [3] pairs per phase (preset to 0)
+    uint32_t vis_cap;
     // Views are sorted by scene; slot k covers views [slot_view_base[k], ...)
     // of scene slot_scene[k] and work items [slot_item_base[k], slot_item_base[k+1]),
     // item = slot_item_base[k] + (view - slot_view_base[k]) * n_groups + group.
@@ -81,7 +85,7 @@ struct Params {
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels
-    uint32_t chunk;            // consecutive visible pairs a raster warp takes per step
+    uint32_t chunk;            // consecutive visible pairs a raster warp takes per step (<= 32)
     // occlusion phases: a visible meshlet at distance r from the camera goes
     // to phase (r > phase_r[0]) + (r > phase_r[1]), limited to n_phases - 1;
     // phases after the first skip meshlets the hierarchical z-buffer proves hidden
@@ -93,13 +97,12 @@ struct Params {
 };
 
 constexpr int kHizTile = 8;
-constexpr uint32_t kPhaseShift = 28;
-constexpr uint32_t kMeshletMask = (1u << kPhaseShift) - 1u;
+constexpr uint32_t kMaxMeshlets = 0x0FFFFFFFu;
 
 // Launch configuration chosen by the host (autotuned).
 struct LaunchCfg {
     uint32_t small_px = 16;
-    uint32_t chunk = 4;
+    uint32_t chunk = 16;
     uint32_t raster_ctas_per_sm = 3;
     uint32_t n_phases = 3;
     float phase_r[2] = {3.0f, 7.0f};

@@ -14,7 +14,7 @@
 //
 // Limits and rules (also stated in include/hsr.h):
 //  * the array holds kNoAllocScratchBytes = 32 MiB; a call needing more
-//    (about 8 bytes per output pixel per view plus 8 bytes per meshlet per
+//    (about 8 bytes per output pixel per view plus 16 bytes per meshlet per
 //    view, plus 176 bytes per view) is rejected with HSR_ERR_OVERFLOW;
 //  * the host-side descriptors are staged in a fixed 1 MiB host buffer
 //    (at most ~6500 views per call);
@@ -83,7 +83,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     const uint64_t items = (uint64_t)n * sd.n_groups;
     const uint32_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
     const uint64_t hbytes = (uint64_t)n * hiz_w * hiz_h * sizeof(uint32_t);
-    const uint64_t need = (uint64_t)off_z + zbytes + list_entries * sizeof(uint2) + hbytes;
+    const uint64_t need = (uint64_t)off_z + zbytes + 2 * list_entries * sizeof(uint2) + hbytes;
     if (need > kNoAllocScratchBytes || desc_bytes > kNoAllocHostBytes) return HSR_ERR_OVERFLOW;
     if (items >= 0xFFFFFFF0ull) return HSR_ERR_OVERFLOW;
 
@@ -148,8 +148,8 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.q_far = host_far_threshold(intr->zfar);
     const LaunchCfg cfg{};
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
-    p.chunk = cfg.chunk > 0 ? cfg.chunk : 1;
-    p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + list_entries * sizeof(uint2));
+    p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;
+    p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + 2 * list_entries * sizeof(uint2));
     p.hiz_w = hiz_w;
     p.hiz_h = hiz_h;
     p.n_phases = cfg.n_phases;

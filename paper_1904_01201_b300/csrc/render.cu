@@ -56,6 +56,13 @@ struct ItemDecoder {
     }
 };
 
+// Slot of entry k of a phase list (see Params::vis). The three lists share
+// 2 * vis_cap slots and hold at most vis_cap entries together.
+__device__ __forceinline__ size_t vis_index(const Params &p, uint32_t phase, uint32_t k)
+{
+    return phase == 0 ? (size_t)k : (phase == 2 ? (size_t)p.vis_cap - 1 - k : (size_t)p.vis_cap + k);
+}
+
 __global__ void __launch_bounds__(256) cull_kernel(const Params p)
 {
     const int lane = threadIdx.x & 31;
@@ -86,13 +93,18 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             }
             phase = (p.n_phases > 1 && d2 > p.phase_r2[0]) + (p.n_phases > 2 && d2 > p.phase_r2[1]);
         }
-        const unsigned mask = __ballot_sync(0xFFFFFFFFu, vis);
-        if (!mask) continue;
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(p.vis_count, (uint32_t)__popc(mask));
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        const uint32_t slot = base + __popc(mask & ((1u << lane) - 1u));
-        if (vis && slot < p.vis_cap) p.vis[slot] = make_uint2(vi, m | (phase << kPhaseShift));
+        // one warp-aggregated append per phase list
+#pragma unroll
+        for (uint32_t ph = 0; ph < 3; ph++) {
+            const bool mine = vis && phase == ph;
+            const unsigned mask = __ballot_sync(0xFFFFFFFFu, mine);
+            if (!mask) continue;
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(p.vis_count + ph, (uint32_t)__popc(mask));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            const uint32_t k = base + __popc(mask & ((1u << lane) - 1u));
+            if (mine) p.vis[vis_index(p, ph, k)] = make_uint2(vi, m);
+        }
     }
 }
 
@@ -100,7 +112,6 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
 struct WarpCtx {
     // view-dependent, warp-uniform
     unsigned long long *zbuf;
-    const Meshlet *meshlets;
     const float4 *mvert;
     const uint2 *mtri;
 };
@@ -133,12 +144,17 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     bigq[slot] = r;
 }
 
-__device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M, const Params &p, uint32_t m,
-                                                EyeHot *vh, EyeCold *vcold, BigTri *bigq, uint32_t *bign, int lane)
+// A meshlet's vertex / triangle ranges and bounding box, held in registers.
+struct MeshletRef {
+    uint32_t vbase, tbase, vend, tend;
+    float box[6];     // bmin xyz, bmax xyz
+};
+
+__device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M, const Params &p,
+                                                const MeshletRef &ml, EyeHot *vh, EyeCold *vcold, BigTri *bigq,
+                                                uint32_t *bign, int lane)
 {
-    const Meshlet ml = c.meshlets[m];
-    const uint32_t vend = c.meshlets[m + 1].vbase, tend = c.meshlets[m + 1].tbase;
-    const int nv = (int)(vend - ml.vbase), nt = (int)(tend - ml.tbase);
+    const int nv = (int)(ml.vend - ml.vbase), nt = (int)(ml.tend - ml.tbase);
     const float zn = p.znear, zf = p.zfar;
 
     // K1: transform + snap this meshlet's vertices
@@ -217,14 +233,14 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-__device__ __forceinline__ bool meshlet_occluded(const Meshlet &ml, const float *M, const Params &p,
-                                                 const uint32_t *hiz_v, int lane)
+__device__ __forceinline__ bool meshlet_occluded(const float *bmin, const float *bmax, const float *M,
+                                                 const Params &p, const uint32_t *hiz_v, int lane)
 {
     float d = 3.0e38f, xe = 0.f, ye = 0.f;
     if (lane < 8) {
-        const float x = (lane & 1) ? ml.bmax[0] : ml.bmin[0];
-        const float y = (lane & 2) ? ml.bmax[1] : ml.bmin[1];
-        const float z = (lane & 4) ? ml.bmax[2] : ml.bmin[2];
+        const float x = (lane & 1) ? bmax[0] : bmin[0];
+        const float y = (lane & 2) ? bmax[1] : bmin[1];
+        const float z = (lane & 4) ? bmax[2] : bmin[2];
         eye_transform(M, x, y, z, xe, ye, d);
     }
     const float dmin = warp_min(d);
@@ -292,18 +308,37 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
     float *vw = s_view[warp];
     if (lane == 0) s_bign[warp] = 0;
     __syncwarp();
-    const uint32_t count = min(*p.vis_count, p.vis_cap);
+    const uint32_t count = min(p.vis_count[phase], p.vis_cap);
     const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t CH = p.chunk;
     WarpCtx c{};
     uint32_t cur_view = 0xFFFFFFFFu, cur_scene = 0xFFFFFFFFu;
-    for (uint32_t e0 = warp_id * p.chunk; e0 < count; e0 += n_warps * p.chunk) {
-        const uint32_t e1 = min(e0 + p.chunk, count);
-        for (uint32_t e = e0; e < e1; e++) {
-            const uint2 pr = p.vis[e];
-            if ((pr.y >> kPhaseShift) != phase) continue;
-            const uint32_t vi = pr.x;
-            const uint32_t m = pr.y & kMeshletMask;
+    for (uint32_t e0 = warp_id * CH; e0 < count; e0 += n_warps * CH) {
+        const uint32_t ne = min(CH, count - e0);
+        // prefetch: lane j loads entry e0 + j and its meshlet record
+        uint32_t pv = 0, pm = 0, pvb = 0, ptb = 0, pve = 0, pte = 0;
+        float pb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if ((uint32_t)lane < ne) {
+            const uint2 pr = p.vis[vis_index(p, phase, e0 + lane)];
+            pv = pr.x;
+            pm = pr.y;
+            const Meshlet *mls = p.scenes[p.views[pv].scene].meshlets;
+            const Meshlet ml = mls[pm];
+            const Meshlet nx = mls[pm + 1];
+            pvb = ml.vbase; ptb = ml.tbase; pve = nx.vbase; pte = nx.tbase;
+            pb[0] = ml.bmin[0]; pb[1] = ml.bmin[1]; pb[2] = ml.bmin[2];
+            pb[3] = ml.bmax[0]; pb[4] = ml.bmax[1]; pb[5] = ml.bmax[2];
+        }
+        for (uint32_t j = 0; j < ne; j++) {
+            const uint32_t vi = __shfl_sync(0xFFFFFFFFu, pv, j);
+            MeshletRef r;
+            r.vbase = __shfl_sync(0xFFFFFFFFu, pvb, j);
+            r.tbase = __shfl_sync(0xFFFFFFFFu, ptb, j);
+            r.vend = __shfl_sync(0xFFFFFFFFu, pve, j);
+            r.tend = __shfl_sync(0xFFFFFFFFu, pte, j);
+#pragma unroll
+            for (int k = 0; k < 6; k++) r.box[k] = __shfl_sync(0xFFFFFFFFu, pb[k], j);
             if (vi != cur_view) {
                 cur_view = vi;
                 const View &V = p.views[vi];
@@ -313,19 +348,18 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
                 if (V.scene != cur_scene) {
                     cur_scene = V.scene;
                     const SceneDev &S = p.scenes[cur_scene];
-                    c.meshlets = S.meshlets;
                     c.mvert = S.mvert;
                     c.mtri = S.mtri;
                 }
                 __syncwarp();
             }
             if (p.stats && lane == 0) atomicAdd(p.stats + phase, 1u);
-            if (phase > 0 &&
-                meshlet_occluded(c.meshlets[m], vw, p, p.hiz + (size_t)vi * p.hiz_w * p.hiz_h, lane)) {
+            if (phase > 0 && meshlet_occluded(r.box, r.box + 3, vw, p,
+                                              p.hiz + (size_t)vi * p.hiz_w * p.hiz_h, lane)) {
                 if (p.stats && lane == 0) atomicAdd(p.stats + 3 + phase, 1u);
                 continue;
             }
-            process_meshlet(c, vw, p, m, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
+            process_meshlet(c, vw, p, r, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
         }
     }
 }
