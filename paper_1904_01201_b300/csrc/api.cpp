@@ -321,6 +321,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     auto *dchar = static_cast<unsigned char *>(dbuf);
     const uint32_t *dslot = reinterpret_cast<const uint32_t *>(dchar + off_slots);
     p.vis_count = reinterpret_cast<uint32_t *>(dchar);
+    p.work_counter = reinterpret_cast<uint32_t *>(dchar) + 4;
     p.vis = reinterpret_cast<uint2 *>(static_cast<unsigned char *>(zbuf) + zbytes);
     p.vis_cap = (uint32_t)std::max<uint64_t>(list_entries, 1);
     p.scenes = reinterpret_cast<const SceneDev *>(dchar + off_scenes);

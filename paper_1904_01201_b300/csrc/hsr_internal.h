@@ -72,6 +72,7 @@ struct Params {
     // from vis[vis_cap] (vis_cap = worst case, every meshlet in every view).
     uint2 *vis;
     uint32_t *vis_count;       // [3] pairs per phase (preset to 0)
+    uint32_t *work_counter;    // [3] raster work cursor per phase (preset to 0)
     uint32_t vis_cap;
     // Views are sorted by scene; slot k covers views [slot_view_base[k], ...)
     // of scene slot_scene[k] and work items [slot_item_base[k], slot_item_base[k+1]),
@@ -102,7 +103,7 @@ constexpr uint32_t kMaxMeshlets = 0x0FFFFFFFu;
 // Launch configuration chosen by the host (autotuned).
 struct LaunchCfg {
     uint32_t small_px = 16;
-    uint32_t chunk = 16;
+    uint32_t chunk = 4;
     uint32_t raster_ctas_per_sm = 3;
     uint32_t n_phases = 3;
     float phase_r[2] = {3.0f, 7.0f};

@@ -126,6 +126,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
 
     Params p{};
     p.vis_count = reinterpret_cast<uint32_t *>(d);
+    p.work_counter = reinterpret_cast<uint32_t *>(d) + 4;
     p.scenes = reinterpret_cast<const SceneDev *>(d + off_scene);
     const uint32_t *dslot = reinterpret_cast<const uint32_t *>(d + off_slots);
     p.slot_item_base = dslot;

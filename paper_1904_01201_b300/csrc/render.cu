@@ -309,12 +309,15 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
     if (lane == 0) s_bign[warp] = 0;
     __syncwarp();
     const uint32_t count = min(p.vis_count[phase], p.vis_cap);
-    const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t CH = p.chunk;
     WarpCtx c{};
     uint32_t cur_view = 0xFFFFFFFFu, cur_scene = 0xFFFFFFFFu;
-    for (uint32_t e0 = warp_id * CH; e0 < count; e0 += n_warps * CH) {
+    for (;;) {
+        // dynamic work distribution: the next CH pairs of this phase's list
+        uint32_t e0 = 0;
+        if (lane == 0) e0 = atomicAdd(p.work_counter + phase, CH);
+        e0 = __shfl_sync(0xFFFFFFFFu, e0, 0);
+        if (e0 >= count) break;
         const uint32_t ne = min(CH, count - e0);
         // prefetch: lane j loads entry e0 + j and its meshlet record
         uint32_t pv = 0, pm = 0, pvb = 0, ptb = 0, pve = 0, pte = 0;
