@@ -219,7 +219,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         list_entries += scenes[s]->dev.n_meshlets;
     }
     const uint64_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
-    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 16ull + (uint64_t)n * hiz_w * hiz_h * 4ull;
+    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 16ull +
+                             (uint64_t)n * hiz_w * hiz_h * 4ull;
     if (scratch > kMaxScratchBytes && n > 1) {
         const uint32_t h = n / 2;
         const size_t px = (size_t)width * height;
@@ -298,11 +299,13 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     LaunchCfg cfg = cfg_in ? *cfg_in : LaunchCfg{};
     const size_t zbytes = (size_t)n * width * height * sizeof(unsigned long long);
     const size_t lbytes = 2 * (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2);
-    const size_t hbytes = (size_t)n * hiz_w * hiz_h * sizeof(uint32_t);
+    const size_t hbytes = ((size_t)n * hiz_w * hiz_h * sizeof(uint32_t) + 255) & ~(size_t)255;
+    const size_t rbytes = (size_t)kBigRecCap * sizeof(BigTriStorage);
+    const size_t ibytes = 3 * (size_t)kBigInstCap * sizeof(uint2);
     void *dbuf = nullptr, *zbuf = nullptr;
     cudaError_t e = cudaMallocAsync(&dbuf, total, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMallocAsync(&zbuf, zbytes + lbytes + hbytes, stream);
+    e = cudaMallocAsync(&zbuf, zbytes + lbytes + hbytes + rbytes + ibytes, stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(dbuf, stream);
         return cuda_status(e);
@@ -344,6 +347,12 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     p.small_px = std::min<uint32_t>(cfg.small_px, 32);
     p.chunk = std::min<uint32_t>(std::max<uint32_t>(cfg.chunk, 1), 32);
     p.hiz = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes);
+    p.big_rec = reinterpret_cast<BigTri *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes + hbytes);
+    p.big_rec_cap = kBigRecCap;
+    p.big_inst = reinterpret_cast<uint2 *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes + hbytes + rbytes);
+    p.big_inst_cap = kBigInstCap;
+    p.big_rec_count = reinterpret_cast<uint32_t *>(dchar) + 8;
+    p.big_inst_count = reinterpret_cast<uint32_t *>(dchar) + 12;
     p.hiz_w = (uint32_t)hiz_w;
     p.hiz_h = (uint32_t)hiz_h;
     p.n_phases = std::min<uint32_t>(std::max<uint32_t>(cfg.n_phases, 1u), 3u);

@@ -94,6 +94,17 @@ struct Params {
     float phase_r2[2];         // squared band radii, metres^2
     uint32_t *hiz;             // [n_views][hiz_h][hiz_w]: max key >> 32 over each 8x8 tile
     uint32_t *stats;           // diagnostic counters or null: [0..2] pairs per phase, [3..5] skipped per phase
+    // Tile bins of large triangles: a triangle with more than small_px
+    // candidate pixels is stored once in `big_rec` and binned to every 8x8
+    // tile its pixel range touches (`big_inst`, one list of big_inst_cap
+    // entries per phase); big_raster_kernel rasterises the bins after each
+    // phase. Null / full bins fall back to the per-warp queue.
+    struct BigTri *big_rec;
+    uint32_t *big_rec_count;   // [1]
+    uint32_t big_rec_cap;
+    uint2 *big_inst;           // (record, first tile of a run, row-major over its tile rectangle)
+    uint32_t *big_inst_count;  // [3]
+    uint32_t big_inst_cap;
     uint32_t hiz_w, hiz_h;
 };
 
@@ -101,6 +112,13 @@ constexpr int kHizTile = 8;
 constexpr uint32_t kMaxMeshlets = 0x0FFFFFFFu;
 
 // Launch configuration chosen by the host (autotuned).
+constexpr uint32_t kBigRecCap = 1u << 18;
+// storage size of one binned large triangle (kernels/raster.cuh BigTri)
+struct alignas(16) BigTriStorage {
+    unsigned char bytes[64];
+};
+constexpr uint32_t kBigInstCap = 1u << 20;
+
 struct LaunchCfg {
     uint32_t small_px = 16;
     uint32_t chunk = 4;

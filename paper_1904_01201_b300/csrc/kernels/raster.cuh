@@ -21,12 +21,14 @@
 
 namespace hsr {
 
-// A queued triangle for the warp-cooperative path (64 bytes).
+// A large triangle for the warp-cooperative and tile-bin paths (64 bytes).
 struct alignas(16) BigTri {
     int X0, Y0, X1, Y1, X2, Y2;
     float pa, pb, q0, qlo, qhi;
     uint32_t id;
     unsigned short x0, y0, x1, y1;      // candidate pixel range, clipped to the image
+    uint32_t view;                       // z-buffer the triangle belongs to (tile-bin path)
+    uint32_t pad_;
 };
 
 __device__ __forceinline__ unsigned long long depth_key(float q, uint32_t id)
@@ -78,6 +80,35 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0
         const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0, qlo, qhi);
         if (!(q >= q_far)) continue;
         zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
+    }
+}
+
+// The whole warp, one 8x8 tile of a binned triangle: lane (lx, ly) covers
+// pixels (lx, ly) and (lx, ly + 4) of the tile, int64 edges.
+__device__ __forceinline__ void raster_tile_warp(const BigTri &t, int tx, int ty, int lane, float q_far,
+                                                 unsigned long long *zbuf, int W)
+{
+    const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
+    const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
+    const int b2 = edge_bias(t.X0, t.Y0, t.X1, t.Y1);
+    const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
+    const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
+    const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
+    const int px = tx * 8 + (lane & 7);
+    if (px < (int)t.x0 || px > (int)t.x1) return;
+    const int Px = 256 * px + 128;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int py = ty * 8 + (lane >> 3) + 4 * h;
+        if (py < (int)t.y0 || py > (int)t.y1) continue;
+        const int Py = 256 * py + 128;
+        const long long e0 = (long long)dx0 * (Py - t.Y1) - (long long)dy0 * (Px - t.X1);
+        const long long e1 = (long long)dx1 * (Py - t.Y2) - (long long)dy1 * (Px - t.X2);
+        const long long e2 = (long long)dx2 * (Py - t.Y0) - (long long)dy2 * (Px - t.X0);
+        if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
+        const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0, t.qlo, t.qhi);
+        if (!(q >= q_far)) continue;
+        zmin(zbuf + (size_t)py * W + px, depth_key(q, t.id));
     }
 }
 

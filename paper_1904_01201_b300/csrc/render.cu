@@ -35,6 +35,8 @@ constexpr int kRasterWarps = 8;
 constexpr int kRasterThreads = kRasterWarps * 32;
 constexpr int kBigCap = 2 * kMeshletTris;        // a lane emits at most two sub-triangles
 constexpr int kShadeThreads = 256;
+static_assert(sizeof(BigTri) == sizeof(BigTriStorage), "binned triangle storage size");
+constexpr uint32_t kTilesPerInst = 8;
 
 // --------------------------------------------------------------------- cull
 // Decode a (view, group) work item: views are sorted by scene, slot k holds
@@ -119,7 +121,7 @@ struct WarpCtx {
 // Emit one front-facing (sub-)triangle: clip its pixel range to the image,
 // raster it here when small, else queue it for the warp.
 __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Params &p, unsigned long long *zbuf,
-                                         BigTri *bigq, uint32_t *bign)
+                                         BigTri *bigq, uint32_t *bign, uint32_t view, uint32_t phase)
 {
     int x0, x1, y0, y1, spanx, spany;
     pixel_range(t, x0, x1, y0, y1, spanx, spany);
@@ -135,13 +137,54 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     }
     float pa, pb;
     depth_plane(t, pa, pb);
-    const uint32_t slot = atomicAdd(bign, 1u);
     BigTri r;
     r.X0 = t.X0; r.Y0 = t.Y0; r.X1 = t.X1; r.Y1 = t.Y1; r.X2 = t.X2; r.Y2 = t.Y2;
     r.pa = pa; r.pb = pb; r.q0 = t.q0; r.qlo = tri_qlo(t); r.qhi = tri_qhi(t); r.id = id;
     r.x0 = (unsigned short)x0; r.x1 = (unsigned short)x1;
     r.y0 = (unsigned short)y0; r.y1 = (unsigned short)y1;
+    r.view = view;
+    r.pad_ = 0;
+    if (p.big_rec) {
+        // bin to 8x8 tiles for the tile raster pass
+        // instances cover runs of kTilesPerInst tiles of the triangle's tile rectangle
+        const uint32_t ntiles = (uint32_t)(((x1 >> 3) - (x0 >> 3) + 1) * ((y1 >> 3) - (y0 >> 3) + 1));
+        const uint32_t ninst = (ntiles + kTilesPerInst - 1) / kTilesPerInst;
+        const uint32_t ri = atomicAdd(p.big_rec_count, 1u);
+        if (ri < p.big_rec_cap) {
+            const uint32_t k0 = atomicAdd(p.big_inst_count + phase, ninst);
+            if (k0 + ninst <= p.big_inst_cap && k0 + ninst >= k0) {
+                p.big_rec[ri] = r;
+                uint2 *inst = p.big_inst + (size_t)phase * p.big_inst_cap + k0;
+                for (uint32_t k = 0; k < ninst; k++) inst[k] = make_uint2(ri, k * kTilesPerInst);
+                return;
+            }
+        }
+    }
+    const uint32_t slot = atomicAdd(bign, 1u);     // bins full: the warp rasterises it
     bigq[slot] = r;
+}
+
+// Tile raster of the binned large triangles of one phase: one warp per
+// instance (a triangle and a run of up to kTilesPerInst of its 8x8 tiles,
+// counted row-major over its tile rectangle), grid-stride.
+__global__ void __launch_bounds__(256) big_raster_kernel(const Params p, uint32_t phase)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t count = min(p.big_inst_count[phase], p.big_inst_cap);
+    const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const uint2 *inst = p.big_inst + (size_t)phase * p.big_inst_cap;
+    for (uint32_t i = warp_id; i < count; i += n_warps) {
+        const uint2 in = inst[i];
+        const BigTri t = p.big_rec[in.x];
+        const int tx0 = t.x0 >> 3, ty0 = t.y0 >> 3;
+        const int ntx = (t.x1 >> 3) - tx0 + 1;
+        const uint32_t ntiles = (uint32_t)(ntx * ((t.y1 >> 3) - ty0 + 1));
+        unsigned long long *zb = p.zbuf + (size_t)t.view * p.width * p.height;
+        const uint32_t kend = min(in.y + kTilesPerInst, ntiles);
+        for (uint32_t k = in.y; k < kend; k++)
+            raster_tile_warp(t, tx0 + (int)(k % ntx), ty0 + (int)(k / ntx), lane, p.q_far, zb, (int)p.width);
+    }
 }
 
 // A meshlet's vertex / triangle ranges and bounding box, held in registers.
@@ -152,7 +195,7 @@ struct MeshletRef {
 
 __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M, const Params &p,
                                                 const MeshletRef &ml, EyeHot *vh, EyeCold *vcold, BigTri *bigq,
-                                                uint32_t *bign, int lane)
+                                                uint32_t *bign, int lane, uint32_t view, uint32_t phase)
 {
     const int nv = (int)(ml.vend - ml.vbase), nt = (int)(ml.tend - ml.tbase);
     const float zn = p.znear, zf = p.zfar;
@@ -187,7 +230,8 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
         if (!all_near && !all_far) {
             Tri2D t;
             if (a.d >= zn && b.d >= zn && cc.d >= zn) {
-                if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, cc.X, cc.Y, cc.q, t)) emit_tri(t, id, p, c.zbuf, bigq, bign);
+                if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, cc.X, cc.Y, cc.q, t))
+                    emit_tri(t, id, p, c.zbuf, bigq, bign, view, phase);
             } else {
                 const EyeCold ca = vcold[ia], cb = vcold[ib], ccc = vcold[ic];
                 CVert<0> v[3];
@@ -202,7 +246,7 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
                     project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
                 for (int f = 0; f + 2 < np; f++)
                     if (orient_cull(X[0], Y[0], q[0], X[f + 1], Y[f + 1], q[f + 1], X[f + 2], Y[f + 2], q[f + 2], t))
-                        emit_tri(t, id, p, c.zbuf, bigq, bign);
+                        emit_tri(t, id, p, c.zbuf, bigq, bign, view, phase);
             }
         }
     }
@@ -275,21 +319,30 @@ __device__ __forceinline__ bool meshlet_occluded(const float *bmin, const float 
 }
 
 // Hierarchical z: per 8x8 tile of each view, the largest stored key >> 32
-// (the farthest fragment, or background = 0xFFFFFFFF).
+// (the farthest fragment, or background = 0xFFFFFFFF). Eight threads per
+// tile, one row each, combined with shuffles.
 __global__ void __launch_bounds__(256) hiz_kernel(const Params p)
 {
     const uint32_t per_view = p.hiz_w * p.hiz_h;
-    const uint32_t total = p.n_views * per_view;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const uint32_t v = t / per_view, r = t % per_view;
-        const uint32_t ty = r / p.hiz_w, tx = r % p.hiz_w;
-        const unsigned long long *zb = p.zbuf + (size_t)v * p.width * p.height;
-        const uint32_t x0 = tx * kHizTile, y0 = ty * kHizTile;
-        const uint32_t x1 = min(x0 + kHizTile, p.width), y1 = min(y0 + kHizTile, p.height);
+    const uint32_t total = p.n_views * per_view * kHizTile;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ((total + 31) & ~31u);
+         g += gridDim.x * blockDim.x) {
         uint32_t mx = 0;
-        for (uint32_t y = y0; y < y1; y++)
-            for (uint32_t x = x0; x < x1; x++) mx = max(mx, (uint32_t)(zb[(size_t)y * p.width + x] >> 32));
-        p.hiz[t] = mx;
+        const uint32_t t = g / kHizTile, row = g % kHizTile;
+        if (g < total) {
+            const uint32_t v = t / per_view, r = t % per_view;
+            const uint32_t ty = r / p.hiz_w, tx = r % p.hiz_w;
+            const uint32_t y = ty * kHizTile + row, x0 = tx * kHizTile;
+            const uint32_t x1 = min(x0 + kHizTile, p.width);
+            if (y < p.height) {
+                const unsigned long long *zr = p.zbuf + (size_t)v * p.width * p.height + (size_t)y * p.width;
+                for (uint32_t x = x0; x < x1; x++) mx = max(mx, (uint32_t)(zr[x] >> 32));
+            }
+        }
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
+        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 4));
+        if (g < total && row == 0) p.hiz[t] = mx;
     }
 }
 
@@ -362,7 +415,7 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
                 if (p.stats && lane == 0) atomicAdd(p.stats + 3 + phase, 1u);
                 continue;
             }
-            process_meshlet(c, vw, p, r, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane);
+            process_meshlet(c, vw, p, r, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane, vi, phase);
         }
     }
 }
@@ -539,8 +592,8 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
             if (e != cudaSuccess) return e;
             attr_dev = dev;
         }
-        const uint32_t hiz_tiles = p.n_views * p.hiz_w * p.hiz_h;
-        const uint32_t hiz_blocks = std::min<uint32_t>((hiz_tiles + 255) / 256, (uint32_t)sms * 16);
+        const uint32_t hiz_threads = p.n_views * p.hiz_w * p.hiz_h * kHizTile;
+        const uint32_t hiz_blocks = std::min<uint32_t>((hiz_threads + 255) / 256, (uint32_t)sms * 16);
         for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
             if (ph > 0) {
                 hiz_kernel<<<hiz_blocks, 256, 0, stream>>>(p);
@@ -550,6 +603,11 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
             raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, smem, stream>>>(p, ph);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
+            if (p.big_rec) {
+                big_raster_kernel<<<(uint32_t)sms * 8, 256, 0, stream>>>(p, ph);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
         }
     } else {
         mark(1, stream);
