@@ -297,11 +297,13 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     }
 
     LaunchCfg cfg = cfg_in ? *cfg_in : LaunchCfg{};
-    const size_t zbytes = (size_t)n * width * height * sizeof(unsigned long long);
-    const size_t lbytes = 2 * (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2);
-    const size_t hbytes = ((size_t)n * hiz_w * hiz_h * sizeof(uint32_t) + 255) & ~(size_t)255;
-    const size_t rbytes = (size_t)kBigRecCap * sizeof(BigTriStorage);
-    const size_t ibytes = 3 * (size_t)kBigInstCap * sizeof(uint2);
+    // scratch sections, each starting on a 256-byte boundary:
+    // z-buffer | visible lists | tile z | binned triangles | bin instances
+    const size_t zbytes = al((size_t)n * width * height * sizeof(unsigned long long));
+    const size_t lbytes = al(2 * (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2));
+    const size_t hbytes = al((size_t)n * hiz_w * hiz_h * sizeof(uint32_t));
+    const size_t rbytes = al((size_t)kBigRecCap * sizeof(BigTriStorage));
+    const size_t ibytes = al(3 * (size_t)kBigInstCap * sizeof(uint2));
     void *dbuf = nullptr, *zbuf = nullptr;
     cudaError_t e = cudaMallocAsync(&dbuf, total, stream);
     if (e != cudaSuccess) return cuda_status(e);

@@ -78,12 +78,13 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     const size_t off_views = off_slots + 256;
     const size_t desc_bytes = off_views + (size_t)n * sizeof(View);
     const size_t off_z = align256(desc_bytes);
-    const uint64_t zbytes = (uint64_t)n * width * height * sizeof(unsigned long long);
+    const uint64_t zbytes = align256((size_t)n * width * height * sizeof(unsigned long long));
     const uint64_t list_entries = (uint64_t)n * sd.n_meshlets;
     const uint64_t items = (uint64_t)n * sd.n_groups;
     const uint32_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
     const uint64_t hbytes = (uint64_t)n * hiz_w * hiz_h * sizeof(uint32_t);
-    const uint64_t need = (uint64_t)off_z + zbytes + 2 * list_entries * sizeof(uint2) + hbytes;
+    const uint64_t lbytes = align256(2 * list_entries * sizeof(uint2));
+    const uint64_t need = (uint64_t)off_z + zbytes + lbytes + hbytes;
     if (need > kNoAllocScratchBytes || desc_bytes > kNoAllocHostBytes) return HSR_ERR_OVERFLOW;
     if (items >= 0xFFFFFFF0ull) return HSR_ERR_OVERFLOW;
 
@@ -150,7 +151,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     const LaunchCfg cfg{};
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;
-    p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + 2 * list_entries * sizeof(uint2));
+    p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + lbytes);
     p.hiz_w = hiz_w;
     p.hiz_h = hiz_h;
     p.n_phases = cfg.n_phases;

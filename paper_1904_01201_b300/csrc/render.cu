@@ -37,6 +37,7 @@ constexpr int kBigCap = 2 * kMeshletTris;        // a lane emits at most two sub
 constexpr int kShadeThreads = 256;
 static_assert(sizeof(BigTri) == sizeof(BigTriStorage), "binned triangle storage size");
 constexpr uint32_t kTilesPerInst = 8;
+constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
 
 // --------------------------------------------------------------------- cull
 // Decode a (view, group) work item: views are sorted by scene, slot k holds
@@ -152,12 +153,14 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
         const uint32_t ri = atomicAdd(p.big_rec_count, 1u);
         if (ri < p.big_rec_cap) {
             const uint32_t k0 = atomicAdd(p.big_inst_count + phase, ninst);
+            uint2 *inst = p.big_inst + (size_t)phase * p.big_inst_cap;
             if (k0 + ninst <= p.big_inst_cap && k0 + ninst >= k0) {
                 p.big_rec[ri] = r;
-                uint2 *inst = p.big_inst + (size_t)phase * p.big_inst_cap + k0;
-                for (uint32_t k = 0; k < ninst; k++) inst[k] = make_uint2(ri, k * kTilesPerInst);
+                for (uint32_t k = 0; k < ninst; k++) inst[k0 + k] = make_uint2(ri, k * kTilesPerInst);
                 return;
             }
+            // reservation straddles the end: mark the in-range slots as empty
+            for (uint32_t k = k0; k < p.big_inst_cap && k - k0 < ninst; k++) inst[k] = make_uint2(kNoRecord, 0u);
         }
     }
     const uint32_t slot = atomicAdd(bign, 1u);     // bins full: the warp rasterises it
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(256) big_raster_kernel(const Params p, uint32_
     const uint2 *inst = p.big_inst + (size_t)phase * p.big_inst_cap;
     for (uint32_t i = warp_id; i < count; i += n_warps) {
         const uint2 in = inst[i];
+        if (in.x == kNoRecord) continue;
         const BigTri t = p.big_rec[in.x];
         const int tx0 = t.x0 >> 3, ty0 = t.y0 >> 3;
         const int ntx = (t.x1 >> 3) - tx0 + 1;
