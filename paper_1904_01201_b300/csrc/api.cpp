@@ -347,6 +347,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = far_threshold(intr->zfar);
     p.small_px = std::min<uint32_t>(cfg.small_px, 32);
+    p.bin_px = cfg.bin_px;
     p.chunk = std::min<uint32_t>(std::max<uint32_t>(cfg.chunk, 1), 32);
     p.hiz = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes);
     p.big_rec = reinterpret_cast<BigTri *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes + hbytes);

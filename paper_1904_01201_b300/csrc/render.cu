@@ -145,7 +145,7 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     r.y0 = (unsigned short)y0; r.y1 = (unsigned short)y1;
     r.view = view;
     r.pad_ = 0;
-    if (p.big_rec) {
+    if (p.big_rec && npx > (int)p.bin_px) {
         // bin to 8x8 tiles for the tile raster pass
         // instances cover runs of kTilesPerInst tiles of the triangle's tile rectangle
         const uint32_t ntiles = (uint32_t)(((x1 >> 3) - (x0 >> 3) + 1) * ((y1 >> 3) - (y0 >> 3) + 1));
