@@ -366,7 +366,9 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
     if (lane == 0) s_bign[warp] = 0;
     __syncwarp();
     const uint32_t count = min(p.vis_count[phase], p.vis_cap);
-    const uint32_t CH = p.chunk;
+    // chunk shrinks when the phase has few pairs, so that every warp gets work
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t CH = max(1u, min(p.chunk, count / (2 * n_warps)));
     WarpCtx c{};
     uint32_t cur_view = 0xFFFFFFFFu, cur_scene = 0xFFFFFFFFu;
     for (;;) {
