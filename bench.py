@@ -266,6 +266,14 @@ def run_gpu(args, wk):
 
     step = step_plain if args.mode == "plain" else step_batched
 
+    # autotuned launch configuration for this workload (untimed; cached per GPU)
+    tuned = None
+    if not args.no_tune:
+        from paper_1904_01201_b300 import tuning
+        cfg, source = tuning.ensure_tuned(wk["scenes"], handles, soa, poses, wk["intr"], W, H, out, stream,
+                                          use_cache=not args.retune)
+        tuned = dict(cfg, source=source)
+
     def barrier():
         if world > 1:
             import torch.distributed as dist
@@ -369,7 +377,7 @@ def run_gpu(args, wk):
         "config": {"workload": wk["name"], "scenes": len(handles), "tris": [int(s.n_tris) for s in wk["scenes"]],
                    "agents": n, "width": W, "height": H, "outputs": "rgb+depth" + ("+ids" if wk["ids"] else ""),
                    "mode": args.mode, "l2": "flushed before every step (256 MiB write, untimed)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "launch_config": tuned or "default"},
         "roofline": {"bound": "hbm", "achieved": raster_achieved, "peak": peak, "unit": "GB/s",
                      "frac": raster_achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "hsr::raster_kernel", "kernel_ms_per_launch": stages["raster"],
@@ -407,6 +415,8 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--agents", type=int, default=0, help="render only the first N agents (profiling)")
+    ap.add_argument("--no-tune", action="store_true", help="use the default launch configuration")
+    ap.add_argument("--retune", action="store_true", help="ignore the tuning cache")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

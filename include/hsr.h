@@ -129,6 +129,44 @@ HSR_API int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes,
                      uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
 
 /*
+ * Launch configuration of the render kernels (performance only: every valid
+ * configuration produces identical outputs).
+ */
+typedef struct {
+    uint32_t small_px;     /* triangles with at most this many candidate pixels: one thread each (1..32) */
+    uint32_t bin_px;       /* more than this: binned to 8x8 screen tiles; in between: per-warp queue */
+    uint32_t chunk;        /* visible (view, meshlet) pairs a raster warp fetches at a time (1..32) */
+    uint32_t ctas_per_sm;  /* raster CTAs per SM (1..3) */
+    uint32_t n_phases;     /* occlusion phases (1..3); 1 disables occlusion culling */
+    float phase_r[2];      /* distance bands of the phases, metres */
+} hsr_config;
+
+/* Fill *cfg with the built-in default configuration. */
+HSR_API int hsr_config_default(hsr_config *cfg);
+
+/*
+ * Autotuner (the batching row of the scope: bin and tile sizes chosen per
+ * workload). Renders the given batch repeatedly (into the given outputs)
+ * under candidate configurations, timing each with CUDA events on the
+ * caller's stream (median of `reps` timed calls after one warm-up), by
+ * coordinate descent from the default; stores the fastest configuration for
+ * this workload signature (scene set, n, width, height, ids present) so that
+ * later hsr_render / hsr_render_batch calls with the same signature use it,
+ * and returns it in *best (and its time in *best_ms). Synchronises the stream.
+ * Arguments as for hsr_render_batch (scene_of_agent may be NULL when
+ * n_scenes == 1).
+ */
+HSR_API int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
+                         const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width,
+                         uint32_t height, uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream,
+                         uint32_t reps, hsr_config *best, float *best_ms);
+
+/* Register a configuration for a workload signature (e.g. one loaded from a
+ * tuning cache); cfg == NULL removes it. */
+HSR_API int hsr_set_tuned_config(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n, uint32_t width,
+                                 uint32_t height, int with_ids, const hsr_config *cfg);
+
+/*
  * Diagnostic stage timing (measurement support, not part of the method).
  * While enabled, every render call records CUDA events on its stream around
  * its three stages; hsr_get_stage_timing waits for the last call's events and

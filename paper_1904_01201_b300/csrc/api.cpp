@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -198,6 +199,69 @@ void view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32
     }
 }
 
+// ------------------------------------------------------------ tuned configs
+struct TuneKey {
+    std::vector<const hsr_scene *> scenes;
+    uint32_t n, width, height;
+    int ids;
+    bool operator<(const TuneKey &o) const
+    {
+        if (scenes != o.scenes) return scenes < o.scenes;
+        if (n != o.n) return n < o.n;
+        if (width != o.width) return width < o.width;
+        if (height != o.height) return height < o.height;
+        return ids < o.ids;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LaunchCfg> g_tuned;
+
+TuneKey make_key(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n, uint32_t w, uint32_t h, int ids)
+{
+    TuneKey k;
+    k.scenes.assign(scenes, scenes + n_scenes);
+    k.n = n;
+    k.width = w;
+    k.height = h;
+    k.ids = ids ? 1 : 0;
+    return k;
+}
+
+bool lookup_tuned(const TuneKey &k, LaunchCfg &out)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(k);
+    if (it == g_tuned.end()) return false;
+    out = it->second;
+    return true;
+}
+
+LaunchCfg from_config(const hsr_config &c)
+{
+    LaunchCfg l;
+    l.small_px = std::min<uint32_t>(std::max<uint32_t>(c.small_px, 1), 32);
+    l.bin_px = std::max<uint32_t>(c.bin_px, l.small_px);
+    l.chunk = std::min<uint32_t>(std::max<uint32_t>(c.chunk, 1), 32);
+    l.raster_ctas_per_sm = std::min<uint32_t>(std::max<uint32_t>(c.ctas_per_sm, 1), 3);
+    l.n_phases = std::min<uint32_t>(std::max<uint32_t>(c.n_phases, 1), 3);
+    l.phase_r[0] = std::isfinite(c.phase_r[0]) ? std::max(c.phase_r[0], 0.0f) : 3.0f;
+    l.phase_r[1] = std::isfinite(c.phase_r[1]) ? std::max(c.phase_r[1], l.phase_r[0]) : 7.0f;
+    return l;
+}
+
+hsr_config to_config(const LaunchCfg &l)
+{
+    hsr_config c;
+    c.small_px = l.small_px;
+    c.bin_px = l.bin_px;
+    c.chunk = l.chunk;
+    c.ctas_per_sm = l.raster_ctas_per_sm;
+    c.n_phases = l.n_phases;
+    c.phase_r[0] = l.phase_r[0];
+    c.phase_r[1] = l.phase_r[1];
+    return c;
+}
+
 // Shared body of hsr_render / hsr_render_batch.
 int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
                  const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width, uint32_t height,
@@ -296,7 +360,11 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         v.frame = i;
     }
 
-    LaunchCfg cfg = cfg_in ? *cfg_in : LaunchCfg{};
+    LaunchCfg cfg;
+    if (cfg_in)
+        cfg = *cfg_in;
+    else
+        lookup_tuned(make_key(scenes, n_scenes, n, width, height, ids != nullptr), cfg);
     // scratch sections, each starting on a 256-byte boundary:
     // z-buffer | visible lists | tile z | binned triangles | bin instances
     const size_t zbytes = al((size_t)n * width * height * sizeof(unsigned long long));
@@ -640,6 +708,105 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         return HSR_ERR_OOM;
     }
     *out = s;
+    return HSR_OK;
+}
+
+int hsr_config_default(hsr_config *cfg)
+{
+    if (!cfg) return HSR_ERR_INVALID_ARG;
+    *cfg = to_config(LaunchCfg{});
+    return HSR_OK;
+}
+
+int hsr_set_tuned_config(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n, uint32_t width,
+                         uint32_t height, int with_ids, const hsr_config *cfg)
+{
+    if (!scenes || n_scenes == 0) return HSR_ERR_INVALID_ARG;
+    const TuneKey k = make_key(scenes, n_scenes, n, width, height, with_ids);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (cfg)
+        g_tuned[k] = from_config(*cfg);
+    else
+        g_tuned.erase(k);
+    return HSR_OK;
+}
+
+int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
+                 const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width, uint32_t height,
+                 uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream, uint32_t reps, hsr_config *best,
+                 float *best_ms)
+{
+    if (!scenes || n_scenes == 0 || (n_scenes > 1 && !scene_of_agent)) return HSR_ERR_INVALID_ARG;
+    reps = std::max<uint32_t>(1, std::min<uint32_t>(reps, 50));
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return HSR_ERR_CUDA;
+    }
+    int status = HSR_OK;
+    auto measure = [&](const LaunchCfg &c, float &ms) -> int {
+        int st = render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
+                              cuda_stream, &c);
+        if (st != HSR_OK) return st;
+        std::vector<float> t;
+        for (uint32_t r = 0; r < reps; r++) {
+            if (cudaEventRecord(e0, stream) != cudaSuccess) return HSR_ERR_CUDA;
+            st = render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
+                              cuda_stream, &c);
+            if (st != HSR_OK) return st;
+            if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return HSR_ERR_CUDA;
+            float x = 0;
+            cudaEventElapsedTime(&x, e0, e1);
+            t.push_back(x);
+        }
+        std::sort(t.begin(), t.end());
+        ms = t[t.size() / 2];
+        return HSR_OK;
+    };
+    // coordinate descent over the launch parameters, two sweeps
+    LaunchCfg cur;
+    float cur_ms = 0;
+    status = measure(cur, cur_ms);
+    const uint32_t small_v[] = {8, 16, 24, 32};
+    const uint32_t bin_v[] = {16, 32, 64, 128, 256, 512, 4096};
+    const uint32_t chunk_v[] = {1, 2, 4, 8, 16};
+    const uint32_t phase_v[] = {1, 2, 3};
+    const float radius_v[][2] = {{2.f, 5.f}, {3.f, 7.f}, {4.f, 10.f}, {6.f, 14.f}};
+    const uint32_t cta_v[] = {2, 3};
+    for (int sweep = 0; sweep < 2 && status == HSR_OK; sweep++) {
+        for (int param = 0; param < 6 && status == HSR_OK; param++) {
+            const int nv = param == 0 ? 4 : param == 1 ? 7 : param == 2 ? 5 : param == 3 ? 3 : param == 4 ? 4 : 2;
+            for (int k = 0; k < nv && status == HSR_OK; k++) {
+                LaunchCfg c = cur;
+                switch (param) {
+                    case 0: c.small_px = small_v[k]; break;
+                    case 1: c.bin_px = bin_v[k]; break;
+                    case 2: c.chunk = chunk_v[k]; break;
+                    case 3: c.n_phases = phase_v[k]; break;
+                    case 4: c.phase_r[0] = radius_v[k][0]; c.phase_r[1] = radius_v[k][1]; break;
+                    default: c.raster_ctas_per_sm = cta_v[k]; break;
+                }
+                c.bin_px = std::max(c.bin_px, c.small_px);
+                float ms = 0;
+                status = measure(c, ms);
+                if (status == HSR_OK && ms < cur_ms) {
+                    cur = c;
+                    cur_ms = ms;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != HSR_OK) return status;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[make_key(scenes, n_scenes, n, width, height, ids != nullptr)] = cur;
+    }
+    if (best) *best = to_config(cur);
+    if (best_ms) *best_ms = cur_ms;
     return HSR_OK;
 }
 

@@ -40,6 +40,20 @@ class hsr_scene_info(ctypes.Structure):
                 ("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3)]
 
 
+class hsr_config(ctypes.Structure):
+    _fields_ = [("small_px", ctypes.c_uint32), ("bin_px", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("n_phases", ctypes.c_uint32), ("phase_r", ctypes.c_float * 2)]
+
+    def as_dict(self):
+        return {"small_px": self.small_px, "bin_px": self.bin_px, "chunk": self.chunk,
+                "ctas_per_sm": self.ctas_per_sm, "n_phases": self.n_phases, "phase_r": list(self.phase_r)}
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(d["small_px"], d["bin_px"], d["chunk"], d["ctas_per_sm"], d["n_phases"],
+                   (ctypes.c_float * 2)(*d["phase_r"]))
+
+
 class HsrError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -63,6 +77,10 @@ def _load():
         "hsr_get_stage_timing": ([P], ctypes.c_int),
         "hsr_set_stage_stats": ([ctypes.c_int], ctypes.c_int),
         "hsr_get_stage_stats": ([P], ctypes.c_int),
+        "hsr_config_default": ([ctypes.POINTER(hsr_config)], ctypes.c_int),
+        "hsr_autotune": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P, U32,
+                          ctypes.POINTER(hsr_config), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "hsr_set_tuned_config": ([P, U32, U32, U32, U32, ctypes.c_int, ctypes.POINTER(hsr_config)], ctypes.c_int),
         "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "hsr_version": ([], ctypes.c_char_p),
     }
@@ -202,6 +220,36 @@ def hsr_render_batch(handles: Sequence[int], scene_of_agent, poses, intr, width,
     return _lib.hsr_render_batch(arr, len(handles), _np_ptr(soa), _np_ptr(poses), poses.shape[0], ctypes.byref(ci),
                                  int(width), int(height), _dev_ptr(rgb), _dev_ptr(depth), _dev_ptr(ids),
                                  _stream_ptr(stream))
+
+
+def hsr_config_default() -> hsr_config:
+    c = hsr_config()
+    _lib.hsr_config_default(ctypes.byref(c))
+    return c
+
+
+def hsr_autotune(handles: Sequence[int], scene_of_agent, poses, intr, width, height, rgb, depth, ids=None,
+                 stream=None, reps: int = 3):
+    """Tune the launch configuration for this workload; returns (hsr_config, ms)."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    soa = None if scene_of_agent is None else np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+    best = hsr_config()
+    ms = ctypes.c_float()
+    st = _lib.hsr_autotune(arr, len(handles), _np_ptr(soa), _np_ptr(poses), poses.shape[0],
+                           ctypes.byref(as_intrinsics(intr)), int(width), int(height), _dev_ptr(rgb), _dev_ptr(depth),
+                           _dev_ptr(ids), _stream_ptr(stream), int(reps), ctypes.byref(best), ctypes.byref(ms))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_autotune")
+    return best, float(ms.value)
+
+
+def hsr_set_tuned_config(handles: Sequence[int], n, width, height, with_ids, cfg) -> None:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    st = _lib.hsr_set_tuned_config(arr, len(handles), int(n), int(width), int(height), 1 if with_ids else 0,
+                                   None if cfg is None else ctypes.byref(cfg))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_set_tuned_config")
 
 
 # -------------------------------------------------------------- conveniences
