@@ -4,7 +4,8 @@
 Default workload (N=1): the 1M-triangle synthetic house with a 4096^2 RGBA8
 atlas, 64 agents at random navigable poses, 256x256 RGB + depth — one step
 renders all 64 views in one batched launch. `--mode plain` renders the same
-views one agent per launch. `--impl reference` times the CPU oracle (the
+views one agent per launch. The batched step is one replay of a
+graph-captured persistent batch (hsr_batch_render). `--impl reference` times the CPU oracle (the
 reference arm: there is no runnable code of the paper).
 
 Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the
@@ -244,7 +245,7 @@ def run_gpu(args, wk):
     poses, soa = wk["poses"], wk["soa"]
     multi = len(handles) > 1
 
-    def step_batched():
+    def step_oneshot():
         if multi:
             st = hsr.hsr_render_batch([h.handle for h in handles], soa, poses, wk["intr"], W, H, out["rgb"],
                                       out["depth"], out.get("ids"), stream)
@@ -253,6 +254,15 @@ def run_gpu(args, wk):
                                 out.get("ids"), stream)
         if st != 0:
             raise hsr.HsrError(st, "render")
+        return 1
+
+    graph = None
+
+    def step_batched():
+        # one replay of the graph-captured persistent batch
+        st = hsr.hsr_batch_render(graph, soa if multi else None, poses, None, stream)
+        if st != 0:
+            raise hsr.HsrError(st, "hsr_batch_render")
         return 1
 
     def step_plain():
@@ -273,6 +283,8 @@ def run_gpu(args, wk):
         cfg, source = tuning.ensure_tuned(wk["scenes"], handles, soa, poses, wk["intr"], W, H, out, stream,
                                           use_cache=not args.retune)
         tuned = dict(cfg, source=source)
+    graph = hsr.hsr_batch_create([h.handle for h in handles], n, wk["intr"], W, H, out["rgb"], out["depth"],
+                                 out.get("ids"))
 
     def barrier():
         if world > 1:
@@ -328,6 +340,13 @@ def run_gpu(args, wk):
             acc[k] += t[k]
     hsr.hsr_set_stage_timing(False)
     stages = {k: v / stage_steps for k, v in acc.items()}
+
+    # one-shot calls (per-call scratch allocation, no graph) on the same views
+    oneshot = None
+    if args.mode == "batched":
+        osteps = max(3, args.steps // 5)
+        oms, _, _ = timed(step_oneshot, osteps, False)
+        oneshot = {"value": n * osteps / (oms / 1e3), "ms_per_step": oms / osteps}
 
     # plain one-agent-per-launch path on the same views, for comparison
     plain = None
@@ -394,6 +413,8 @@ def run_gpu(args, wk):
         "clocks": clocks,
         "kernel_sha": kernel_source_hash(),
     }
+    if oneshot:
+        res["oneshot"] = oneshot
     if plain:
         res["plain"] = plain
         res["batched_over_plain"] = value / plain["value"]

@@ -141,6 +141,30 @@ typedef struct {
     float phase_r[2];      /* distance bands of the phases, metres */
 } hsr_config;
 
+/*
+ * Persistent batch (the batched form of the scope: many agents of several
+ * resident scenes per launch, captured once in a CUDA graph and replayed).
+ * hsr_batch_create sizes all scratch for up to n_cap views at width x height
+ * of the given scenes, binds the output buffers (rgb [n_cap][H][W][3], depth
+ * [n_cap][H][W], ids [n_cap][H][W] or NULL, device), and captures the whole
+ * render (descriptor upload, culling, raster phases, shading) into CUDA
+ * graphs; cfg == NULL uses the tuned configuration of this signature, if
+ * any, else the default. hsr_batch_render sets up n <= n_cap views from host
+ * poses (scene_of_agent: host [n] indices into the create-time scenes, or
+ * NULL for scene 0; frames: host [n] output frames < n_cap, or NULL for
+ * 0..n-1) and replays the graph on `cuda_stream`. Replays of one batch must
+ * be ordered on the GPU (same stream or explicit waits): they share scratch.
+ * Host arrays may be reused when the call returns; it may wait for the
+ * replay before last to finish its descriptor upload.
+ */
+typedef struct hsr_batch hsr_batch;
+HSR_API int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_cap,
+                             const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb,
+                             float *depth, uint32_t *ids, const hsr_config *cfg, hsr_batch **out);
+HSR_API int hsr_batch_render(hsr_batch *batch, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
+                             const uint32_t *frames, void *cuda_stream);
+HSR_API int hsr_batch_destroy(hsr_batch *batch);
+
 /* Fill *cfg with the built-in default configuration. */
 HSR_API int hsr_config_default(hsr_config *cfg);
 

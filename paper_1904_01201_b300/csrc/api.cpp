@@ -29,6 +29,7 @@ struct hsr_scene {
     hsr_scene_info info{};
 };
 
+
 namespace {
 
 constexpr double kCoordLimit = 1048576.0;       // |vertex coordinate| <= 2^20
@@ -262,25 +263,200 @@ hsr_config to_config(const LaunchCfg &l)
     return c;
 }
 
-// Shared body of hsr_render / hsr_render_batch.
+// ------------------------------------------------------------ render plan
+// Layout of the per-render descriptors (host staging and device copy) and of
+// the device scratch, for a capacity of n_cap views of the given scenes.
+//   descriptors: header (counters + dyn words) | scene table | slot arrays | views
+//   scratch:     z-buffer | visible lists | tile z | binned triangles | bin instances
+struct Plan {
+    uint32_t n_cap = 0, width = 0, height = 0, n_scenes = 0;
+    LaunchCfg cfg;
+    uint64_t list_cap = 1;           // visible pairs per list (worst case over the capacity)
+    uint64_t item_cap = 0;           // (view, group) work items (worst case)
+    uint32_t hiz_w = 0, hiz_h = 0;
+    size_t off_scenes = 0, off_slots = 0, off_views = 0, desc_bytes = 0;
+    size_t z_off = 0, l_off = 0, h_off = 0, r_off = 0, i_off = 0, scratch_bytes = 0, zbytes = 0;
+};
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Header words of the descriptor buffer.
+constexpr int kHdrVisCount = 0, kHdrWork = 4, kHdrBigRec = 8, kHdrBigInst = 12, kHdrDyn = 16;
+
+// max_meshlets / max_groups: per-view worst case (largest scene that may be rendered)
+void make_plan(Plan &pl, uint32_t n_scenes, uint32_t n_cap, uint32_t width, uint32_t height,
+               uint64_t list_entries, uint64_t items, const LaunchCfg &cfg)
+{
+    pl.n_cap = n_cap;
+    pl.width = width;
+    pl.height = height;
+    pl.n_scenes = n_scenes;
+    pl.cfg = cfg;
+    pl.list_cap = std::max<uint64_t>(list_entries, 1);
+    pl.item_cap = items;
+    pl.hiz_w = (width + kHizTile - 1) / kHizTile;
+    pl.hiz_h = (height + kHizTile - 1) / kHizTile;
+    pl.off_scenes = 256;
+    pl.off_slots = pl.off_scenes + al256(sizeof(SceneDev) * n_scenes);
+    pl.off_views = pl.off_slots + al256(sizeof(uint32_t) * (3 * (size_t)n_scenes + 1));
+    pl.desc_bytes = pl.off_views + sizeof(View) * (size_t)n_cap;
+    pl.zbytes = al256((size_t)n_cap * width * height * sizeof(unsigned long long));
+    pl.z_off = 0;
+    pl.l_off = pl.z_off + pl.zbytes;
+    pl.h_off = pl.l_off + al256(2 * (size_t)pl.list_cap * sizeof(uint2));
+    pl.r_off = pl.h_off + al256((size_t)n_cap * pl.hiz_w * pl.hiz_h * sizeof(uint32_t));
+    pl.i_off = pl.r_off + al256((size_t)kBigRecCap * sizeof(BigTriStorage));
+    pl.scratch_bytes = pl.i_off + al256(3 * (size_t)kBigInstCap * sizeof(uint2));
+}
+
+// Camera setup of n views (a1) into the host staging buffer `hbuf`
+// (pl.desc_bytes): views sorted by scene (stable), slot arrays, scene table,
+// zeroed counters and the dynamic header words. frames[i] (or i) is the
+// output frame of agent i.
+int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint32_t *scene_of_agent,
+                     const hsr_pose *poses, uint32_t n, const uint32_t *frames, const hsr_intrinsics &intr,
+                     unsigned char *hbuf)
+{
+    if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
+    std::vector<uint32_t> order(n);
+    for (uint32_t i = 0; i < n; i++) {
+        order[i] = i;
+        if ((scene_of_agent ? scene_of_agent[i] : 0u) >= pl.n_scenes) return HSR_ERR_INVALID_ARG;
+    }
+    if (scene_of_agent)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return scene_of_agent[a] < scene_of_agent[b]; });
+    std::memset(hbuf, 0, pl.off_scenes);
+    SceneDev *hs = reinterpret_cast<SceneDev *>(hbuf + pl.off_scenes);
+    for (uint32_t i = 0; i < pl.n_scenes; i++) hs[i] = scenes[i]->dev;
+    uint32_t *hslot = reinterpret_cast<uint32_t *>(hbuf + pl.off_slots);
+    const uint32_t S = pl.n_scenes;
+    std::memset(hslot, 0, sizeof(uint32_t) * (3 * (size_t)S + 1));
+    uint32_t n_slots = 0;
+    uint64_t items = 0, lists = 0;
+    View *hv = reinterpret_cast<View *>(hbuf + pl.off_views);
+    for (uint32_t k = 0; k < n; k++) {
+        const uint32_t i = order[k];
+        const uint32_t sidx = scene_of_agent ? scene_of_agent[i] : 0u;
+        if (n_slots == 0 || hslot[2 * S + 1 + n_slots - 1] != sidx) {
+            hslot[n_slots] = (uint32_t)items;             // slot_item_base
+            hslot[S + 1 + n_slots] = k;                   // slot_view_base
+            hslot[2 * S + 1 + n_slots] = sidx;            // slot_scene
+            n_slots++;
+        }
+        items += scenes[sidx]->dev.n_groups;
+        lists += scenes[sidx]->dev.n_meshlets;
+        View &v = hv[k];
+        std::memset(&v, 0, sizeof(View));
+        if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
+        if (!snap_in_range(scenes[sidx], poses[i], intr)) return HSR_ERR_INVALID_ARG;
+        view_planes(v.M, intr, pl.width, pl.height, v.planes);
+        for (int c = 0; c < 3; c++) v.pos[c] = poses[i].pos[c];
+        v.scene = sidx;
+        v.frame = frames ? frames[i] : i;
+    }
+    if (items > pl.item_cap || lists > pl.list_cap) return HSR_ERR_OVERFLOW;
+    hslot[n_slots] = (uint32_t)items;                      // slot_item_base[n_slots]
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(hbuf);
+    hdr[kHdrDyn + 0] = n;
+    hdr[kHdrDyn + 1] = (uint32_t)items;
+    hdr[kHdrDyn + 2] = n_slots;
+    return HSR_OK;
+}
+
+// Kernel parameters for descriptors at `desc` and scratch at `scratch`.
+Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, const hsr_intrinsics &intr,
+                   uint8_t *rgb, float *depth, uint32_t *ids, bool reset_zbuf)
+{
+    Params p{};
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(desc);
+    const uint32_t S = pl.n_scenes;
+    const uint32_t *dslot = reinterpret_cast<const uint32_t *>(desc + pl.off_slots);
+    p.vis_count = hdr + kHdrVisCount;
+    p.work_counter = hdr + kHdrWork;
+    p.big_rec_count = hdr + kHdrBigRec;
+    p.big_inst_count = hdr + kHdrBigInst;
+    p.dyn = hdr + kHdrDyn;
+    p.scenes = reinterpret_cast<const SceneDev *>(desc + pl.off_scenes);
+    p.views = reinterpret_cast<const View *>(desc + pl.off_views);
+    p.slot_item_base = dslot;
+    p.slot_view_base = dslot + S + 1;
+    p.slot_scene = dslot + 2 * S + 1;
+    p.n_slots = S;
+    p.zbuf = reinterpret_cast<unsigned long long *>(scratch + pl.z_off);
+    p.vis = reinterpret_cast<uint2 *>(scratch + pl.l_off);
+    p.vis_cap = (uint32_t)pl.list_cap;
+    p.hiz = reinterpret_cast<uint32_t *>(scratch + pl.h_off);
+    p.hiz_w = pl.hiz_w;
+    p.hiz_h = pl.hiz_h;
+    p.big_rec = reinterpret_cast<BigTri *>(scratch + pl.r_off);
+    p.big_rec_cap = kBigRecCap;
+    p.big_inst = reinterpret_cast<uint2 *>(scratch + pl.i_off);
+    p.big_inst_cap = kBigInstCap;
+    p.rgb = rgb;
+    p.depth = depth;
+    p.ids = ids;
+    p.n_views = pl.n_cap;
+    p.width = pl.width;
+    p.height = pl.height;
+    p.total_items = (uint32_t)std::min<uint64_t>(pl.item_cap, 0xFFFFFFF0ull);
+    p.fx = intr.fx; p.fy = intr.fy; p.cx = intr.cx; p.cy = intr.cy;
+    p.znear = intr.znear; p.zfar = intr.zfar;
+    p.q_far = far_threshold(intr.zfar);
+    const LaunchCfg &cfg = pl.cfg;
+    p.small_px = std::min<uint32_t>(std::max<uint32_t>(cfg.small_px, 1), 32);
+    p.bin_px = std::max(cfg.bin_px, p.small_px);
+    p.chunk = std::min<uint32_t>(std::max<uint32_t>(cfg.chunk, 1), 32);
+    p.n_phases = std::min<uint32_t>(std::max<uint32_t>(cfg.n_phases, 1u), 3u);
+    p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
+    p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
+    p.stats = stage_stats_buffer();
+    p.reset_zbuf = reset_zbuf ? 1u : 0u;
+    return p;
+}
+
+// Stream work of one render: upload descriptors, optionally preset the
+// z-buffer, launch the kernels.
+cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const void *h_desc, bool preset_z,
+                           cudaStream_t stream)
+{
+    cudaError_t e = cudaMemcpyAsync(d_desc, h_desc, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
+    if (preset_z) {
+        e = cudaMemsetAsync(p.zbuf, 0xFF, pl.zbytes, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_render(p, pl.cfg, stream);
+}
+
+bool validate_common(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_pose *poses, uint32_t n,
+                     const hsr_intrinsics *intr, uint32_t width, uint32_t height, const void *rgb, const void *depth)
+{
+    if (!scenes || n_scenes == 0 || !poses || n == 0 || !rgb || !depth) return false;
+    if (width == 0 || height == 0 || width > 4096 || height > 4096) return false;
+    if (!intrinsics_ok(intr)) return false;
+    for (uint32_t i = 0; i < n_scenes; i++)
+        if (!scenes[i]) return false;
+    return true;
+}
+
+// Shared body of hsr_render / hsr_render_batch: per-call scratch from the
+// stream-ordered allocator, descriptors through thread-local pinned staging.
 int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
                  const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width, uint32_t height,
                  uint8_t *rgb, float *depth, uint32_t *ids, void *stream_ptr, const LaunchCfg *cfg_in)
 {
-    if (!scenes || n_scenes == 0 || !poses || n == 0 || !rgb || !depth) return HSR_ERR_INVALID_ARG;
-    if (width == 0 || height == 0 || width > 4096 || height > 4096) return HSR_ERR_INVALID_ARG;
-    if (!intrinsics_ok(intr)) return HSR_ERR_INVALID_ARG;
-    for (uint32_t i = 0; i < n_scenes; i++)
-        if (!scenes[i]) return HSR_ERR_INVALID_ARG;
+    if (!validate_common(scenes, n_scenes, poses, n, intr, width, height, rgb, depth)) return HSR_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
-    // scratch: z-buffer (8 B / pixel / view) + worst-case visible-meshlet list
-    // (8 B per meshlet per view); large calls are split into halves
-    uint64_t list_entries = 0;
+    // scratch: z-buffer (8 B / pixel / view) + visible lists (16 B per meshlet
+    // per view) + tile z; large calls are split into halves
+    uint64_t list_entries = 0, items = 0;
     for (uint32_t i = 0; i < n; i++) {
         const uint32_t s = scene_of_agent ? scene_of_agent[i] : 0u;
         if (s >= n_scenes) return HSR_ERR_INVALID_ARG;
         list_entries += scenes[s]->dev.n_meshlets;
+        items += scenes[s]->dev.n_groups;
     }
     const uint64_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
     const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 16ull +
@@ -295,147 +471,97 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
                             width, height, rgb + 3 * px * h, depth + px * h, ids ? ids + px * h : nullptr, stream_ptr,
                             cfg_in);
     }
-
-    // views sorted by scene (stable), grouped into slots
-    std::vector<uint32_t> order(n);
-    for (uint32_t i = 0; i < n; i++) order[i] = i;
-    if (scene_of_agent)
-        std::stable_sort(order.begin(), order.end(),
-                         [&](uint32_t a, uint32_t b) { return scene_of_agent[a] < scene_of_agent[b]; });
-    std::vector<uint32_t> slot_scene, slot_view_base, slot_item_base;
-    uint64_t items = 0;
-    for (uint32_t k = 0; k < n; k++) {
-        const uint32_t s = scene_of_agent ? scene_of_agent[order[k]] : 0u;
-        if (slot_scene.empty() || slot_scene.back() != s) {
-            slot_scene.push_back(s);
-            slot_view_base.push_back(k);
-            slot_item_base.push_back((uint32_t)items);
-        }
-        items += scenes[s]->dev.n_groups;
-    }
     if (items >= 0xFFFFFFF0ull || list_entries >= 0xFFFFFFF0ull) return HSR_ERR_INVALID_ARG;
-    slot_item_base.push_back((uint32_t)items);
-    const uint32_t n_slots = (uint32_t)slot_scene.size();
-
-    // host staging: [counters | scenes | slot arrays | views]
-    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t off_scenes = 256;
-    const size_t off_slots = off_scenes + al(sizeof(SceneDev) * n_scenes);
-    const size_t off_views = off_slots + al(sizeof(uint32_t) * (3 * (size_t)n_slots + 1));
-    const size_t total = off_views + sizeof(View) * (size_t)n;
-    Staging &st = g_staging;
-    if (st.pending) {
-        if (cudaEventSynchronize(st.done) != cudaSuccess) return HSR_ERR_CUDA;
-        st.pending = false;
-    }
-    if (st.cap < total) {
-        if (st.host) cudaFreeHost(st.host);
-        st.host = nullptr;
-        st.cap = 0;
-        const size_t cap = std::max<size_t>(total, 64 * 1024);
-        if (cudaHostAlloc(&st.host, cap, cudaHostAllocDefault) != cudaSuccess) return HSR_ERR_OOM;
-        st.cap = cap;
-    }
-    if (!st.done && cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) return HSR_ERR_CUDA;
-    auto *hbuf = static_cast<unsigned char *>(st.host);
-    std::memset(hbuf, 0, off_scenes);
-    SceneDev *hs = reinterpret_cast<SceneDev *>(hbuf + off_scenes);
-    for (uint32_t i = 0; i < n_scenes; i++) hs[i] = scenes[i]->dev;
-    uint32_t *hslot = reinterpret_cast<uint32_t *>(hbuf + off_slots);
-    for (uint32_t k = 0; k <= n_slots; k++) hslot[k] = slot_item_base[k];
-    for (uint32_t k = 0; k < n_slots; k++) hslot[n_slots + 1 + k] = slot_view_base[k];
-    for (uint32_t k = 0; k < n_slots; k++) hslot[2 * n_slots + 1 + k] = slot_scene[k];
-    View *hv = reinterpret_cast<View *>(hbuf + off_views);
-    for (uint32_t k = 0; k < n; k++) {
-        const uint32_t i = order[k];
-        const uint32_t sidx = scene_of_agent ? scene_of_agent[i] : 0u;
-        View &v = hv[k];
-        std::memset(&v, 0, sizeof(View));
-        // a1: camera setup
-        if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
-        if (!snap_in_range(scenes[sidx], poses[i], *intr)) return HSR_ERR_INVALID_ARG;
-        view_planes(v.M, *intr, width, height, v.planes);
-        for (int k = 0; k < 3; k++) v.pos[k] = poses[i].pos[k];
-        v.scene = sidx;
-        v.frame = i;
-    }
 
     LaunchCfg cfg;
     if (cfg_in)
         cfg = *cfg_in;
     else
         lookup_tuned(make_key(scenes, n_scenes, n, width, height, ids != nullptr), cfg);
-    // scratch sections, each starting on a 256-byte boundary:
-    // z-buffer | visible lists | tile z | binned triangles | bin instances
-    const size_t zbytes = al((size_t)n * width * height * sizeof(unsigned long long));
-    const size_t lbytes = al(2 * (size_t)std::max<uint64_t>(list_entries, 1) * sizeof(uint2));
-    const size_t hbytes = al((size_t)n * hiz_w * hiz_h * sizeof(uint32_t));
-    const size_t rbytes = al((size_t)kBigRecCap * sizeof(BigTriStorage));
-    const size_t ibytes = al(3 * (size_t)kBigInstCap * sizeof(uint2));
-    void *dbuf = nullptr, *zbuf = nullptr;
-    cudaError_t e = cudaMallocAsync(&dbuf, total, stream);
+    Plan pl;
+    make_plan(pl, n_scenes, n, width, height, list_entries, items, cfg);
+
+    Staging &st = g_staging;
+    if (st.pending) {
+        if (cudaEventSynchronize(st.done) != cudaSuccess) return HSR_ERR_CUDA;
+        st.pending = false;
+    }
+    if (st.cap < pl.desc_bytes) {
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.cap = 0;
+        const size_t cap = std::max<size_t>(pl.desc_bytes, 64 * 1024);
+        if (cudaHostAlloc(&st.host, cap, cudaHostAllocDefault) != cudaSuccess) return HSR_ERR_OOM;
+        st.cap = cap;
+    }
+    if (!st.done && cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) return HSR_ERR_CUDA;
+    auto *hbuf = static_cast<unsigned char *>(st.host);
+    int status = fill_descriptors(pl, scenes, scene_of_agent, poses, n, nullptr, *intr, hbuf);
+    if (status != HSR_OK) return status;
+
+    void *dbuf = nullptr, *sbuf = nullptr;
+    cudaError_t e = cudaMallocAsync(&dbuf, pl.desc_bytes, stream);
     if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMallocAsync(&zbuf, zbytes + lbytes + hbytes + rbytes + ibytes, stream);
+    e = cudaMallocAsync(&sbuf, pl.scratch_bytes, stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(dbuf, stream);
         return cuda_status(e);
     }
-    e = cudaMemcpyAsync(dbuf, hbuf, total, cudaMemcpyHostToDevice, stream);
+    const Params p = make_params(pl, static_cast<unsigned char *>(dbuf), static_cast<unsigned char *>(sbuf), *intr,
+                                 rgb, depth, ids, false);
+    e = cudaMemcpyAsync(dbuf, hbuf, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(zbuf, 0xFF, zbytes, stream);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(zbuf, stream);
-        cudaFreeAsync(dbuf, stream);
-        return HSR_ERR_CUDA;
-    }
-    st.pending = true;
-
-    Params p{};
-    auto *dchar = static_cast<unsigned char *>(dbuf);
-    const uint32_t *dslot = reinterpret_cast<const uint32_t *>(dchar + off_slots);
-    p.vis_count = reinterpret_cast<uint32_t *>(dchar);
-    p.work_counter = reinterpret_cast<uint32_t *>(dchar) + 4;
-    p.vis = reinterpret_cast<uint2 *>(static_cast<unsigned char *>(zbuf) + zbytes);
-    p.vis_cap = (uint32_t)std::max<uint64_t>(list_entries, 1);
-    p.scenes = reinterpret_cast<const SceneDev *>(dchar + off_scenes);
-    p.views = reinterpret_cast<const View *>(dchar + off_views);
-    p.slot_item_base = dslot;
-    p.slot_view_base = dslot + n_slots + 1;
-    p.slot_scene = dslot + 2 * n_slots + 1;
-    p.n_slots = n_slots;
-    p.zbuf = static_cast<unsigned long long *>(zbuf);
-    p.rgb = rgb;
-    p.depth = depth;
-    p.ids = ids;
-    p.n_views = n;
-    p.width = width;
-    p.height = height;
-    p.total_items = (uint32_t)items;
-    p.fx = intr->fx; p.fy = intr->fy; p.cx = intr->cx; p.cy = intr->cy;
-    p.znear = intr->znear; p.zfar = intr->zfar;
-    p.q_far = far_threshold(intr->zfar);
-    p.small_px = std::min<uint32_t>(cfg.small_px, 32);
-    p.bin_px = cfg.bin_px;
-    p.chunk = std::min<uint32_t>(std::max<uint32_t>(cfg.chunk, 1), 32);
-    p.hiz = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes);
-    p.big_rec = reinterpret_cast<BigTri *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes + hbytes);
-    p.big_rec_cap = kBigRecCap;
-    p.big_inst = reinterpret_cast<uint2 *>(static_cast<unsigned char *>(zbuf) + zbytes + lbytes + hbytes + rbytes);
-    p.big_inst_cap = kBigInstCap;
-    p.big_rec_count = reinterpret_cast<uint32_t *>(dchar) + 8;
-    p.big_inst_count = reinterpret_cast<uint32_t *>(dchar) + 12;
-    p.hiz_w = (uint32_t)hiz_w;
-    p.hiz_h = (uint32_t)hiz_h;
-    p.n_phases = std::min<uint32_t>(std::max<uint32_t>(cfg.n_phases, 1u), 3u);
-    p.stats = stage_stats_buffer();
-    p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
-    p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
-    e = launch_render(p, cfg, stream);
-    cudaError_t e1 = cudaFreeAsync(zbuf, stream);
+    if (e == cudaSuccess) st.pending = true;
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.zbuf, 0xFF, pl.zbytes, stream);
+    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream);
+    cudaError_t e1 = cudaFreeAsync(sbuf, stream);
     cudaError_t e2 = cudaFreeAsync(dbuf, stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (e1 != cudaSuccess || e2 != cudaSuccess) return HSR_ERR_CUDA;
     return HSR_OK;
+}
+
+}  // namespace
+
+struct hsr_batch {
+    int device = 0;
+    std::vector<const hsr_scene *> scenes;
+    hsr_intrinsics intr{};
+    uint8_t *rgb = nullptr;
+    float *depth = nullptr;
+    uint32_t *ids = nullptr;
+    unsigned char *d_desc[2] = {nullptr, nullptr};
+    unsigned char *h_desc[2] = {nullptr, nullptr};
+    unsigned char *d_scratch = nullptr;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    bool launched[2] = {false, false};
+    int cur = 0;
+    Plan plan;
+    std::mutex mu;
+};
+
+namespace {
+
+// Release everything a batch holds (after synchronising its device).
+void free_batch(hsr_batch *b)
+{
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    for (int k = 0; k < 2; k++) {
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+        if (b->done[k]) cudaEventDestroy(b->done[k]);
+        if (b->d_desc[k]) cudaFree(b->d_desc[k]);
+        if (b->h_desc[k]) cudaFreeHost(b->h_desc[k]);
+    }
+    if (b->d_scratch) cudaFree(b->d_scratch);
+    cudaSetDevice(prev);
+    delete b;
 }
 
 }  // namespace
@@ -708,6 +834,95 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         return HSR_ERR_OOM;
     }
     *out = s;
+    return HSR_OK;
+}
+
+int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_cap,
+                     const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb, float *depth,
+                     uint32_t *ids, const hsr_config *cfg, hsr_batch **out)
+{
+    if (!out) return HSR_ERR_INVALID_ARG;
+    *out = nullptr;
+    hsr_pose dummy{};
+    if (!validate_common(scenes, n_scenes, &dummy, n_cap, intr, width, height, rgb, depth)) return HSR_ERR_INVALID_ARG;
+    uint64_t max_m = 0, max_g = 0;
+    for (uint32_t i = 0; i < n_scenes; i++) {
+        max_m = std::max<uint64_t>(max_m, scenes[i]->dev.n_meshlets);
+        max_g = std::max<uint64_t>(max_g, scenes[i]->dev.n_groups);
+    }
+    const uint64_t list_entries = (uint64_t)n_cap * max_m, items = (uint64_t)n_cap * max_g;
+    if (items >= 0xFFFFFFF0ull || list_entries >= 0xFFFFFFF0ull) return HSR_ERR_INVALID_ARG;
+    LaunchCfg lc;
+    if (cfg)
+        lc = from_config(*cfg);
+    else
+        lookup_tuned(make_key(scenes, n_scenes, n_cap, width, height, ids != nullptr), lc);
+    hsr_batch *b = new (std::nothrow) hsr_batch();
+    if (!b) return HSR_ERR_OOM;
+    cudaGetDevice(&b->device);
+    b->scenes.assign(scenes, scenes + n_scenes);
+    b->intr = *intr;
+    b->rgb = rgb;
+    b->depth = depth;
+    b->ids = ids;
+    Plan pl;
+    make_plan(pl, n_scenes, n_cap, width, height, list_entries, items, lc);
+    cudaError_t e = cudaSuccess;
+    cudaStream_t cs = nullptr;
+    auto fail = [&](cudaError_t err) {
+        if (cs) cudaStreamDestroy(cs);
+        free_batch(b);
+        return cuda_status(err);
+    };
+    if ((e = cudaMalloc(&b->d_scratch, pl.scratch_bytes)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(b->d_scratch + pl.z_off, 0xFF, pl.zbytes)) != cudaSuccess) return fail(e);
+    if ((e = prepare_kernels()) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    for (int k = 0; k < 2; k++) {
+        if ((e = cudaMalloc(&b->d_desc[k], pl.desc_bytes)) != cudaSuccess) return fail(e);
+        if ((e = cudaHostAlloc(&b->h_desc[k], pl.desc_bytes, cudaHostAllocDefault)) != cudaSuccess) return fail(e);
+        std::memset(b->h_desc[k], 0, pl.desc_bytes);
+        if ((e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, *intr, rgb, depth, ids, true);
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
+        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], false, cs);
+        e = cudaStreamEndCapture(cs, &b->graph[k]);
+        if (er != cudaSuccess) return fail(er);
+        if (e != cudaSuccess) return fail(e);
+        if ((e = cudaGraphInstantiate(&b->exec[k], b->graph[k], 0)) != cudaSuccess) return fail(e);
+    }
+    cudaStreamDestroy(cs);
+    cs = nullptr;
+    b->plan = pl;
+    *out = b;
+    return HSR_OK;
+}
+
+int hsr_batch_render(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
+                     const uint32_t *frames, void *cuda_stream)
+{
+    if (!b || !poses || n == 0) return HSR_ERR_INVALID_ARG;
+    const Plan &pl = b->plan;
+    if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
+    if (frames)
+        for (uint32_t i = 0; i < n; i++)
+            if (frames[i] >= pl.n_cap) return HSR_ERR_INVALID_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lock(b->mu);
+    const int k = b->cur;
+    if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
+    int st = fill_descriptors(pl, b->scenes.data(), scene_of_agent, poses, n, frames, b->intr, b->h_desc[k]);
+    if (st != HSR_OK) return st;
+    if (cudaGraphLaunch(b->exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    b->launched[k] = true;
+    b->cur ^= 1;
+    return HSR_OK;
+}
+
+int hsr_batch_destroy(hsr_batch *b)
+{
+    free_batch(b);
     return HSR_OK;
 }
 

@@ -80,9 +80,14 @@ struct Params {
     const uint32_t *slot_item_base;   // n_slots + 1
     const uint32_t *slot_view_base;   // n_slots
     const uint32_t *slot_scene;       // n_slots
-    uint32_t n_slots;
-    uint32_t n_views, width, height;
-    uint32_t total_items;      // sum over views of their scene's group count
+    uint32_t n_slots;          // capacity of the slot arrays
+    uint32_t n_views, width, height;   // n_views: capacity (frames of scratch); the active count is dyn[0]
+    uint32_t total_items;      // upper bound of the work items (grid sizing); the exact count is dyn[1]
+    // dyn[0] = active views, dyn[1] = (view, group) work items, dyn[2] = slots in use:
+    // read by the kernels from device memory, so one captured graph can replay
+    // batches of different sizes and scene mixes
+    const uint32_t *dyn;
+    uint32_t reset_zbuf;       // shade writes ~0 back to every key it reads (persistent z-buffers)
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels
@@ -128,6 +133,9 @@ struct LaunchCfg {
     uint32_t n_phases = 3;
     float phase_r[2] = {3.0f, 7.0f};
 };
+
+// Sets kernel attributes for the current device (call before stream capture).
+cudaError_t prepare_kernels();
 
 // Launches the cull, raster and shade kernels on `stream`.
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream);

@@ -110,6 +110,10 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     slot[1] = (uint32_t)items;      // slot_item_base[1]
     slot[2] = 0;                    // slot_view_base[0]
     slot[3] = 0;                    // slot_scene[0]
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(h);
+    hdr[16] = n;                    // active views
+    hdr[17] = (uint32_t)items;      // work items
+    hdr[18] = 1;                    // slots in use
     View *hv = reinterpret_cast<View *>(h + off_views);
     for (uint32_t i = 0; i < n; i++) {
         View &v = hv[i];
@@ -134,6 +138,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.slot_view_base = dslot + 2;
     p.slot_scene = dslot + 3;
     p.n_slots = 1;
+    p.dyn = reinterpret_cast<const uint32_t *>(d) + 16;
     p.views = reinterpret_cast<const View *>(d + off_views);
     p.zbuf = reinterpret_cast<unsigned long long *>(d + off_z);
     p.vis = reinterpret_cast<uint2 *>(d + off_z + zbytes);

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
     const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     ItemDecoder dec;
-    for (uint32_t item = warp_id; item < p.total_items; item += n_warps) {
+    const uint32_t total_items = p.dyn[1];
+    for (uint32_t item = warp_id; item < total_items; item += n_warps) {
         dec.locate(p, item);
         const uint32_t local = item - dec.lo;
         const uint32_t vi = dec.vbase + local / dec.G, g = local % dec.G;
@@ -328,7 +329,7 @@ __device__ __forceinline__ bool meshlet_occluded(const float *bmin, const float 
 __global__ void __launch_bounds__(256) hiz_kernel(const Params p)
 {
     const uint32_t per_view = p.hiz_w * p.hiz_h;
-    const uint32_t total = p.n_views * per_view * kHizTile;
+    const uint32_t total = p.dyn[0] * per_view * kHizTile;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ((total + 31) & ~31u);
          g += gridDim.x * blockDim.x) {
         uint32_t mx = 0;
@@ -433,7 +434,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
 {
     const uint32_t W = p.width, H = p.height;
     const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
-    const unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
+    unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
     const size_t fbase = (size_t)frame * W * H;
     const bool vec = (W % 4 == 0) && (((uintptr_t)p.rgb & 3) == 0) && (((uintptr_t)p.depth & 15) == 0) &&
                      (((uintptr_t)p.ids & 15) == 0);
@@ -447,9 +448,16 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
             const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(zb + pi);
             const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(zb + pi + 2);
             key[0] = k01.x; key[1] = k01.y; key[2] = k23.x; key[3] = k23.y;
+            if (p.reset_zbuf) {
+                *reinterpret_cast<ulonglong2 *>(zb + pi) = make_ulonglong2(~0ull, ~0ull);
+                *reinterpret_cast<ulonglong2 *>(zb + pi + 2) = make_ulonglong2(~0ull, ~0ull);
+            }
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
+            for (int k = 0; k < 4; k++) {
+                key[k] = k < (int)n ? zb[pi + k] : ~0ull;
+                if (p.reset_zbuf && k < (int)n) zb[pi + k] = ~0ull;
+            }
         }
         uint32_t rgb[4], id[4];
         float dep[4];
@@ -482,6 +490,7 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
     __shared__ SceneDev sS;
     __shared__ uint32_t s_frame;
     const uint32_t vi = view0 + blockIdx.y;
+    if (vi >= p.dyn[0]) return;
     if (threadIdx.x < 12) sM[threadIdx.x] = p.views[vi].M[threadIdx.x];
     if (threadIdx.x == 0) {
         sS = p.scenes[p.views[vi].scene];
@@ -494,6 +503,23 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
         shade_rows<3>(p, sS, sM, vi, s_frame);
     else
         shade_rows<0>(p, sS, sM, vi, s_frame);
+}
+
+constexpr size_t kRasterSmem = kRasterWarps * kMeshletVerts * (sizeof(EyeHot) + sizeof(EyeCold)) +
+                               kRasterWarps * kBigCap * sizeof(BigTri);
+
+static cudaError_t set_raster_smem_attr(int dev)
+{
+    static int attr_dev[64];
+    static bool init = false;
+    if (!init) {
+        for (int &a : attr_dev) a = 0;
+        init = true;
+    }
+    if (dev >= 0 && dev < 64 && attr_dev[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRasterSmem);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_dev[dev] = 1;
+    return e;
 }
 
 // --------------------------------------------------------------------- stage timing
@@ -573,6 +599,16 @@ static inline void mark(int k, cudaStream_t stream)
 }
 
 // --------------------------------------------------------------------- launch
+static cudaError_t set_raster_smem_attr(int dev);
+
+cudaError_t prepare_kernels()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    return set_raster_smem_attr(dev);
+}
+
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream)
 {
     int dev = 0, sms = 0;
@@ -590,14 +626,8 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         mark(1, stream);
-        constexpr size_t smem = kRasterWarps * kMeshletVerts * (sizeof(EyeHot) + sizeof(EyeCold)) +
-                                kRasterWarps * kBigCap * sizeof(BigTri);
-        static int attr_dev = -1;
-        if (attr_dev != dev) {
-            e = cudaFuncSetAttribute(raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_dev = dev;
-        }
+        e = set_raster_smem_attr(dev);
+        if (e != cudaSuccess) return e;
         const uint32_t hiz_threads = p.n_views * p.hiz_w * p.hiz_h * kHizTile;
         const uint32_t hiz_blocks = std::min<uint32_t>((hiz_threads + 255) / 256, (uint32_t)sms * 16);
         for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
@@ -606,7 +636,7 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
                 e = cudaGetLastError();
                 if (e != cudaSuccess) return e;
             }
-            raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, smem, stream>>>(p, ph);
+            raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, kRasterSmem, stream>>>(p, ph);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             if (p.big_rec) {

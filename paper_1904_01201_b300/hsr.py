@@ -81,6 +81,10 @@ def _load():
         "hsr_autotune": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P, P, U32,
                           ctypes.POINTER(hsr_config), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "hsr_set_tuned_config": ([P, U32, U32, U32, U32, ctypes.c_int, ctypes.POINTER(hsr_config)], ctypes.c_int),
+        "hsr_batch_create": ([P, U32, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
+                              ctypes.POINTER(hsr_config), ctypes.POINTER(P)], ctypes.c_int),
+        "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
+        "hsr_batch_destroy": ([P], ctypes.c_int),
         "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "hsr_version": ([], ctypes.c_char_p),
     }
@@ -250,6 +254,56 @@ def hsr_set_tuned_config(handles: Sequence[int], n, width, height, with_ids, cfg
                                    None if cfg is None else ctypes.byref(cfg))
     if st != HSR_OK:
         raise HsrError(st, "hsr_set_tuned_config")
+
+
+def hsr_batch_create(handles: Sequence[int], n_cap, intr, width, height, rgb, depth, ids=None, cfg=None) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    out = ctypes.c_void_p()
+    st = _lib.hsr_batch_create(arr, len(handles), int(n_cap), ctypes.byref(as_intrinsics(intr)), int(width),
+                               int(height), _dev_ptr(rgb), _dev_ptr(depth), _dev_ptr(ids),
+                               None if cfg is None else ctypes.byref(cfg), ctypes.byref(out))
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_batch_create")
+    return out.value
+
+
+def hsr_batch_render(batch, scene_of_agent, poses, frames=None, stream=None) -> int:
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    soa = None if scene_of_agent is None else np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+    fr = None if frames is None else np.ascontiguousarray(frames, dtype=np.uint32).reshape(-1)
+    return _lib.hsr_batch_render(ctypes.c_void_p(batch), _np_ptr(soa), _np_ptr(poses), poses.shape[0], _np_ptr(fr),
+                                 _stream_ptr(stream))
+
+
+def hsr_batch_destroy(batch) -> None:
+    _lib.hsr_batch_destroy(ctypes.c_void_p(batch))
+
+
+class Batch:
+    """A persistent graph-captured render batch bound to output tensors."""
+
+    def __init__(self, scenes, n_cap, intr, width, height, ids=True, cfg=None, device="cuda"):
+        self.scenes = list(scenes)
+        self.out = alloc_outputs(n_cap, width, height, ids, device)
+        self.handle = hsr_batch_create([s.handle for s in self.scenes], n_cap, intr, width, height,
+                                       self.out["rgb"], self.out["depth"], self.out.get("ids"), cfg)
+
+    def render(self, poses, scene_of_agent=None, frames=None, stream=None):
+        st = hsr_batch_render(self.handle, scene_of_agent, poses, frames, stream)
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_batch_render")
+        return self.out
+
+    def close(self):
+        if self.handle:
+            hsr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------- conveniences

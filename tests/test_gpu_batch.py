@@ -1,0 +1,60 @@
+"""Graph-captured persistent batch: every replay equals the one-shot render
+of the same views bit for bit (poses change between replays, fewer views than
+the capacity, mixed scenes, permuted output frames)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1904_01201_b300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_1904_01201_b300 import hsr  # noqa: E402
+from paper_1904_01201_b300 import workloads as wl  # noqa: E402
+
+
+def _np(out, sel=None):
+    torch.cuda.synchronize()
+    r = {"rgb": out["rgb"].cpu().numpy(), "depth": out["depth"].cpu().numpy(), "ids": hsr.ids_u32(out["ids"])}
+    return {k: (v if sel is None else v[sel]) for k, v in r.items()}
+
+
+def test_batch_replays_match_one_shot():
+    scenes = [wl.make_house(21, 80_000, 512), wl.make_room(22, 8000)]
+    hs = [hsr.SceneHandle(s) for s in scenes]
+    W, H, cap = 96, 80, 12
+    intr = wl.pinhole_90(W, H)
+    b = hsr.Batch(hs, cap, intr, W, H)
+    rng = np.random.default_rng(0)
+    for rep in range(4):
+        n = [cap, 7, cap, 3][rep]
+        soa = rng.integers(0, 2, n).astype(np.uint32)
+        poses = np.zeros((n, 7), np.float32)
+        for s in range(2):
+            k = int((soa == s).sum())
+            if k:
+                poses[soa == s] = wl.random_poses(scenes[s], k, 100 * rep + s)
+        frames = rng.permutation(cap)[:n].astype(np.uint32) if rep % 2 else None
+        out = b.render(poses, soa, frames)
+        got = _np(out, frames if frames is not None else np.arange(n))
+        ref = _np(hsr.render_batch(hs, soa, poses, intr, W, H))
+        for key in ref:
+            assert np.array_equal(got[key], ref[key]), (rep, key)
+    b.close()
+    for h in hs:
+        h.close()
+
+
+def test_batch_rejects_too_many_views():
+    sc = wl.make_room(3, 2000)
+    h = hsr.SceneHandle(sc)
+    b = hsr.Batch([h], 2, wl.pinhole_90(32, 32), 32, 32)
+    assert hsr.hsr_batch_render(b.handle, None, wl.random_poses(sc, 3, 0)) == hsr.HSR_ERR_OVERFLOW
+    assert hsr.hsr_batch_render(b.handle, None, wl.random_poses(sc, 2, 0), np.array([0, 5], np.uint32)) == \
+        hsr.HSR_ERR_INVALID_ARG
+    b.close()
+    h.close()
