@@ -334,7 +334,7 @@ def run_gpu(args, wk):
     acc = {"cull": 0.0, "raster": 0.0, "shade": 0.0, "total": 0.0}
     for _ in range(stage_steps):
         flush.zero_()
-        step_batched() if args.mode == "batched" else step_plain()
+        step_oneshot() if args.mode == "batched" else step_plain()   # same kernels as the graph replay
         t = hsr.hsr_get_stage_timing()
         for k in acc:
             acc[k] += t[k]
