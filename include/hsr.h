@@ -129,6 +129,63 @@ HSR_API int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes,
                      uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
 
 /*
+ * Serving (continuous batching of render requests as rollout workers step).
+ * A server keeps the scenes resident, owns a pool of output framebuffers per
+ * served square resolution (its admission budget, fb_bytes, split by
+ * res_weight), and runs a scheduler thread: submitted requests queue per
+ * resolution; a request is admitted when a framebuffer slot of its
+ * resolution is free; admitted requests of one resolution are packed into a
+ * micro-batch (<= max_batch views, waiting at most max_wait_us for more) and
+ * rendered by replaying that resolution's captured graph on one of n_streams
+ * streams, so micro-batches overlap on the device. Each request yields one
+ * result (polled), which points at its device frame until released.
+ * Results are identical to a one-shot hsr_render of the same view.
+ */
+typedef struct hsr_server hsr_server;
+typedef struct {
+    uint32_t n_res;            /* served square resolutions (1..8) */
+    uint32_t res[8];           /* side lengths in pixels */
+    float res_weight[8];       /* share of fb_bytes per resolution */
+    uint64_t fb_bytes;         /* framebuffer pool: the admission budget */
+    uint32_t max_batch;        /* views per micro-batch */
+    uint32_t n_streams;        /* micro-batches in flight */
+    uint32_t max_queue;        /* queued requests beyond this are rejected */
+    uint32_t max_wait_us;      /* a partial micro-batch waits at most this long */
+    float znear, zfar;         /* every resolution: 90 degree HFOV pinhole */
+    int with_ids;              /* also produce the id buffer */
+} hsr_server_config;
+typedef struct {
+    uint64_t tag;              /* caller's identifier, returned in the result */
+    uint32_t scene;            /* index into the server's scenes */
+    uint32_t res;              /* one of the served resolutions */
+    hsr_pose pose;
+} hsr_request;
+typedef struct {
+    uint64_t tag;
+    int status;                /* HSR_OK, HSR_ERR_OVERFLOW (queue full), HSR_ERR_INVALID_ARG, ... */
+    uint32_t res, slot;
+    uint8_t *rgb;              /* device [res][res][3] */
+    float *depth;              /* device [res][res] */
+    uint32_t *ids;             /* device [res][res] or NULL */
+    double t_submit, t_launch, t_done;   /* seconds on hsr_server_now's clock */
+} hsr_result;
+typedef struct {
+    uint64_t submitted, completed, rejected, batches;
+    uint32_t queued, in_flight;
+    uint64_t fb_bytes_used, fb_bytes_total;
+} hsr_server_stats;
+HSR_API int hsr_server_create(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_server_config *cfg,
+                              hsr_server **out);
+HSR_API int hsr_server_submit(hsr_server *server, const hsr_request *requests, uint32_t n);
+/* Completed results (up to max); waits up to wait_us for the first one. */
+HSR_API int hsr_server_poll(hsr_server *server, hsr_result *out, uint32_t max, uint32_t *n_out, uint32_t wait_us);
+/* Return the framebuffers of consumed results to the pool. */
+HSR_API int hsr_server_release(hsr_server *server, const hsr_result *results, uint32_t n);
+HSR_API int hsr_server_get_stats(hsr_server *server, hsr_server_stats *stats);
+HSR_API double hsr_server_now(void);
+HSR_API int hsr_server_destroy(hsr_server *server);
+
+/*
  * Launch configuration of the render kernels (performance only: every valid
  * configuration produces identical outputs).
  */

@@ -539,6 +539,7 @@ struct hsr_batch {
     bool launched[2] = {false, false};
     int cur = 0;
     Plan plan;
+    uint32_t n_frames = 0;
     std::mutex mu;
 };
 
@@ -837,11 +838,16 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
     return HSR_OK;
 }
 
-int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_cap,
-                     const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb, float *depth,
-                     uint32_t *ids, const hsr_config *cfg, hsr_batch **out)
+}  // extern "C"
+
+namespace hsr {
+// Batch with view capacity n_cap writing into output frames [0, n_frames).
+int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_cap, uint32_t n_frames,
+                 const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb, float *depth,
+                 uint32_t *ids, const hsr_config *cfg, hsr_batch **out)
 {
     if (!out) return HSR_ERR_INVALID_ARG;
+    if (n_frames < n_cap) return HSR_ERR_INVALID_ARG;
     *out = nullptr;
     hsr_pose dummy{};
     if (!validate_common(scenes, n_scenes, &dummy, n_cap, intr, width, height, rgb, depth)) return HSR_ERR_INVALID_ARG;
@@ -894,8 +900,19 @@ int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t
     cudaStreamDestroy(cs);
     cs = nullptr;
     b->plan = pl;
+    b->n_frames = n_frames;
     *out = b;
     return HSR_OK;
+}
+}  // namespace hsr
+
+extern "C" {
+
+int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_cap,
+                     const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb, float *depth,
+                     uint32_t *ids, const hsr_config *cfg, hsr_batch **out)
+{
+    return batch_create(scenes, n_scenes, n_cap, n_cap, intr, width, height, rgb, depth, ids, cfg, out);
 }
 
 int hsr_batch_render(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
@@ -906,7 +923,7 @@ int hsr_batch_render(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pos
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
     if (frames)
         for (uint32_t i = 0; i < n; i++)
-            if (frames[i] >= pl.n_cap) return HSR_ERR_INVALID_ARG;
+            if (frames[i] >= b->n_frames) return HSR_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     std::lock_guard<std::mutex> lock(b->mu);
     const int k = b->cur;

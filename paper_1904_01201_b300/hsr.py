@@ -54,6 +54,31 @@ class hsr_config(ctypes.Structure):
                    (ctypes.c_float * 2)(*d["phase_r"]))
 
 
+class hsr_server_config(ctypes.Structure):
+    _fields_ = [("n_res", ctypes.c_uint32), ("res", ctypes.c_uint32 * 8), ("res_weight", ctypes.c_float * 8),
+                ("fb_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
+                ("max_queue", ctypes.c_uint32), ("max_wait_us", ctypes.c_uint32), ("znear", ctypes.c_float),
+                ("zfar", ctypes.c_float), ("with_ids", ctypes.c_int)]
+
+
+class hsr_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int), ("res", ctypes.c_uint32),
+                ("slot", ctypes.c_uint32), ("rgb", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("ids", ctypes.c_void_p), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class hsr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("queued", ctypes.c_uint32), ("in_flight", ctypes.c_uint32),
+                ("fb_bytes_used", ctypes.c_uint64), ("fb_bytes_total", ctypes.c_uint64)]
+
+
+# hsr_request as a numpy record (tag, scene, res, pose[7]), 48 bytes
+REQUEST_DTYPE = np.dtype([("tag", np.uint64), ("scene", np.uint32), ("res", np.uint32), ("pose", np.float32, 7)],
+                         align=True)
+
+
 class HsrError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -85,6 +110,13 @@ def _load():
                               ctypes.POINTER(hsr_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
         "hsr_batch_destroy": ([P], ctypes.c_int),
+        "hsr_server_create": ([P, U32, ctypes.POINTER(hsr_server_config), ctypes.POINTER(P)], ctypes.c_int),
+        "hsr_server_submit": ([P, P, U32], ctypes.c_int),
+        "hsr_server_poll": ([P, P, U32, ctypes.POINTER(U32), U32], ctypes.c_int),
+        "hsr_server_release": ([P, P, U32], ctypes.c_int),
+        "hsr_server_get_stats": ([P, ctypes.POINTER(hsr_server_stats)], ctypes.c_int),
+        "hsr_server_now": ([], ctypes.c_double),
+        "hsr_server_destroy": ([P], ctypes.c_int),
         "hsr_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "hsr_version": ([], ctypes.c_char_p),
     }

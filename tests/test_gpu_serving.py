@@ -1,0 +1,109 @@
+"""Serving: every request's result equals its one-shot render bit for bit,
+alone and in the mix; admission waits for framebuffers; queue overflow and bad
+requests are reported per request."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1904_01201_b300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_1904_01201_b300 import hsr, serve  # noqa: E402
+from paper_1904_01201_b300 import workloads as wl  # noqa: E402
+
+RES = (32, 64, 96)
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    sc = [wl.make_house(31, 60_000, 512), wl.make_room(32, 6000)]
+    hs = [hsr.SceneHandle(s) for s in sc]
+    yield sc, hs
+    for h in hs:
+        h.close()
+
+
+def _requests(sc, n, seed):
+    rng = np.random.default_rng(seed)
+    req = np.zeros(n, dtype=hsr.REQUEST_DTYPE)
+    for i in range(n):
+        s = int(rng.integers(0, len(sc)))
+        req[i]["tag"] = i
+        req[i]["scene"] = s
+        req[i]["res"] = RES[int(rng.integers(0, len(RES)))]
+        req[i]["pose"] = wl.random_poses(sc[s], 1, seed * 1000 + i)[0]
+    return req
+
+
+def _collect(srv, n, with_ids, release=True):
+    got = {}
+    while len(got) < n:
+        res = srv.poll(100000)
+        assert res, "server stalled"
+        for r in res:
+            got[r.tag] = (r.status, serve.frame_tensors(r, with_ids) if r.status == 0 else None)
+        if release:
+            srv.release(res)
+    return got
+
+
+def _check_alone(sc, hs, req, got, with_ids):
+    for i, rq in enumerate(req):
+        st, fr = got[int(rq["tag"])]
+        assert st == 0
+        r = int(rq["res"])
+        ref = hsr.render(hs[int(rq["scene"])], rq["pose"][None], wl.pinhole_90(r, r), r, r, ids=with_ids)
+        torch.cuda.synchronize()
+        assert torch.equal(fr["rgb"], ref["rgb"][0]), i
+        assert torch.equal(fr["depth"], ref["depth"][0]), i
+        if with_ids:
+            assert torch.equal(fr["ids"], ref["ids"][0]), i
+
+
+def test_served_results_equal_one_shot_renders(scenes):
+    sc, hs = scenes
+    srv = serve.Server(hs, res=RES, weights=(1, 1, 1), fb_bytes=64 << 20, max_batch=8, n_streams=2,
+                       max_wait_us=100, with_ids=True)
+    req = _requests(sc, 90, 1)
+    for k in range(0, 90, 15):                 # bursts: later requests arrive while earlier ones render
+        srv.submit(req[k:k + 15])
+    got = _collect(srv, 90, True)
+    _check_alone(sc, hs, req, got, True)
+    st = srv.stats()
+    assert st["completed"] == 90 and st["rejected"] == 0 and st["fb_bytes_used"] == 0
+    assert st["batches"] >= 90 // 8
+    srv.close()
+
+
+def test_admission_waits_for_framebuffers(scenes):
+    sc, hs = scenes
+    # room for about two frames per resolution: requests wait for releases
+    srv = serve.Server(hs, res=RES, weights=(1, 1, 1), fb_bytes=3 * 2 * 96 * 96 * 7, max_batch=8, n_streams=2,
+                       max_wait_us=0, with_ids=False)
+    req = _requests(sc, 40, 2)
+    srv.submit(req)
+    got = _collect(srv, 40, False)
+    _check_alone(sc, hs, req, got, False)
+    srv.close()
+
+
+def test_queue_overflow_and_bad_requests(scenes):
+    sc, hs = scenes
+    srv = serve.Server(hs, res=RES, weights=(1, 1, 1), fb_bytes=8 << 20, max_batch=4, n_streams=1, max_queue=5,
+                       with_ids=False)
+    req = _requests(sc, 30, 3)
+    req[0]["res"] = 33                          # not served
+    srv.submit(req)
+    got = _collect(srv, 30, False)
+    statuses = [got[i][0] for i in range(30)]
+    assert statuses[0] == hsr.HSR_ERR_INVALID_ARG
+    assert statuses.count(hsr.HSR_ERR_OVERFLOW) >= 1
+    assert all(s in (0, hsr.HSR_ERR_OVERFLOW, hsr.HSR_ERR_INVALID_ARG) for s in statuses)
+    st = srv.stats()
+    assert st["rejected"] == statuses.count(hsr.HSR_ERR_OVERFLOW)
+    srv.close()
