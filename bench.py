@@ -423,13 +423,52 @@ def run_gpu(args, wk):
     return res
 
 
+def run_serving(args):
+    """Serving configuration: the batching scenes resident, requests from 1024
+    random-walking agents at resolutions 64/128/256/512 (weights
+    0.2/0.4/0.3/0.1), Poisson arrivals swept over rates; frames/s and
+    p50/p99 latency per rate."""
+    import torch
+    from paper_1904_01201_b300 import hsr, serve
+    from paper_1904_01201_b300 import workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    scenes = wl.batching_scenes(args.seed)
+    handles = [hsr.SceneHandle(s) for s in scenes]
+    srv = serve.Server(handles, res=(64, 128, 256, 512), weights=(0.2, 0.4, 0.3, 0.1), fb_bytes=4 << 30,
+                       max_batch=args.serve_batch, n_streams=args.serve_streams, max_wait_us=args.serve_wait_us)
+    rates = [float(r) for r in args.rates.split(",")]
+    rows = []
+    clk = ClockSampler()
+    for k, rate in enumerate(rates):
+        n = int(max(4000, min(22000, rate * 4)))
+        req = serve.make_requests(scenes, n, seed=args.seed + k)
+        rows.append(serve.run_load(srv, req, rate, warmup=min(2000, n // 10), seed=args.seed + k))
+    clocks = clk.stop()
+    srv.close()
+    best = max(rows, key=lambda r: r["frames_per_s"])
+    return {"metric": "served RGB-D frames/sec with p50/p99 request latency", "value": best["frames_per_s"],
+            "unit": UNIT, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/int", "data": "synthetic",
+            "config": {"workload": "serving-8scenes-1024agents-mix64-512", "tris": [int(s.n_tris) for s in scenes],
+                       "max_batch": args.serve_batch, "streams": args.serve_streams,
+                       "max_wait_us": args.serve_wait_us, "fb_bytes": 4 << 30},
+            "per_rate": [{k: v for k, v in r.items() if k != "stats"} | {"batches": r["stats"]["batches"]}
+                         for r in rows],
+            "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hsr", choices=["hsr", "reference"])
-    ap.add_argument("--workload", default="house", choices=["house", "room", "batching", "large"])
+    ap.add_argument("--workload", default="house", choices=["house", "room", "batching", "large", "serving"])
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving: request rates (1/s)")
+    ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--serve-streams", type=int, default=3)
+    ap.add_argument("--serve-wait-us", type=int, default=300)
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -441,6 +480,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "serving":
+        res = run_serving(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
     wk = make_workload(args.workload, args.seed)
     if args.agents:
         k = min(args.agents, len(wk["soa"]))
