@@ -54,7 +54,20 @@ def lib():
                                        ctypes.c_uint32, P, P, ctypes.c_uint32, P, ctypes.c_uint32,
                                        ctypes.c_uint32, P, P, P, P, ctypes.c_int]
         _lib.oracle_render.restype = ctypes.c_int
+        _lib.oracle_render_noisy.argtypes = _lib.oracle_render.argtypes + [ctypes.c_float, ctypes.c_uint64, P]
+        _lib.oracle_render_noisy.restype = ctypes.c_int
+        _lib.oracle_philox4x32_10.argtypes = [P, P, P]
+        _lib.oracle_philox4x32_10.restype = None
     return _lib
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox-4x32-10 block (Salmon et al. 2011) of a 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(2)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -72,7 +85,8 @@ def camera(pose) -> np.ndarray:
 
 
 def render(scene, poses, intr, width: int, height: int, nthreads: int = 0,
-           ids: bool = True, coverage: bool = False) -> dict:
+           ids: bool = True, coverage: bool = False, noise_sigma: float = 0.0, noise_seed: int = 0,
+           agent_ids=None) -> dict:
     """Render every pose of `poses` ([N,7]) and return numpy outputs.
 
     `scene` has attributes xyz, idx, uv, vrgb, atlas, sem (see workloads.Scene);
@@ -96,9 +110,11 @@ def render(scene, poses, intr, width: int, height: int, nthreads: int = 0,
     aw = ah = 0
     if atlas is not None:
         ah, aw = atlas.shape[0], atlas.shape[1]
-    st = lib().oracle_render(_ptr(xyz), xyz.shape[0], _ptr(idx), idx.shape[0], _ptr(uv), _ptr(vrgb),
-                             _ptr(atlas), aw, ah, _ptr(sem), _ptr(poses), n, _ptr(intr), width, height,
-                             _ptr(rgb), _ptr(depth), _ptr(out_ids), _ptr(cover), int(nthreads))
+    agents = None if agent_ids is None else np.ascontiguousarray(agent_ids, dtype=np.uint32).reshape(n)
+    st = lib().oracle_render_noisy(_ptr(xyz), xyz.shape[0], _ptr(idx), idx.shape[0], _ptr(uv), _ptr(vrgb),
+                                   _ptr(atlas), aw, ah, _ptr(sem), _ptr(poses), n, _ptr(intr), width, height,
+                                   _ptr(rgb), _ptr(depth), _ptr(out_ids), _ptr(cover), int(nthreads),
+                                   float(noise_sigma), int(noise_seed) & ((1 << 64) - 1), _ptr(agents))
     if st != OK:
         raise ValueError(f"oracle_render failed with status {st}")
     out = {"rgb": rgb, "depth": depth}

@@ -40,6 +40,13 @@
  *              vertex colours; channel = min(255, floor(c + 0.5)).
  *   outputs  : RGB u8, depth 1/q (float), id = semantic[tri] or tri;
  *              background RGB 0, depth 0, id 0xFFFFFFFF.
+ *   noise    : optional noisy depth (Appendix C: iid Gaussian, mean 0,
+ *              std sigma, added to inverse depth per pixel): for a hit pixel
+ *              q' = q + sigma z, z = sqrt(-2 ln u1) cos(2 pi u2) (fp64), with
+ *              u1, u2 from Philox-4x32-10 (Salmon et al. 2011) at counter
+ *              (pixel index, agent, 0x6e6f6973, 0) and key (seed lo, seed hi),
+ *              u = ((x >> 9) + 0.5) 2^-23; depth = 1/q', or 0 when
+ *              q' <= 1/far (no valid return).
  */
 #include <math.h>
 #include <pthread.h>
@@ -54,6 +61,30 @@
 #define OR_ERR_RANGE 3      /* a snapped coordinate left +-2^30 sub-pixels */
 
 static uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static float u2f(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+
+/* Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round
+   multiplies two counter words by fixed odd constants, mixes the high and low
+   halves with the other words and the key, and bumps the key by the Weyl
+   increments. */
+void oracle_philox4x32_10(const uint32_t *ctr_in, const uint32_t *key_in, uint32_t *out)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += W0;
+        k1 += W1;
+    }
+    for (int i = 0; i < 4; i++) out[i] = c[i];
+}
+
+static double unit_open(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 /* camera matrix from a pose (x, y, z, qw, qx, qy, qz) */
 int oracle_camera(const float *pose, float *M)
@@ -99,6 +130,10 @@ typedef struct {
     float fx, fy, cx, cy, znear, zfar;
     uint32_t W, H;
     uint8_t *rgb; float *depth; uint32_t *ids; uint32_t *cover;
+    /* depth noise */
+    float noise_sigma;
+    uint64_t noise_seed;
+    const uint32_t *agent_ids;
     /* work split */
     uint32_t f0, f1;
     int status;
@@ -312,6 +347,20 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
             }
         }
     }
+    if (J->noise_sigma > 0.0f) {
+        const uint32_t agent = J->agent_ids ? J->agent_ids[f] : f;
+        const uint32_t key[2] = {(uint32_t)J->noise_seed, (uint32_t)(J->noise_seed >> 32)};
+        for (size_t pix = 0; pix < npx; pix++) {
+            if (best[pix] == ~(uint64_t)0) continue;
+            const uint32_t ctr[4] = {(uint32_t)pix, agent, 0x6e6f6973u, 0u};
+            uint32_t r[4];
+            oracle_philox4x32_10(ctr, key, r);
+            const double z = sqrt(-2.0 * log(unit_open(r[0]))) * cos(2.0 * 3.14159265358979323846 * unit_open(r[1]));
+            const double q = (double)u2f(~(uint32_t)(best[pix] >> 32));
+            const double qn = q + (double)J->noise_sigma * z;
+            dep[pix] = qn <= 1.0 / (double)J->zfar ? 0.0f : (float)(1.0 / qn);
+        }
+    }
     return OR_OK;
 }
 
@@ -326,11 +375,27 @@ static void *worker(void *arg)
     return NULL;
 }
 
+int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
+                        const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
+                        const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
+                        uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
+                        int nthreads, float noise_sigma, uint64_t noise_seed, const uint32_t *agent_ids);
+
 int oracle_render(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
                   const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
                   const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
                   uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
                   int nthreads)
+{
+    return oracle_render_noisy(xyz, nv, idx, nt, uv, vrgb, atlas, aw, ah, sem, poses, n, intr, W, H, rgb, depth,
+                               ids, cover, nthreads, 0.0f, 0, NULL);
+}
+
+int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
+                        const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
+                        const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
+                        uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
+                        int nthreads, float noise_sigma, uint64_t noise_seed, const uint32_t *agent_ids)
 {
     if (!xyz || !idx || !poses || !intr || !rgb || !depth || n == 0 || W == 0 || H == 0) return OR_ERR_ARG;
     for (size_t i = 0; i < 3 * (size_t)nt; i++)
@@ -349,6 +414,7 @@ int oracle_render(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t n
         J->fx = intr[0]; J->fy = intr[1]; J->cx = intr[2]; J->cy = intr[3];
         J->znear = intr[4]; J->zfar = intr[5];
         J->W = W; J->H = H; J->rgb = rgb; J->depth = depth; J->ids = ids; J->cover = cover;
+        J->noise_sigma = noise_sigma; J->noise_seed = noise_seed; J->agent_ids = agent_ids;
         J->f0 = (uint32_t)((uint64_t)n * i / nthreads);
         J->f1 = (uint32_t)((uint64_t)n * (i + 1) / nthreads);
     }
