@@ -129,6 +129,36 @@ HSR_API int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes,
                      uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
 
 /*
+ * Depth-sensor noise (Appendix C, noisy-depth evaluation): iid Gaussian noise
+ * of standard deviation depth_sigma (1/m) added to the inverse depth of every
+ * covered pixel; the paper's experiment uses 0.4. Pixel p of an agent with
+ * key a draws two words of Philox-4x32-10 (Salmon et al., SC'11) at counter
+ * (p, a, 0x6e6f6973, 0) under key (seed low word, seed high word), maps each
+ * word x to u = ((x >> 9) + 0.5) * 2^-23 in (0, 1) and takes the Box-Muller
+ * variate z = sqrt(-2 ln u1) cos(2 pi u2); q' = 1/depth + depth_sigma * z.
+ * The pixel reports depth 1/q', or 0 (no return) when q' <= 1/zfar.
+ * Background pixels stay 0; colour and ids are unchanged. agent_ids: host [n]
+ * stream keys, or NULL to key each agent by its output frame. depth_sigma
+ * must be finite and >= 0 (0 = noise-free) and reserved 0, else
+ * HSR_ERR_INVALID_ARG. The struct and agent_ids are read before the call
+ * returns.
+ */
+typedef struct {
+    float depth_sigma;
+    uint32_t reserved;
+    uint64_t seed;
+    const uint32_t *agent_ids;
+} hsr_depth_noise;
+
+/* hsr_render_batch with depth noise (noise may be NULL; scene_of_agent may be
+ * NULL when n_scenes == 1). */
+HSR_API int hsr_render_noisy(const hsr_scene *const *scenes, uint32_t n_scenes,
+                     const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
+                     const hsr_intrinsics *intr, uint32_t width, uint32_t height,
+                     uint8_t *rgb, float *depth, uint32_t *ids, const hsr_depth_noise *noise,
+                     void *cuda_stream);
+
+/*
  * Serving (continuous batching of render requests as rollout workers step).
  * A server keeps the scenes resident, owns a pool of output framebuffers per
  * served square resolution (its admission budget, fb_bytes, split by
@@ -220,6 +250,12 @@ HSR_API int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, 
                              float *depth, uint32_t *ids, const hsr_config *cfg, hsr_batch **out);
 HSR_API int hsr_batch_render(hsr_batch *batch, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
                              const uint32_t *frames, void *cuda_stream);
+/* hsr_batch_render with depth noise (noise may be NULL); agents without
+ * agent_ids are keyed by their output frame. The noise settings are per
+ * replay: one captured graph serves noisy and noise-free batches. */
+HSR_API int hsr_batch_render_noisy(hsr_batch *batch, const uint32_t *scene_of_agent, const hsr_pose *poses,
+                                   uint32_t n, const uint32_t *frames, const hsr_depth_noise *noise,
+                                   void *cuda_stream);
 HSR_API int hsr_batch_destroy(hsr_batch *batch);
 
 /* Fill *cfg with the built-in default configuration. */

@@ -309,15 +309,31 @@ void make_plan(Plan &pl, uint32_t n_scenes, uint32_t n_cap, uint32_t width, uint
     pl.scratch_bytes = pl.i_off + al256(3 * (size_t)kBigInstCap * sizeof(uint2));
 }
 
+// Depth-noise request of one call: the public struct (or none) plus the
+// offset of this call's agents within the caller's (a split call renders
+// agents [agent_base, agent_base + n)).
+struct NoiseReq {
+    const hsr_depth_noise *noise = nullptr;
+    uint32_t agent_base = 0;
+};
+
+bool noise_ok(const hsr_depth_noise *nz)
+{
+    return !nz || (std::isfinite(nz->depth_sigma) && nz->depth_sigma >= 0.f && nz->reserved == 0);
+}
+
 // Camera setup of n views (a1) into the host staging buffer `hbuf`
 // (pl.desc_bytes): views sorted by scene (stable), slot arrays, scene table,
 // zeroed counters and the dynamic header words. frames[i] (or i) is the
-// output frame of agent i.
+// output frame of agent i; its depth-noise stream is keyed by
+// noise.agent_ids[i], else by agent_base + its output frame.
 int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint32_t *scene_of_agent,
                      const hsr_pose *poses, uint32_t n, const uint32_t *frames, const hsr_intrinsics &intr,
-                     unsigned char *hbuf)
+                     unsigned char *hbuf, const NoiseReq &nr = NoiseReq{})
 {
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
+    if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
+    const uint32_t *agent_ids = nr.noise ? nr.noise->agent_ids : nullptr;
     std::vector<uint32_t> order(n);
     for (uint32_t i = 0; i < n; i++) {
         order[i] = i;
@@ -354,6 +370,7 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
         for (int c = 0; c < 3; c++) v.pos[c] = poses[i].pos[c];
         v.scene = sidx;
         v.frame = frames ? frames[i] : i;
+        v.agent = agent_ids ? agent_ids[i] : nr.agent_base + v.frame;
     }
     if (items > pl.item_cap || lists > pl.list_cap) return HSR_ERR_OVERFLOW;
     hslot[n_slots] = (uint32_t)items;                      // slot_item_base[n_slots]
@@ -361,6 +378,11 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
     hdr[kHdrDyn + 0] = n;
     hdr[kHdrDyn + 1] = (uint32_t)items;
     hdr[kHdrDyn + 2] = n_slots;
+    if (nr.noise && nr.noise->depth_sigma > 0.f) {
+        std::memcpy(&hdr[kHdrDyn + 3], &nr.noise->depth_sigma, sizeof(float));
+        hdr[kHdrDyn + 4] = (uint32_t)nr.noise->seed;
+        hdr[kHdrDyn + 5] = (uint32_t)(nr.noise->seed >> 32);
+    }
     return HSR_OK;
 }
 
@@ -403,6 +425,7 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
     p.fx = intr.fx; p.fy = intr.fy; p.cx = intr.cx; p.cy = intr.cy;
     p.znear = intr.znear; p.zfar = intr.zfar;
     p.q_far = far_threshold(intr.zfar);
+    p.inv_far = (float)(1.0 / (double)intr.zfar);
     const LaunchCfg &cfg = pl.cfg;
     p.small_px = std::min<uint32_t>(std::max<uint32_t>(cfg.small_px, 1), 32);
     p.bin_px = std::max(cfg.bin_px, p.small_px);
@@ -444,9 +467,11 @@ bool validate_common(const hsr_scene *const *scenes, uint32_t n_scenes, const hs
 // stream-ordered allocator, descriptors through thread-local pinned staging.
 int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
                  const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width, uint32_t height,
-                 uint8_t *rgb, float *depth, uint32_t *ids, void *stream_ptr, const LaunchCfg *cfg_in)
+                 uint8_t *rgb, float *depth, uint32_t *ids, void *stream_ptr, const LaunchCfg *cfg_in,
+                 const NoiseReq &nr = NoiseReq{})
 {
     if (!validate_common(scenes, n_scenes, poses, n, intr, width, height, rgb, depth)) return HSR_ERR_INVALID_ARG;
+    if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
     // scratch: z-buffer (8 B / pixel / view) + visible lists (16 B per meshlet
@@ -465,11 +490,19 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         const uint32_t h = n / 2;
         const size_t px = (size_t)width * height;
         int st = render_views(scenes, n_scenes, scene_of_agent, poses, h, intr, width, height, rgb, depth, ids,
-                              stream_ptr, cfg_in);
+                              stream_ptr, cfg_in, nr);
         if (st != HSR_OK) return st;
+        hsr_depth_noise tail{};
+        NoiseReq nr2 = nr;
+        nr2.agent_base += h;
+        if (nr.noise && nr.noise->agent_ids) {
+            tail = *nr.noise;
+            tail.agent_ids += h;
+            nr2.noise = &tail;
+        }
         return render_views(scenes, n_scenes, scene_of_agent ? scene_of_agent + h : nullptr, poses + h, n - h, intr,
                             width, height, rgb + 3 * px * h, depth + px * h, ids ? ids + px * h : nullptr, stream_ptr,
-                            cfg_in);
+                            cfg_in, nr2);
     }
     if (items >= 0xFFFFFFF0ull || list_entries >= 0xFFFFFFF0ull) return HSR_ERR_INVALID_ARG;
 
@@ -496,7 +529,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     }
     if (!st.done && cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) return HSR_ERR_CUDA;
     auto *hbuf = static_cast<unsigned char *>(st.host);
-    int status = fill_descriptors(pl, scenes, scene_of_agent, poses, n, nullptr, *intr, hbuf);
+    int status = fill_descriptors(pl, scenes, scene_of_agent, poses, n, nullptr, *intr, hbuf, nr);
     if (status != HSR_OK) return status;
 
     void *dbuf = nullptr, *sbuf = nullptr;
@@ -918,7 +951,13 @@ int hsr_batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t
 int hsr_batch_render(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
                      const uint32_t *frames, void *cuda_stream)
 {
-    if (!b || !poses || n == 0) return HSR_ERR_INVALID_ARG;
+    return hsr_batch_render_noisy(b, scene_of_agent, poses, n, frames, nullptr, cuda_stream);
+}
+
+int hsr_batch_render_noisy(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
+                           const uint32_t *frames, const hsr_depth_noise *noise, void *cuda_stream)
+{
+    if (!b || !poses || n == 0 || !noise_ok(noise)) return HSR_ERR_INVALID_ARG;
     const Plan &pl = b->plan;
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
     if (frames)
@@ -928,7 +967,9 @@ int hsr_batch_render(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pos
     std::lock_guard<std::mutex> lock(b->mu);
     const int k = b->cur;
     if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
-    int st = fill_descriptors(pl, b->scenes.data(), scene_of_agent, poses, n, frames, b->intr, b->h_desc[k]);
+    NoiseReq nr;
+    nr.noise = noise;
+    int st = fill_descriptors(pl, b->scenes.data(), scene_of_agent, poses, n, frames, b->intr, b->h_desc[k], nr);
     if (st != HSR_OK) return st;
     if (cudaGraphLaunch(b->exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
@@ -1096,6 +1137,18 @@ int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes, const ui
     if (!scene_of_agent) return HSR_ERR_INVALID_ARG;
     return render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
                         cuda_stream, nullptr);
+}
+
+int hsr_render_noisy(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
+                     const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width,
+                     uint32_t height, uint8_t *rgb, float *depth, uint32_t *ids, const hsr_depth_noise *noise,
+                     void *cuda_stream)
+{
+    if (n_scenes > 1 && !scene_of_agent) return HSR_ERR_INVALID_ARG;
+    NoiseReq nr;
+    nr.noise = noise;
+    return render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
+                        cuda_stream, nullptr, nr);
 }
 
 }  // extern "C"

@@ -56,7 +56,8 @@ struct alignas(16) View {
     float pos[3];              // camera position (distance bands of the occlusion phases)
     uint32_t scene;
     uint32_t frame;
-    uint32_t pad_[3];
+    uint32_t agent;            // key of the depth-noise stream
+    uint32_t pad_[2];
 };
 
 struct Params {
@@ -83,11 +84,13 @@ struct Params {
     uint32_t n_slots;          // capacity of the slot arrays
     uint32_t n_views, width, height;   // n_views: capacity (frames of scratch); the active count is dyn[0]
     uint32_t total_items;      // upper bound of the work items (grid sizing); the exact count is dyn[1]
-    // dyn[0] = active views, dyn[1] = (view, group) work items, dyn[2] = slots in use:
+    // dyn[0] = active views, dyn[1] = (view, group) work items, dyn[2] = slots in use,
+    // dyn[3] = depth-noise sigma (float bits; 0 = noise-free), dyn[4..5] = noise seed (low, high):
     // read by the kernels from device memory, so one captured graph can replay
     // batches of different sizes and scene mixes
     const uint32_t *dyn;
     uint32_t reset_zbuf;       // shade writes ~0 back to every key it reads (persistent z-buffers)
+    float inv_far;             // 1/far: a noisy inverse depth at or below it reports depth 0
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels

@@ -165,6 +165,36 @@ __device__ __forceinline__ uint32_t shade_colour(const SceneDev &S, const float 
     return 0xFFFFFFu;
 }
 
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 products mixed with the other counter words and a key bumped by
+// Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Appendix C noise model: inverse depth plus iid Gaussian noise of std sigma
+// (Box-Muller on two Philox words at counter (pixel, agent, 'nois', 0));
+// a noisy inverse depth at or below 1/far reports no return (depth 0).
+__device__ __forceinline__ float noisy_depth(float sigma, uint32_t k0, uint32_t k1, float inv_far, float q,
+                                             uint32_t pixel, uint32_t agent)
+{
+    const uint4 r = philox4x32_10(make_uint4(pixel, agent, 0x6e6f6973u, 0u), k0, k1);
+    const float u1 = ((float)(r.x >> 9) + 0.5f) * 1.1920928955078125e-07f;   // 2^-23
+    const float u2 = ((float)(r.y >> 9) + 0.5f) * 1.1920928955078125e-07f;
+    const float z = sqrtf(-2.0f * logf(u1)) * cosf(6.283185307179586f * u2);
+    const float qn = __fmaf_rn(sigma, z, q);
+    return qn > inv_far ? __frcp_rn(qn) : 0.0f;
+}
+
 // Shade one pixel given its key; `st` caches the last triangle's setup.
 template <int NA>
 __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S, const float *M, const Params &p,

@@ -124,6 +124,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
         for (int k = 0; k < 3; k++) v.pos[k] = poses[i].pos[k];
         v.scene = 0;
         v.frame = i;
+        v.agent = i;
     }
     // Pageable source: the copy has consumed `h` when this call returns.
     if (cudaMemcpyAsync(d, h, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HSR_ERR_CUDA;
@@ -153,6 +154,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.fx = intr->fx; p.fy = intr->fy; p.cx = intr->cx; p.cy = intr->cy;
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = host_far_threshold(intr->zfar);
+    p.inv_far = (float)(1.0 / (double)intr->zfar);
     const LaunchCfg cfg{};
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
 // --------------------------------------------------------------------- shade
 template <int NA>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
-                                           uint32_t frame)
+                                           uint32_t frame, uint32_t agent)
 {
     const uint32_t W = p.width, H = p.height;
     const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
@@ -438,6 +438,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
     const size_t fbase = (size_t)frame * W * H;
     const bool vec = (W % 4 == 0) && (((uintptr_t)p.rgb & 3) == 0) && (((uintptr_t)p.depth & 15) == 0) &&
                      (((uintptr_t)p.ids & 15) == 0);
+    const float sigma = __uint_as_float(p.dyn[3]);
     ShadeTri<NA> st;
     for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < quads; qi += gridDim.x * blockDim.x) {
         const uint32_t y = qi / qpr, x0 = (qi % qpr) * 4;
@@ -463,6 +464,14 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
         float dep[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k]);
+        if (sigma > 0.f) {
+            const uint32_t k0 = p.dyn[4], k1 = p.dyn[5];
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (key[k] != ~0ull)
+                    dep[k] = noisy_depth(sigma, k0, k1, p.inv_far, __uint_as_float(~(uint32_t)(key[k] >> 32)),
+                                         (uint32_t)(pi + k), agent);
+        }
         const size_t o = fbase + pi;
         if (vec) {
             // four packed 24-bit RGB values -> three little-endian words
@@ -488,21 +497,22 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
 {
     __shared__ float sM[12];
     __shared__ SceneDev sS;
-    __shared__ uint32_t s_frame;
+    __shared__ uint32_t s_frame, s_agent;
     const uint32_t vi = view0 + blockIdx.y;
     if (vi >= p.dyn[0]) return;
     if (threadIdx.x < 12) sM[threadIdx.x] = p.views[vi].M[threadIdx.x];
     if (threadIdx.x == 0) {
         sS = p.scenes[p.views[vi].scene];
         s_frame = p.views[vi].frame;
+        s_agent = p.views[vi].agent;
     }
     __syncthreads();
     if (sS.color_mode == kColorTexture)
-        shade_rows<2>(p, sS, sM, vi, s_frame);
+        shade_rows<2>(p, sS, sM, vi, s_frame, s_agent);
     else if (sS.color_mode == kColorVertex)
-        shade_rows<3>(p, sS, sM, vi, s_frame);
+        shade_rows<3>(p, sS, sM, vi, s_frame, s_agent);
     else
-        shade_rows<0>(p, sS, sM, vi, s_frame);
+        shade_rows<0>(p, sS, sM, vi, s_frame, s_agent);
 }
 
 constexpr size_t kRasterSmem = kRasterWarps * kMeshletVerts * (sizeof(EyeHot) + sizeof(EyeCold)) +

@@ -54,6 +54,11 @@ class hsr_config(ctypes.Structure):
                    (ctypes.c_float * 2)(*d["phase_r"]))
 
 
+class hsr_depth_noise(ctypes.Structure):
+    _fields_ = [("depth_sigma", ctypes.c_float), ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("agent_ids", ctypes.c_void_p)]
+
+
 class hsr_server_config(ctypes.Structure):
     _fields_ = [("n_res", ctypes.c_uint32), ("res", ctypes.c_uint32 * 8), ("res_weight", ctypes.c_float * 8),
                 ("fb_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
@@ -110,6 +115,9 @@ def _load():
                               ctypes.POINTER(hsr_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
         "hsr_batch_destroy": ([P], ctypes.c_int),
+        "hsr_render_noisy": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
+                              ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
+        "hsr_batch_render_noisy": ([P, P, P, U32, P, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_server_create": ([P, U32, ctypes.POINTER(hsr_server_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_server_submit": ([P, P, U32], ctypes.c_int),
         "hsr_server_poll": ([P, P, U32, ctypes.POINTER(U32), U32], ctypes.c_int),
@@ -258,6 +266,31 @@ def hsr_render_batch(handles: Sequence[int], scene_of_agent, poses, intr, width,
                                  _stream_ptr(stream))
 
 
+def _noise(sigma, seed, agent_ids):
+    """(hsr_depth_noise or None, keep-alive array) for the noisy entry points."""
+    if sigma is None:
+        return None, None
+    aid = None if agent_ids is None else np.ascontiguousarray(agent_ids, dtype=np.uint32).reshape(-1)
+    nz = hsr_depth_noise(float(sigma), 0, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                         None if aid is None else aid.ctypes.data)
+    return nz, aid
+
+
+def hsr_render_noisy(handles: Sequence[int], scene_of_agent, poses, intr, width, height, rgb, depth, ids=None,
+                     noise_sigma=None, noise_seed=0, agent_ids=None, stream=None) -> int:
+    """hsr_render_batch with inverse-depth Gaussian noise (Appendix C). Returns the status."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    soa = None if scene_of_agent is None else np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+    nz, keep = _noise(noise_sigma, noise_seed, agent_ids)
+    st = _lib.hsr_render_noisy(arr, len(handles), _np_ptr(soa), _np_ptr(poses), poses.shape[0],
+                               ctypes.byref(as_intrinsics(intr)), int(width), int(height), _dev_ptr(rgb),
+                               _dev_ptr(depth), _dev_ptr(ids), None if nz is None else ctypes.byref(nz),
+                               _stream_ptr(stream))
+    del keep
+    return st
+
+
 def hsr_config_default() -> hsr_config:
     c = hsr_config()
     _lib.hsr_config_default(ctypes.byref(c))
@@ -307,6 +340,18 @@ def hsr_batch_render(batch, scene_of_agent, poses, frames=None, stream=None) -> 
                                  _stream_ptr(stream))
 
 
+def hsr_batch_render_noisy(batch, scene_of_agent, poses, frames=None, noise_sigma=None, noise_seed=0,
+                           agent_ids=None, stream=None) -> int:
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    soa = None if scene_of_agent is None else np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+    fr = None if frames is None else np.ascontiguousarray(frames, dtype=np.uint32).reshape(-1)
+    nz, keep = _noise(noise_sigma, noise_seed, agent_ids)
+    st = _lib.hsr_batch_render_noisy(ctypes.c_void_p(batch), _np_ptr(soa), _np_ptr(poses), poses.shape[0],
+                                     _np_ptr(fr), None if nz is None else ctypes.byref(nz), _stream_ptr(stream))
+    del keep
+    return st
+
+
 def hsr_batch_destroy(batch) -> None:
     _lib.hsr_batch_destroy(ctypes.c_void_p(batch))
 
@@ -320,8 +365,13 @@ class Batch:
         self.handle = hsr_batch_create([s.handle for s in self.scenes], n_cap, intr, width, height,
                                        self.out["rgb"], self.out["depth"], self.out.get("ids"), cfg)
 
-    def render(self, poses, scene_of_agent=None, frames=None, stream=None):
-        st = hsr_batch_render(self.handle, scene_of_agent, poses, frames, stream)
+    def render(self, poses, scene_of_agent=None, frames=None, stream=None, noise_sigma=None, noise_seed=0,
+               agent_ids=None):
+        if noise_sigma is None:
+            st = hsr_batch_render(self.handle, scene_of_agent, poses, frames, stream)
+        else:
+            st = hsr_batch_render_noisy(self.handle, scene_of_agent, poses, frames, noise_sigma, noise_seed,
+                                        agent_ids, stream)
         if st != HSR_OK:
             raise HsrError(st, "hsr_batch_render")
         return self.out
@@ -368,13 +418,19 @@ def alloc_outputs(n: int, width: int, height: int, ids: bool = True, device="cud
     return out
 
 
-def render(scene: SceneHandle, poses, intr, width: int, height: int, ids: bool = True, out=None, stream=None):
-    """Render poses [N,7] of one scene into (new or given) device tensors."""
+def render(scene: SceneHandle, poses, intr, width: int, height: int, ids: bool = True, out=None, stream=None,
+           noise_sigma=None, noise_seed=0, agent_ids=None):
+    """Render poses [N,7] of one scene into (new or given) device tensors;
+    noise_sigma adds inverse-depth Gaussian noise to the depth (Appendix C)."""
     poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
     out = out or alloc_outputs(poses.shape[0], width, height, ids)
-    st = hsr_render(scene.handle, poses, intr, width, height, out["rgb"], out["depth"], out.get("ids"), stream)
+    if noise_sigma is None:
+        st = hsr_render(scene.handle, poses, intr, width, height, out["rgb"], out["depth"], out.get("ids"), stream)
+    else:
+        st = hsr_render_noisy([scene.handle], None, poses, intr, width, height, out["rgb"], out["depth"],
+                              out.get("ids"), noise_sigma, noise_seed, agent_ids, stream)
     if st != HSR_OK:
-        raise HsrError(st, "hsr_render")
+        raise HsrError(st, "hsr_render_noisy" if noise_sigma is not None else "hsr_render")
     return out
 
 
