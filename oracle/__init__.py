@@ -58,6 +58,9 @@ def lib():
         _lib.oracle_render_noisy.restype = ctypes.c_int
         _lib.oracle_philox4x32_10.argtypes = [P, P, P]
         _lib.oracle_philox4x32_10.restype = None
+        _lib.oracle_actuate.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, P, P]
+        _lib.oracle_actuate.restype = ctypes.c_int
     return _lib
 
 
@@ -72,6 +75,25 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+STOP, MOVE_FORWARD, TURN_LEFT, TURN_RIGHT = 0, 1, 2, 3
+
+
+def actuate(pose, action: int, navmap, step: float = 0.25, turn_deg: float = 10.0):
+    """Pose after one action (Sec. 4 action space) on a navigability grid.
+
+    navmap: (x0, z0, cell, grid [nz, nx] uint8).  Returns (new pose [7]
+    float32, moved: bool)."""
+    p = np.ascontiguousarray(pose, dtype=np.float32).reshape(7)
+    x0, z0, cell, grid = navmap
+    g = np.ascontiguousarray(grid, dtype=np.uint8)
+    out = np.zeros(7, dtype=np.float32)
+    st = lib().oracle_actuate(_ptr(p), int(action), float(step), float(turn_deg), float(x0), float(z0),
+                              float(cell), g.shape[1], g.shape[0], _ptr(g), _ptr(out))
+    if st < 0 or st > 1:
+        raise ValueError("unknown action")
+    return out, bool(st)
 
 
 def camera(pose) -> np.ndarray:

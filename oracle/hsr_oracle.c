@@ -112,6 +112,65 @@ int oracle_camera(const float *pose, float *M)
     return OR_OK;
 }
 
+/*
+ * Agent actuation (Sec. 4 "Agent embodiment and action space": stop,
+ * move_forward 0.25 m, turn_left / turn_right 10 degrees, idealised, no
+ * actuation noise).  Readings, all arithmetic in double from the float state,
+ * each pose component rounded once to float at the end:
+ *   stop    : the pose is unchanged.
+ *   forward : heading = R (0, 0, -1) of the normalised quaternion with its
+ *             vertical component dropped: h = (-2(xz + wy), -(1 - 2(x^2 + y^2)));
+ *             p' = p + step * h / |h| on x and z (y unchanged), rounded to
+ *             float; refused (pose unchanged) when |h| = 0 or when the grid
+ *             cell holding the rounded p' is not navigable: cell
+ *             (floor((x - x0)/cell), floor((z - z0)/cell)), outside the grid
+ *             counts as blocked (no sliding along obstacles).
+ *   turn    : q' = r * q with r = (cos(t/2), 0, sin(t/2), 0) about world +Y,
+ *             t = +turn for left, -turn for right (degrees * pi / 180), then
+ *             q' / |q'|.  Products and sums in the order written below.
+ * grid: [nz][nx] bytes, nonzero = navigable.  Returns 1 if the pose moved or
+ * turned, 0 if unchanged, -1 for an unknown action.
+ */
+int oracle_actuate(const float *pose, int action, double step, double turn_deg, float x0, float z0, float cell,
+                   uint32_t nx, uint32_t nz, const uint8_t *grid, float *out)
+{
+    memcpy(out, pose, 7 * sizeof(float));
+    double w = pose[3], x = pose[4], y = pose[5], z = pose[6];
+    const double n = sqrt(((w * w + x * x) + y * y) + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    if (action == 0) return 0;
+    if (action == 1) {
+        const double hx = -2.0 * (x * z + w * y);
+        const double hz = -(1.0 - 2.0 * (x * x + y * y));
+        const double len = sqrt(hx * hx + hz * hz);
+        if (!(len > 0.0)) return 0;
+        const float nxp = (float)((double)pose[0] + step * (hx / len));
+        const float nzp = (float)((double)pose[2] + step * (hz / len));
+        const double ci = floor(((double)nxp - (double)x0) / (double)cell);
+        const double ck = floor(((double)nzp - (double)z0) / (double)cell);
+        if (!(ci >= 0.0 && ci < (double)nx && ck >= 0.0 && ck < (double)nz)) return 0;
+        if (!grid[(size_t)ck * nx + (size_t)ci]) return 0;
+        out[0] = nxp;
+        out[2] = nzp;
+        return 1;
+    }
+    if (action == 2 || action == 3) {
+        const double t = (action == 2 ? turn_deg : -turn_deg) * (3.14159265358979323846 / 180.0);
+        const double c = cos(0.5 * t), s = sin(0.5 * t);
+        const double w2 = c * w - s * y;
+        const double x2 = c * x + s * z;
+        const double y2 = c * y + s * w;
+        const double z2 = c * z - s * x;
+        const double n2 = sqrt(((w2 * w2 + x2 * x2) + y2 * y2) + z2 * z2);
+        out[3] = (float)(w2 / n2);
+        out[4] = (float)(x2 / n2);
+        out[5] = (float)(y2 / n2);
+        out[6] = (float)(z2 / n2);
+        return 1;
+    }
+    return -1;
+}
+
 typedef struct {
     float xe, ye, d;        /* eye space, d = -z_e */
     uint32_t vid;           /* caller's vertex index (clip ordering) */

@@ -621,6 +621,42 @@ def random_poses(scene: Scene, n: int, seed: int = 0) -> np.ndarray:
     return out.astype(np.float32)
 
 
+def navmap(scene: Scene, cell: float = 0.05, clear: float = AGENT_RADIUS):
+    """Top-down navigability grid of a scene: (x0, z0, cell, grid [nz, nx] u8),
+    grid cell (i, k) covering [x0 + i cell, x0 + (i+1) cell) x [z0 + k cell, ...)
+    is 1 iff its centre is free floor with `clear` metres to every wall and
+    obstacle footprint (the agent cylinder of Sec. 4 fits there)."""
+    r = np.array(scene.rooms, dtype=np.float64).reshape(-1, 4)
+    x0, z0 = float(np.floor(r[:, 0].min())), float(np.floor(r[:, 1].min()))
+    nx = int(math.ceil((r[:, 2].max() - x0) / cell)) + 1
+    nz = int(math.ceil((r[:, 3].max() - z0) / cell)) + 1
+    xc = x0 + (np.arange(nx) + 0.5) * cell
+    zc = z0 + (np.arange(nz) + 0.5) * cell
+    X, Z = np.meshgrid(xc, zc)
+    free = np.zeros(X.shape, dtype=bool)
+    for (a, b, c, d) in scene.rooms:
+        free |= (X >= a + clear) & (X <= c - clear) & (Z >= b + clear) & (Z <= d - clear)
+    for (a, b, c, d) in scene.boxes:
+        free &= ~((X >= a - clear) & (X <= c + clear) & (Z >= b - clear) & (Z <= d + clear))
+    for (cx, cz, rr) in scene.circles:
+        free &= (X - cx) ** 2 + (Z - cz) ** 2 > (rr + clear) ** 2
+    return np.float32(x0), np.float32(z0), np.float32(cell), free.astype(np.uint8)
+
+
+def navigable_poses(scene: Scene, nav, n: int, seed: int = 0) -> np.ndarray:
+    """[n,7] float32 poses at camera height on navigable cells of `nav`, yaw uniform."""
+    x0, z0, cell, grid = nav
+    rs = Stream(seed, "navposes-" + scene.name)
+    ks, iis = np.nonzero(grid)
+    pick = rs.integers(n, 0, len(ks))
+    out = np.zeros((n, 7), dtype=np.float64)
+    out[:, 0] = float(x0) + (iis[pick] + 0.5) * float(cell)
+    out[:, 1] = CAMERA_HEIGHT
+    out[:, 2] = float(z0) + (ks[pick] + 0.5) * float(cell)
+    out[:, 3:] = yaw_quat(rs.uniform(n, 0.0, 2 * math.pi))
+    return out.astype(np.float32)
+
+
 class RandomWalk:
     """Agents stepping with move_forward 0.25 m / turn_left 10 deg / turn_right 10 deg,
     chosen uniformly; forward moves that leave free space are refused (no sliding)."""
