@@ -258,6 +258,66 @@ HSR_API int hsr_batch_render_noisy(hsr_batch *batch, const uint32_t *scene_of_ag
                                    void *cuda_stream);
 HSR_API int hsr_batch_destroy(hsr_batch *batch);
 
+/*
+ * Agents with device-resident state (Sec. 4 "Agent embodiment and action
+ * space": the agent acts with stop, move_forward, turn_left, turn_right,
+ * mapped to idealised actuations of 0.25 m and 10 degrees). A step batch
+ * takes one action per agent instead of a pose: a pass on the device moves
+ * each agent's pose and builds its camera, then the render runs; the host
+ * sends only action ids.
+ *
+ * Actuation rules (double arithmetic from the float pose, each stored
+ * component rounded once to float):
+ *   stop         : pose unchanged (the observation is rendered again).
+ *   move_forward : heading = R (0, 0, -1) of the normalised quaternion with its
+ *                  vertical part dropped, h = (-2(xz + wy), -(1 - 2(x^2 + y^2)));
+ *                  p' = p + forward_m * h / |h| on x and z, rounded to float.
+ *                  Refused (pose unchanged; no sliding) when |h| = 0 or the
+ *                  grid cell (floor((x - x0)/cell), floor((z - z0)/cell)) of
+ *                  p' is outside the grid or not navigable.
+ *   turn_left / turn_right : q' = r q with r = (cos(t/2), 0, sin(t/2), 0),
+ *                  t = +turn_deg / -turn_deg (about world +Y), then q' / |q'|.
+ *
+ * hsr_agents_create: scenes [n_scenes] (the same array, in the same order, as
+ * the batches that step these agents), navmaps [n_scenes] (grid: host
+ * [nz][nx] bytes, nonzero = navigable, copied; the grid's x/z extent must lie
+ * inside the scene's bounding box), scene_of_agent [n_agents] (NULL: scene 0),
+ * poses [n_agents]: valid camera poses (unit quaternion within 1e-3) on
+ * navigable cells with y inside the scene's bounding box; act NULL means
+ * 0.25 m and 10 degrees. Errors: HSR_ERR_INVALID_ARG for any violation,
+ * HSR_ERR_OOM, HSR_ERR_CUDA. The state lives on the device current at create.
+ * hsr_agents_get_poses copies all poses to host [n_agents] after the work
+ * queued on cuda_stream (it waits for that stream).
+ * hsr_agents_set_poses overwrites agents idx [n] (host) with poses [n] under
+ * the create-time rules, ordered on cuda_stream.
+ * hsr_batch_step: agent_idx [n] distinct agents (< n_agents), actions [n]
+ * (hsr_action), frames [n] output frames or NULL for 0..n-1, noise as for
+ * hsr_batch_render_noisy (streams keyed by the output frame unless
+ * agent_ids are given). The batch and the agents must have the same scenes
+ * and device. Steps that touch the same agent must be ordered on the GPU.
+ */
+enum { HSR_ACTION_STOP = 0, HSR_ACTION_MOVE_FORWARD = 1, HSR_ACTION_TURN_LEFT = 2, HSR_ACTION_TURN_RIGHT = 3 };
+typedef struct {
+    float x0, z0;          /* world x, z of the grid's corner: cell (0, 0) covers [x0, x0 + cell) x [z0, z0 + cell) */
+    float cell;            /* cell edge, metres (> 0) */
+    uint32_t nx, nz;       /* grid size (>= 1 each) */
+    const uint8_t *grid;   /* host [nz][nx] */
+} hsr_navmap;
+typedef struct {
+    float forward_m;       /* move_forward displacement, metres (finite, >= 0) */
+    float turn_deg;        /* turn angle, degrees (finite) */
+} hsr_actuation;
+typedef struct hsr_agents hsr_agents;
+HSR_API int hsr_agents_create(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_navmap *navmaps,
+                              uint32_t n_agents, const uint32_t *scene_of_agent, const hsr_pose *poses,
+                              const hsr_actuation *act, hsr_agents **out);
+HSR_API int hsr_agents_get_poses(hsr_agents *agents, hsr_pose *poses, void *cuda_stream);
+HSR_API int hsr_agents_set_poses(hsr_agents *agents, const uint32_t *idx, const hsr_pose *poses, uint32_t n,
+                                 void *cuda_stream);
+HSR_API int hsr_agents_destroy(hsr_agents *agents);
+HSR_API int hsr_batch_step(hsr_batch *batch, hsr_agents *agents, const uint32_t *agent_idx, const uint8_t *actions,
+                           uint32_t n, const uint32_t *frames, const hsr_depth_noise *noise, void *cuda_stream);
+
 /* Fill *cfg with the built-in default configuration. */
 HSR_API int hsr_config_default(hsr_config *cfg);
 

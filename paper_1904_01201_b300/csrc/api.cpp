@@ -17,6 +17,7 @@
 
 #include <cuda_runtime.h>
 
+#include "camera.h"
 #include "hsr_internal.h"
 
 using namespace hsr;
@@ -33,7 +34,6 @@ struct hsr_scene {
 namespace {
 
 constexpr double kCoordLimit = 1048576.0;       // |vertex coordinate| <= 2^20
-constexpr double kSnapLimit = 1073741824.0;     // |snapped coordinate| < 2^30
 
 bool finite3(const float *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
@@ -80,33 +80,7 @@ uint64_t spread21(uint64_t x)
 
 // Camera matrix (reading of Sec. 4 "Sensory input": a pinhole sensor at the
 // agent pose). Double precision, fixed operation order, rounded once to float.
-bool camera_matrix(const hsr_pose &pose, float M[12])
-{
-    for (int i = 0; i < 3; i++)
-        if (!std::isfinite(pose.pos[i])) return false;
-    for (int i = 0; i < 4; i++)
-        if (!std::isfinite(pose.quat[i])) return false;
-    double w = pose.quat[0], x = pose.quat[1], y = pose.quat[2], z = pose.quat[3];
-    const double n = std::sqrt(((w * w + x * x) + y * y) + z * z);
-    if (!(std::fabs(n - 1.0) <= 1e-3)) return false;
-    w /= n; x /= n; y /= n; z /= n;
-    double R[3][3];
-    R[0][0] = 1.0 - 2.0 * (y * y + z * z);
-    R[0][1] = 2.0 * (x * y - w * z);
-    R[0][2] = 2.0 * (x * z + w * y);
-    R[1][0] = 2.0 * (x * y + w * z);
-    R[1][1] = 1.0 - 2.0 * (x * x + z * z);
-    R[1][2] = 2.0 * (y * z - w * x);
-    R[2][0] = 2.0 * (x * z - w * y);
-    R[2][1] = 2.0 * (y * z + w * x);
-    R[2][2] = 1.0 - 2.0 * (x * x + y * y);
-    const double px = pose.pos[0], py = pose.pos[1], pz = pose.pos[2];
-    for (int i = 0; i < 3; i++) {
-        for (int j = 0; j < 3; j++) M[i * 4 + j] = (float)R[j][i];
-        M[i * 4 + 3] = (float)(-((R[0][i] * px + R[1][i] * py) + R[2][i] * pz));
-    }
-    return true;
-}
+bool camera_matrix(const hsr_pose &pose, float M[12]) { return camera_from_pose(pose.pos, pose.quat, M); }
 
 bool intrinsics_ok(const hsr_intrinsics *in)
 {
@@ -137,21 +111,7 @@ float far_threshold(float zfar)
 // box corner and d >= near.
 bool snap_in_range(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in)
 {
-    double r2 = 0.0;
-    for (int c = 0; c < 8; c++) {
-        double d2 = 0.0;
-        for (int k = 0; k < 3; k++) {
-            const double v = (c >> k) & 1 ? s->info.aabb_max[k] : s->info.aabb_min[k];
-            const double dd = v - (double)pose.pos[k];
-            d2 += dd * dd;
-        }
-        r2 = std::max(r2, d2);
-    }
-    const double R = std::sqrt(r2) * (1.0 + 1e-6) + 1e-6;
-    const double f = std::max((double)in.fx, (double)in.fy);
-    const double c = std::max(std::fabs((double)in.cx), std::fabs((double)in.cy));
-    const double bound = 256.0 * (f * R / (double)in.znear + c + 2.0);
-    return bound < kSnapLimit;
+    return snap_bound_ok(s->info.aabb_min, s->info.aabb_max, pose.pos, in.fx, in.fy, in.cx, in.cy, in.znear);
 }
 
 struct Staging {
@@ -168,36 +128,11 @@ struct Staging {
 };
 thread_local Staging g_staging;
 
-// World-space culling planes of a view (n . p + off >= 0 inside), double
-// precision from the float matrix: the image borders pushed out by
-// kPlaneMarginPx pixels, and the near / far planes pushed out by
-// kPlaneMarginDepth metres, so culling only removes geometry that cannot
-// produce a sample.
-constexpr double kPlaneMarginPx = 2.0;
-constexpr double kPlaneMarginDepth = 1e-4;
 constexpr uint64_t kMaxScratchBytes = 2ull << 30;
 
 void view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32_t H, float planes[24])
 {
-    const double m = kPlaneMarginPx;
-    const double fx = in.fx, fy = in.fy, cx = in.cx, cy = in.cy;
-    const double ne[6][3] = {{fx, 0, -(cx + m)},
-                             {-fx, 0, -((double)W + m - cx)},
-                             {0, -fy, -(cy + m)},
-                             {0, fy, -((double)H + m - cy)},
-                             {0, 0, -1},
-                             {0, 0, 1}};
-    const double oe[6] = {0, 0, 0, 0, -((double)in.znear - kPlaneMarginDepth), (double)in.zfar + kPlaneMarginDepth};
-    for (int k = 0; k < 6; k++) {
-        for (int j = 0; j < 3; j++) {
-            double n = 0;
-            for (int i = 0; i < 3; i++) n += (double)M[i * 4 + j] * ne[k][i];
-            planes[4 * k + j] = (float)n;
-        }
-        double off = oe[k];
-        for (int i = 0; i < 3; i++) off += (double)M[i * 4 + 3] * ne[k][i];
-        planes[4 * k + 3] = (float)off;
-    }
+    frustum_planes(M, in.fx, in.fy, in.cx, in.cy, in.znear, in.zfar, W, H, planes);
 }
 
 // ------------------------------------------------------------ tuned configs
@@ -317,6 +252,14 @@ struct NoiseReq {
     uint32_t agent_base = 0;
 };
 
+// Step batches: each view names an agent-state slot and an action; the
+// actuation pass on the device sets up its camera.
+struct StepReq {
+    const uint32_t *state = nullptr;
+    const uint8_t *action = nullptr;
+    uint64_t agents_dev = 0;         // device address of the AgentsDev
+};
+
 bool noise_ok(const hsr_depth_noise *nz)
 {
     return !nz || (std::isfinite(nz->depth_sigma) && nz->depth_sigma >= 0.f && nz->reserved == 0);
@@ -329,7 +272,7 @@ bool noise_ok(const hsr_depth_noise *nz)
 // noise.agent_ids[i], else by agent_base + its output frame.
 int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint32_t *scene_of_agent,
                      const hsr_pose *poses, uint32_t n, const uint32_t *frames, const hsr_intrinsics &intr,
-                     unsigned char *hbuf, const NoiseReq &nr = NoiseReq{})
+                     unsigned char *hbuf, const NoiseReq &nr = NoiseReq{}, const StepReq *step = nullptr)
 {
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
     if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
@@ -364,10 +307,15 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
         lists += scenes[sidx]->dev.n_meshlets;
         View &v = hv[k];
         std::memset(&v, 0, sizeof(View));
-        if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
-        if (!snap_in_range(scenes[sidx], poses[i], intr)) return HSR_ERR_INVALID_ARG;
-        view_planes(v.M, intr, pl.width, pl.height, v.planes);
-        for (int c = 0; c < 3; c++) v.pos[c] = poses[i].pos[c];
+        if (step) {
+            v.state = step->state[i];
+            v.action = step->action[i];
+        } else {
+            if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
+            if (!snap_in_range(scenes[sidx], poses[i], intr)) return HSR_ERR_INVALID_ARG;
+            view_planes(v.M, intr, pl.width, pl.height, v.planes);
+            for (int c = 0; c < 3; c++) v.pos[c] = poses[i].pos[c];
+        }
         v.scene = sidx;
         v.frame = frames ? frames[i] : i;
         v.agent = agent_ids ? agent_ids[i] : nr.agent_base + v.frame;
@@ -378,6 +326,10 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
     hdr[kHdrDyn + 0] = n;
     hdr[kHdrDyn + 1] = (uint32_t)items;
     hdr[kHdrDyn + 2] = n_slots;
+    if (step) {
+        hdr[kHdrDyn + 6] = (uint32_t)step->agents_dev;
+        hdr[kHdrDyn + 7] = (uint32_t)(step->agents_dev >> 32);
+    }
     if (nr.noise && nr.noise->depth_sigma > 0.f) {
         std::memcpy(&hdr[kHdrDyn + 3], &nr.noise->depth_sigma, sizeof(float));
         hdr[kHdrDyn + 4] = (uint32_t)nr.noise->seed;
@@ -441,10 +393,14 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
 // Stream work of one render: upload descriptors, optionally preset the
 // z-buffer, launch the kernels.
 cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const void *h_desc, bool preset_z,
-                           cudaStream_t stream)
+                           cudaStream_t stream, bool actuate = false)
 {
     cudaError_t e = cudaMemcpyAsync(d_desc, h_desc, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return e;
+    if (actuate) {
+        e = launch_actuate(p, pl.n_cap, stream);
+        if (e != cudaSuccess) return e;
+    }
     if (preset_z) {
         e = cudaMemsetAsync(p.zbuf, 0xFF, pl.zbytes, stream);
         if (e != cudaSuccess) return e;
@@ -568,6 +524,8 @@ struct hsr_batch {
     unsigned char *d_scratch = nullptr;
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaGraph_t step_graph[2] = {nullptr, nullptr};      // upload, actuation, render (captured on first step)
+    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool launched[2] = {false, false};
     int cur = 0;
@@ -589,6 +547,8 @@ void free_batch(hsr_batch *b)
     for (int k = 0; k < 2; k++) {
         if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
         if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+        if (b->step_exec[k]) cudaGraphExecDestroy(b->step_exec[k]);
+        if (b->step_graph[k]) cudaGraphDestroy(b->step_graph[k]);
         if (b->done[k]) cudaEventDestroy(b->done[k]);
         if (b->d_desc[k]) cudaFree(b->d_desc[k]);
         if (b->h_desc[k]) cudaFreeHost(b->h_desc[k]);
@@ -972,6 +932,70 @@ int hsr_batch_render_noisy(hsr_batch *b, const uint32_t *scene_of_agent, const h
     int st = fill_descriptors(pl, b->scenes.data(), scene_of_agent, poses, n, frames, b->intr, b->h_desc[k], nr);
     if (st != HSR_OK) return st;
     if (cudaGraphLaunch(b->exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    b->launched[k] = true;
+    b->cur ^= 1;
+    return HSR_OK;
+}
+
+int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, const uint8_t *actions, uint32_t n,
+                   const uint32_t *frames, const hsr_depth_noise *noise, void *cuda_stream)
+{
+    AgentsView av{};
+    if (!b || !agent_idx || !actions || n == 0 || !noise_ok(noise) || !agents_view(agents, av))
+        return HSR_ERR_INVALID_ARG;
+    const Plan &pl = b->plan;
+    if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
+    if (av.device != b->device || av.n_scenes != b->scenes.size()) return HSR_ERR_INVALID_ARG;
+    for (uint32_t s = 0; s < av.n_scenes; s++) {
+        if (av.scenes[s] != b->scenes[s]) return HSR_ERR_INVALID_ARG;
+        // agents stay inside their scene's box: a camera at one corner sees
+        // the farthest corner at the largest possible distance
+        const hsr_scene_info &in = av.info[s];
+        if (!snap_bound_ok(in.aabb_min, in.aabb_max, in.aabb_min, b->intr.fx, b->intr.fy, b->intr.cx, b->intr.cy,
+                           b->intr.znear))
+            return HSR_ERR_INVALID_ARG;
+    }
+    std::vector<uint32_t> soa(n), sorted(agent_idx, agent_idx + n);
+    for (uint32_t i = 0; i < n; i++) {
+        if (agent_idx[i] >= av.n_agents || actions[i] > HSR_ACTION_TURN_RIGHT) return HSR_ERR_INVALID_ARG;
+        if (frames && frames[i] >= b->n_frames) return HSR_ERR_INVALID_ARG;
+        soa[i] = av.scene_of_agent[agent_idx[i]];
+    }
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return HSR_ERR_INVALID_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lock(b->mu);
+    const int k = b->cur;
+    if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
+    if (!b->step_exec[k]) {
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSR_ERR_CUDA;
+        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, b->intr, b->rgb, b->depth, b->ids, true);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], false, cs, true);
+            e = cudaStreamEndCapture(cs, &b->step_graph[k]);
+            if (er != cudaSuccess) e = er;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->step_exec[k], b->step_graph[k], 0);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            if (b->step_graph[k]) cudaGraphDestroy(b->step_graph[k]);
+            b->step_graph[k] = nullptr;
+            b->step_exec[k] = nullptr;
+            return cuda_status(e);
+        }
+    }
+    NoiseReq nr;
+    nr.noise = noise;
+    StepReq sr;
+    sr.state = agent_idx;
+    sr.action = actions;
+    sr.agents_dev = (uint64_t)(uintptr_t)av.dev;
+    int st = fill_descriptors(pl, b->scenes.data(), soa.data(), nullptr, n, frames, b->intr, b->h_desc[k], nr, &sr);
+    if (st != HSR_OK) return st;
+    if (cudaGraphLaunch(b->step_exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
     b->cur ^= 1;

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/hsr.h"
+
 namespace hsr {
 
 // Meshlets: up to 32 triangles and 64 distinct vertices, spatially coherent
@@ -57,7 +59,30 @@ struct alignas(16) View {
     uint32_t scene;
     uint32_t frame;
     uint32_t agent;            // key of the depth-noise stream
-    uint32_t pad_[2];
+    uint32_t state;            // agent-state slot moved by the actuation pass (step batches)
+    uint32_t action;           // action applied to that slot first (hsr_action)
+};
+
+static_assert(sizeof(View) == 176, "View is 11 x 16 bytes");
+
+// Navigability grid of one scene on the device, with the scene's bounding box
+// (the fixed-point range check of a moved camera).
+struct NavDev {
+    float x0, z0, cell;
+    uint32_t nx, nz, pad_;
+    const uint8_t *grid;       // [nz][nx], nonzero = navigable
+    float amin[3], amax[3];
+};
+
+// Device-resident agents: poses, per-scene grids, actuation amounts. Its
+// device address sits in the descriptor header (dyn[6], dyn[7]) of a step
+// batch, so one captured graph serves any agent set.
+struct AgentsDev {
+    float *pose;               // [n_agents][7]: x, y, z, qw, qx, qy, qz
+    const NavDev *nav;         // [n_scenes]
+    uint32_t n_agents, n_scenes;
+    double step;               // forward displacement, metres
+    double c_turn[2], s_turn[2];   // cos, sin of half the left [0] / right [1] turn angle
 };
 
 struct Params {
@@ -85,7 +110,8 @@ struct Params {
     uint32_t n_views, width, height;   // n_views: capacity (frames of scratch); the active count is dyn[0]
     uint32_t total_items;      // upper bound of the work items (grid sizing); the exact count is dyn[1]
     // dyn[0] = active views, dyn[1] = (view, group) work items, dyn[2] = slots in use,
-    // dyn[3] = depth-noise sigma (float bits; 0 = noise-free), dyn[4..5] = noise seed (low, high):
+    // dyn[3] = depth-noise sigma (float bits; 0 = noise-free), dyn[4..5] = noise seed (low, high),
+    // dyn[6..7] = device address of the AgentsDev of a step batch (low, high):
     // read by the kernels from device memory, so one captured graph can replay
     // batches of different sizes and scene mixes
     const uint32_t *dyn;
@@ -142,6 +168,21 @@ cudaError_t prepare_kernels();
 
 // Launches the cull, raster and shade kernels on `stream`.
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream);
+// What a step batch needs to know about an agent set (agents.cpp).
+struct AgentsView {
+    int device;
+    const hsr_scene *const *scenes;
+    uint32_t n_scenes;
+    const uint32_t *scene_of_agent;    // [n_agents]
+    uint32_t n_agents;
+    const AgentsDev *dev;              // device address
+    const hsr_scene_info *info;        // [n_scenes]
+};
+bool agents_view(const hsr_agents *a, AgentsView &out);
+
+// Actuation pass of a step batch: applies each view's action to its agent
+// state and writes the view's camera (n_cap: capacity, the grid size).
+cudaError_t launch_actuate(const Params &p, uint32_t n_cap, cudaStream_t stream);
 
 // Stage timing (diagnostic): events around cull / raster / shade.
 cudaError_t stage_timing_enable(bool on);

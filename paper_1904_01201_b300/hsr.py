@@ -59,6 +59,18 @@ class hsr_depth_noise(ctypes.Structure):
                 ("agent_ids", ctypes.c_void_p)]
 
 
+class hsr_navmap(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_float), ("z0", ctypes.c_float), ("cell", ctypes.c_float), ("nx", ctypes.c_uint32),
+                ("nz", ctypes.c_uint32), ("grid", ctypes.c_void_p)]
+
+
+class hsr_actuation(ctypes.Structure):
+    _fields_ = [("forward_m", ctypes.c_float), ("turn_deg", ctypes.c_float)]
+
+
+HSR_ACTION_STOP, HSR_ACTION_MOVE_FORWARD, HSR_ACTION_TURN_LEFT, HSR_ACTION_TURN_RIGHT = 0, 1, 2, 3
+
+
 class hsr_server_config(ctypes.Structure):
     _fields_ = [("n_res", ctypes.c_uint32), ("res", ctypes.c_uint32 * 8), ("res_weight", ctypes.c_float * 8),
                 ("fb_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32), ("n_streams", ctypes.c_uint32),
@@ -115,6 +127,12 @@ def _load():
                               ctypes.POINTER(hsr_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
         "hsr_batch_destroy": ([P], ctypes.c_int),
+        "hsr_agents_create": ([P, U32, P, U32, P, P, ctypes.POINTER(hsr_actuation), ctypes.POINTER(P)],
+                              ctypes.c_int),
+        "hsr_agents_get_poses": ([P, P, P], ctypes.c_int),
+        "hsr_agents_set_poses": ([P, P, P, U32, P], ctypes.c_int),
+        "hsr_agents_destroy": ([P], ctypes.c_int),
+        "hsr_batch_step": ([P, P, P, P, U32, P, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_render_noisy": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
                               ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_batch_render_noisy": ([P, P, P, U32, P, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
@@ -356,6 +374,71 @@ def hsr_batch_destroy(batch) -> None:
     _lib.hsr_batch_destroy(ctypes.c_void_p(batch))
 
 
+class Agents:
+    """Device-resident agent poses on navigability grids (see hsr_agents_create).
+
+    navmaps: per scene (x0, z0, cell, grid [nz, nx] u8)."""
+
+    def __init__(self, scenes, navmaps, poses, scene_of_agent=None, forward_m=0.25, turn_deg=10.0):
+        self.scenes = list(scenes)
+        poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+        self.n = poses.shape[0]
+        grids = [np.ascontiguousarray(g, dtype=np.uint8) for (_, _, _, g) in navmaps]
+        maps = (hsr_navmap * len(grids))(*[hsr_navmap(float(x0), float(z0), float(c), g.shape[1], g.shape[0],
+                                                      g.ctypes.data)
+                                           for (x0, z0, c, _), g in zip(navmaps, grids)])
+        arr = (ctypes.c_void_p * len(self.scenes))(*[sc.handle for sc in self.scenes])
+        soa = None if scene_of_agent is None else np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+        act = hsr_actuation(float(forward_m), float(turn_deg))
+        out = ctypes.c_void_p()
+        st = _lib.hsr_agents_create(arr, len(self.scenes), maps, self.n, _np_ptr(soa), _np_ptr(poses),
+                                    ctypes.byref(act), ctypes.byref(out))
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_agents_create")
+        self.handle = out.value
+
+    def poses(self, stream=None) -> np.ndarray:
+        out = np.zeros((self.n, 7), dtype=np.float32)
+        st = _lib.hsr_agents_get_poses(ctypes.c_void_p(self.handle), _np_ptr(out), _stream_ptr(stream))
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_agents_get_poses")
+        return out
+
+    def set_poses(self, idx, poses, stream=None):
+        idx = np.ascontiguousarray(idx, dtype=np.uint32).reshape(-1)
+        poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+        st = _lib.hsr_agents_set_poses(ctypes.c_void_p(self.handle), _np_ptr(idx), _np_ptr(poses), idx.shape[0],
+                                       _stream_ptr(stream))
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_agents_set_poses")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.hsr_agents_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hsr_batch_step(batch, agents, agent_idx, actions, frames=None, noise_sigma=None, noise_seed=0, agent_ids=None,
+                   stream=None) -> int:
+    idx = np.ascontiguousarray(agent_idx, dtype=np.uint32).reshape(-1)
+    act = np.ascontiguousarray(actions, dtype=np.uint8).reshape(-1)
+    if act.shape != idx.shape:
+        return HSR_ERR_INVALID_ARG
+    fr = None if frames is None else np.ascontiguousarray(frames, dtype=np.uint32).reshape(-1)
+    nz, keep = _noise(noise_sigma, noise_seed, agent_ids)
+    st = _lib.hsr_batch_step(ctypes.c_void_p(batch), ctypes.c_void_p(agents), _np_ptr(idx), _np_ptr(act),
+                             idx.shape[0], _np_ptr(fr), None if nz is None else ctypes.byref(nz),
+                             _stream_ptr(stream))
+    del keep
+    return st
+
+
 class Batch:
     """A persistent graph-captured render batch bound to output tensors."""
 
@@ -374,6 +457,15 @@ class Batch:
                                         agent_ids, stream)
         if st != HSR_OK:
             raise HsrError(st, "hsr_batch_render")
+        return self.out
+
+    def step(self, agents: "Agents", agent_idx, actions, frames=None, stream=None, noise_sigma=None, noise_seed=0,
+             agent_ids=None):
+        """Apply one action per listed agent on the device, then render them."""
+        st = hsr_batch_step(self.handle, agents.handle, agent_idx, actions, frames, noise_sigma, noise_seed,
+                            agent_ids, stream)
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_batch_step")
         return self.out
 
     def close(self):
