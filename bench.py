@@ -437,24 +437,37 @@ def run_serving(args):
     handles = [hsr.SceneHandle(s) for s in scenes]
     srv = serve.Server(handles, res=(64, 128, 256, 512), weights=(0.2, 0.4, 0.3, 0.1), fb_bytes=4 << 30,
                        max_batch=args.serve_batch, n_streams=args.serve_streams, max_wait_us=args.serve_wait_us)
+    actions = args.serve_requests == "action"
+    agents = None
+    if actions:
+        agents, _ = serve.make_agents(scenes, handles, 1024, seed=args.seed)
+        srv.attach_agents(agents)
     rates = [float(r) for r in args.rates.split(",")]
     rows = []
     clk = ClockSampler()
+    batches0 = 0
     for k, rate in enumerate(rates):
         n = int(max(4000, min(22000, rate * 4)))
-        req = serve.make_requests(scenes, n, seed=args.seed + k)
-        rows.append(serve.run_load(srv, req, rate, warmup=min(2000, n // 10), seed=args.seed + k))
+        if actions:
+            req = serve.make_action_requests(n, 1024, seed=args.seed + k)
+        else:
+            req = serve.make_requests(scenes, n, seed=args.seed + k)
+        row = serve.run_load(srv, req, rate, warmup=min(2000, n // 10), seed=args.seed + k)
+        row["batches"] = row["stats"]["batches"] - batches0
+        batches0 = row["stats"]["batches"]
+        rows.append(row)
     clocks = clk.stop()
     srv.close()
+    if agents is not None:
+        agents.close()
     best = max(rows, key=lambda r: r["frames_per_s"])
     return {"metric": "served RGB-D frames/sec with p50/p99 request latency", "value": best["frames_per_s"],
             "unit": UNIT, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/int", "data": "synthetic",
             "config": {"workload": "serving-8scenes-1024agents-mix64-512", "tris": [int(s.n_tris) for s in scenes],
-                       "max_batch": args.serve_batch, "streams": args.serve_streams,
-                       "max_wait_us": args.serve_wait_us, "fb_bytes": 4 << 30},
-            "per_rate": [{k: v for k, v in r.items() if k != "stats"} | {"batches": r["stats"]["batches"]}
-                         for r in rows],
+                       "requests": args.serve_requests, "max_batch": args.serve_batch,
+                       "streams": args.serve_streams, "max_wait_us": args.serve_wait_us, "fb_bytes": 4 << 30},
+            "per_rate": [{k: v for k, v in r.items() if k != "stats"} for r in rows],
             "clocks": clocks}
 
 
@@ -469,6 +482,8 @@ def main():
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-streams", type=int, default=3)
     ap.add_argument("--serve-wait-us", type=int, default=300)
+    ap.add_argument("--serve-requests", default="action", choices=["action", "pose"],
+                    help="serving: requests carry an action of a device-resident agent, or a host pose")
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

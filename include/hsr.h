@@ -62,6 +62,7 @@ typedef enum {
 } hsr_status;
 
 typedef struct hsr_scene hsr_scene;          /* opaque, library-owned */
+typedef struct hsr_agents hsr_agents;        /* opaque, library-owned (device-resident agents) */
 
 typedef struct {
     float pos[3];      /* camera position in world metres                  */
@@ -170,6 +171,13 @@ HSR_API int hsr_render_noisy(const hsr_scene *const *scenes, uint32_t n_scenes,
  * streams, so micro-batches overlap on the device. Each request yields one
  * result (polled), which points at its device frame until released.
  * Results are identical to a one-shot hsr_render of the same view.
+ *
+ * Action requests (agent >= 0; needs hsr_server_attach_agents) carry an
+ * action instead of a pose: the agent's device-resident pose is moved by the
+ * actuation rules of hsr_batch_step and the new view is rendered; scene and
+ * pose fields are ignored. Per agent, actions apply in submission order and
+ * one at a time: an agent's next action is launched after its previous one
+ * completed. A micro-batch holds either pose or action requests.
  */
 typedef struct hsr_server hsr_server;
 typedef struct {
@@ -186,9 +194,11 @@ typedef struct {
 } hsr_server_config;
 typedef struct {
     uint64_t tag;              /* caller's identifier, returned in the result */
-    uint32_t scene;            /* index into the server's scenes */
+    uint32_t scene;            /* pose requests: index into the server's scenes */
     uint32_t res;              /* one of the served resolutions */
-    hsr_pose pose;
+    hsr_pose pose;             /* pose requests: the camera pose to render */
+    int32_t agent;             /* < 0: pose request; else an action request of this agent of the attached set */
+    uint32_t action;           /* action requests: hsr_action applied on the device before rendering */
 } hsr_request;
 typedef struct {
     uint64_t tag;
@@ -206,6 +216,10 @@ typedef struct {
 } hsr_server_stats;
 HSR_API int hsr_server_create(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_server_config *cfg,
                               hsr_server **out);
+/* Bind the agent set that action requests step (its scenes: the server's, in
+ * the same order; same device). Only while no request is queued or in
+ * flight; agents must outlive the server or a later attach. NULL detaches. */
+HSR_API int hsr_server_attach_agents(hsr_server *server, hsr_agents *agents);
 HSR_API int hsr_server_submit(hsr_server *server, const hsr_request *requests, uint32_t n);
 /* Completed results (up to max); waits up to wait_us for the first one. */
 HSR_API int hsr_server_poll(hsr_server *server, hsr_result *out, uint32_t max, uint32_t *n_out, uint32_t wait_us);
@@ -307,7 +321,6 @@ typedef struct {
     float forward_m;       /* move_forward displacement, metres (finite, >= 0) */
     float turn_deg;        /* turn angle, degrees (finite) */
 } hsr_actuation;
-typedef struct hsr_agents hsr_agents;
 HSR_API int hsr_agents_create(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_navmap *navmaps,
                               uint32_t n_agents, const uint32_t *scene_of_agent, const hsr_pose *poses,
                               const hsr_actuation *act, hsr_agents **out);

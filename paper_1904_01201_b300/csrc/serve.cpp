@@ -19,6 +19,8 @@
 
 #include <cuda_runtime.h>
 
+#include "hsr_internal.h"
+
 namespace hsr {
 int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_cap, uint32_t n_frames,
                  const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb, float *depth,
@@ -36,6 +38,7 @@ double now_s()
 struct Pending {
     hsr_request req;
     double t_submit;
+    uint64_t seq;              // action requests: the agent's submission number
 };
 
 struct ResPool {
@@ -47,7 +50,8 @@ struct ResPool {
     hsr_intrinsics intr{};
     std::vector<uint32_t> free_slots;
     std::vector<hsr_batch *> batch;      // one per stream
-    std::deque<Pending> pending;
+    std::deque<Pending> pending;         // pose requests
+    std::deque<Pending> pending_act;     // action requests
 };
 
 struct InFlight;
@@ -70,6 +74,11 @@ struct hsr_server {
     uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0;
     uint32_t in_flight = 0, queued = 0;
     uint64_t fb_used = 0, fb_total = 0;
+    // attached agents (action requests)
+    hsr_agents *agents = nullptr;
+    uint32_t n_agents = 0;
+    std::vector<uint64_t> agent_submitted, agent_launched;
+    std::vector<uint8_t> agent_busy;
 };
 
 namespace {
@@ -78,7 +87,28 @@ struct InFlight {
     hsr_server *srv;
     int stream;
     std::vector<hsr_result> results;
+    std::vector<uint32_t> agents;        // action batches: the agents to free on completion
 };
+
+// How far into an action queue the scheduler looks for requests whose agent
+// is free (requests behind a busy agent wait without blocking the others).
+constexpr size_t kActScan = 8;
+
+// Action requests of a queue that may launch now, in queue order: the agent's
+// oldest unlaunched action, agent not in flight; at most `max` of them.
+void eligible_actions(const hsr_server *s, const std::deque<Pending> &q, size_t max, std::vector<size_t> &pos)
+{
+    pos.clear();
+    const size_t scan = std::min(q.size(), kActScan * std::max<size_t>(max, 1));
+    for (size_t i = 0; i < scan && pos.size() < max; i++) {
+        const Pending &p = q[i];
+        const uint32_t a = (uint32_t)p.req.agent;
+        if (s->agent_busy[a] || p.seq != s->agent_launched[a]) continue;
+        bool dup = false;
+        for (size_t j : pos) dup |= q[j].req.agent == p.req.agent;
+        if (!dup) pos.push_back(i);
+    }
+}
 
 uint64_t frame_bytes(uint32_t res, bool ids) { return (uint64_t)res * res * (ids ? 11u : 7u); }
 
@@ -96,6 +126,7 @@ void CUDART_CB on_done(void *arg)
         s->completed += f->results.size();
         s->in_flight -= (uint32_t)f->results.size();
         s->busy[f->stream] = false;
+        for (uint32_t a : f->agents) s->agent_busy[a] = false;
     }
     s->cv.notify_all();
     s->done_cv.notify_all();
@@ -127,55 +158,102 @@ void run(hsr_server *s)
             int r = -1;
             for (size_t k = 0; k < s->pools.size(); k++)
                 if (s->pools[k].res == p.req.res) r = (int)k;
-            if (r < 0 || p.req.scene >= s->scenes.size()) {
+            const bool act = p.req.agent >= 0;
+            if (r < 0 || (!act && p.req.scene >= s->scenes.size())) {
+                // (action requests were checked at submit: they always route)
                 s->queued--;
                 fail_request(s, p, HSR_ERR_INVALID_ARG);
             }
+            else if (act)
+                s->pools[r].pending_act.push_back(p);
             else
                 s->pools[r].pending.push_back(p);
         }
-        // launch on free streams: the resolution whose oldest request waited longest
+        // launch on free streams: the (resolution, kind) queue whose oldest
+        // launchable request waited longest
         bool launched = false;
         double next_deadline = 1e300;
+        std::vector<size_t> elig;
         for (size_t st = 0; st < s->streams.size(); st++) {
             if (s->busy[st]) continue;
-            int best = -1;
+            int best = -1, best_kind = 0;
             double oldest = 1e300;
             const double t = now_s();
             for (size_t k = 0; k < s->pools.size(); k++) {
                 ResPool &P = s->pools[k];
-                if (P.pending.empty() || P.free_slots.empty()) continue;
-                const uint32_t can = (uint32_t)std::min<size_t>(
-                    std::min<size_t>(P.pending.size(), P.free_slots.size()), s->cfg.max_batch);
-                const double waited = t - P.pending.front().t_submit;
-                const bool full = can >= s->cfg.max_batch || can >= P.free_slots.size();
-                if (!full && waited * 1e6 < s->cfg.max_wait_us) {
-                    next_deadline = std::min(next_deadline, P.pending.front().t_submit + s->cfg.max_wait_us * 1e-6);
-                    continue;
-                }
-                if (P.pending.front().t_submit < oldest) {
-                    oldest = P.pending.front().t_submit;
-                    best = (int)k;
+                if (P.free_slots.empty()) continue;
+                for (int kind = 0; kind < 2; kind++) {
+                    const std::deque<Pending> &q = kind ? P.pending_act : P.pending;
+                    if (q.empty()) continue;
+                    const size_t lim = std::min<size_t>(P.free_slots.size(), s->cfg.max_batch);
+                    size_t can;
+                    double head;
+                    if (kind) {
+                        eligible_actions(s, q, lim, elig);
+                        if (elig.empty()) continue;
+                        can = elig.size();
+                        head = q[elig[0]].t_submit;
+                    } else {
+                        can = std::min(q.size(), lim);
+                        head = q.front().t_submit;
+                    }
+                    const double waited = t - head;
+                    const bool full = can >= s->cfg.max_batch || can >= P.free_slots.size();
+                    if (!full && waited * 1e6 < s->cfg.max_wait_us) {
+                        next_deadline = std::min(next_deadline, head + s->cfg.max_wait_us * 1e-6);
+                        continue;
+                    }
+                    if (head < oldest) {
+                        oldest = head;
+                        best = (int)k;
+                        best_kind = kind;
+                    }
                 }
             }
             if (best < 0) break;
             ResPool &P = s->pools[best];
-            const uint32_t n = (uint32_t)std::min<size_t>(
-                std::min<size_t>(P.pending.size(), P.free_slots.size()), s->cfg.max_batch);
+            std::deque<Pending> &q = best_kind ? P.pending_act : P.pending;
+            const size_t lim = std::min<size_t>(P.free_slots.size(), s->cfg.max_batch);
+            std::vector<Pending> take;
+            if (best_kind) {
+                eligible_actions(s, q, lim, elig);
+                for (size_t j : elig) take.push_back(q[j]);
+                for (size_t j = elig.size(); j-- > 0;) q.erase(q.begin() + (std::ptrdiff_t)elig[j]);
+            } else {
+                const size_t n0 = std::min(q.size(), lim);
+                for (size_t j = 0; j < n0; j++) {
+                    take.push_back(q.front());
+                    q.pop_front();
+                }
+            }
+            const uint32_t n = (uint32_t)take.size();
             InFlight *f = new (std::nothrow) InFlight();
-            if (!f) break;
+            if (!f) {
+                // out of host memory: put the requests back and retry later
+                for (size_t j = take.size(); j-- > 0;) q.push_front(take[j]);
+                break;
+            }
             f->srv = s;
             f->stream = (int)st;
-            std::vector<uint32_t> soa(n), frames(n);
+            std::vector<uint32_t> soa(n), frames(n), agent_idx(n);
+            std::vector<uint8_t> actions(n);
             std::vector<hsr_pose> poses(n);
             const double tl = now_s();
             for (uint32_t i = 0; i < n; i++) {
-                Pending p = P.pending.front();
-                P.pending.pop_front();
+                const Pending &p = take[i];
                 const uint32_t slot = P.free_slots.back();
                 P.free_slots.pop_back();
-                soa[i] = p.req.scene;
-                poses[i] = p.req.pose;
+                if (best_kind) {
+                    const uint32_t a = (uint32_t)p.req.agent;
+                    agent_idx[i] = a;
+                    actions[i] = (uint8_t)p.req.action;
+                    s->agent_launched[a]++;
+                    s->agent_busy[a] = 1;
+                    f->agents.push_back(a);
+                } else {
+                    soa[i] = p.req.scene;
+                    poses[i] = p.req.pose;
+                }
                 frames[i] = slot;
                 hsr_result r{};
                 r.tag = p.req.tag;
@@ -198,7 +276,10 @@ void run(hsr_server *s)
             hsr_batch *b = P.batch[st];
             cudaStream_t stream = s->streams[st];
             lock.unlock();
-            int rc = hsr_batch_render(b, soa.data(), poses.data(), n, frames.data(), stream);
+            hsr_agents *ag = s->agents;
+            int rc = best_kind ? hsr_batch_step(b, ag, agent_idx.data(), actions.data(), n, frames.data(), nullptr,
+                                                stream)
+                               : hsr_batch_render(b, soa.data(), poses.data(), n, frames.data(), stream);
             if (rc == HSR_OK && cudaLaunchHostFunc(stream, on_done, f) != cudaSuccess) rc = HSR_ERR_CUDA;
             lock.lock();
             if (rc != HSR_OK) {
@@ -213,6 +294,7 @@ void run(hsr_server *s)
                 s->completed += n;
                 s->in_flight -= n;
                 s->busy[st] = false;
+                for (uint32_t a : f->agents) s->agent_busy[a] = false;
                 delete f;
                 s->done_cv.notify_all();
             }
@@ -318,6 +400,26 @@ int hsr_server_create(const hsr_scene *const *scenes, uint32_t n_scenes, const h
     return HSR_OK;
 }
 
+int hsr_server_attach_agents(hsr_server *s, hsr_agents *agents)
+{
+    if (!s) return HSR_ERR_INVALID_ARG;
+    hsr::AgentsView av{};
+    if (agents) {
+        if (!hsr::agents_view(agents, av) || av.device != s->device || av.n_scenes != s->scenes.size())
+            return HSR_ERR_INVALID_ARG;
+        for (uint32_t i = 0; i < av.n_scenes; i++)
+            if (av.scenes[i] != s->scenes[i]) return HSR_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->queued || s->in_flight || !s->incoming.empty()) return HSR_ERR_INVALID_ARG;
+    s->agents = agents;
+    s->n_agents = agents ? av.n_agents : 0;
+    s->agent_submitted.assign(s->n_agents, 0);
+    s->agent_launched.assign(s->n_agents, 0);
+    s->agent_busy.assign(s->n_agents, 0);
+    return HSR_OK;
+}
+
 int hsr_server_submit(hsr_server *s, const hsr_request *reqs, uint32_t n)
 {
     if (!s || (!reqs && n)) return HSR_ERR_INVALID_ARG;
@@ -325,13 +427,22 @@ int hsr_server_submit(hsr_server *s, const hsr_request *reqs, uint32_t n)
     {
         std::lock_guard<std::mutex> lock(s->mu);
         for (uint32_t i = 0; i < n; i++) {
-            Pending p{reqs[i], t};
+            Pending p{reqs[i], t, 0};
             s->submitted++;
+            if (p.req.agent >= 0) {
+                bool res_ok = false;
+                for (const ResPool &P : s->pools) res_ok |= P.res == p.req.res;
+                if (!res_ok || (uint32_t)p.req.agent >= s->n_agents || p.req.action > HSR_ACTION_TURN_RIGHT) {
+                    fail_request(s, p, HSR_ERR_INVALID_ARG);
+                    continue;
+                }
+            }
             if (s->queued >= s->cfg.max_queue) {
                 s->rejected++;
                 fail_request(s, p, HSR_ERR_OVERFLOW);
                 continue;
             }
+            if (p.req.agent >= 0) p.seq = s->agent_submitted[p.req.agent]++;
             s->queued++;
             s->incoming.push_back(p);
         }

@@ -92,8 +92,9 @@ class hsr_server_stats(ctypes.Structure):
 
 
 # hsr_request as a numpy record (tag, scene, res, pose[7]), 48 bytes
-REQUEST_DTYPE = np.dtype([("tag", np.uint64), ("scene", np.uint32), ("res", np.uint32), ("pose", np.float32, 7)],
-                         align=True)
+REQUEST_DTYPE = np.dtype([("tag", np.uint64), ("scene", np.uint32), ("res", np.uint32), ("pose", np.float32, 7),
+                          ("agent", np.int32), ("action", np.uint32)], align=True)
+assert REQUEST_DTYPE.itemsize == 56
 
 
 class HsrError(RuntimeError):
@@ -138,6 +139,7 @@ def _load():
         "hsr_batch_render_noisy": ([P, P, P, U32, P, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_server_create": ([P, U32, ctypes.POINTER(hsr_server_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_server_submit": ([P, P, U32], ctypes.c_int),
+        "hsr_server_attach_agents": ([P, P], ctypes.c_int),
         "hsr_server_poll": ([P, P, U32, ctypes.POINTER(U32), U32], ctypes.c_int),
         "hsr_server_release": ([P, P, U32], ctypes.c_int),
         "hsr_server_get_stats": ([P, ctypes.POINTER(hsr_server_stats)], ctypes.c_int),

@@ -47,6 +47,14 @@ class Server:
         self.handle = out.value
         self._buf = (hsr.hsr_result * 4096)()
 
+    def attach_agents(self, agents) -> None:
+        """Bind the hsr.Agents set that action requests step (None detaches)."""
+        st = hsr.library().hsr_server_attach_agents(ctypes.c_void_p(self.handle),
+                                                    None if agents is None else ctypes.c_void_p(agents.handle))
+        if st != hsr.HSR_OK:
+            raise hsr.HsrError(st, "hsr_server_attach_agents")
+        self.agents = agents
+
     def submit(self, requests: np.ndarray) -> None:
         requests = np.ascontiguousarray(requests, dtype=hsr.REQUEST_DTYPE)
         st = hsr.library().hsr_server_submit(ctypes.c_void_p(self.handle), requests.ctypes.data_as(ctypes.c_void_p),
@@ -121,12 +129,41 @@ def make_requests(scenes_np: Sequence, n_requests: int, n_agents: int = 1024, re
     cw = np.cumsum(np.asarray(weights, dtype=np.float64) / sum(weights))
     ri = np.minimum(np.searchsorted(cw, rs.uniform(n_requests), side="right"), len(res) - 1)
     req = np.zeros(n_requests, dtype=hsr.REQUEST_DTYPE)
+    req["agent"] = -1
     for i in range(n_requests):
         si, j = owner[int(agent[i])]
         req[i]["tag"] = i
         req[i]["scene"] = si
         req[i]["res"] = res[int(ri[i])]
         req[i]["pose"] = walks[si].step(j)
+    return req
+
+
+def make_agents(scenes_np: Sequence, handles: Sequence, n_agents: int = 1024, seed: int = 0, cell: float = 0.05):
+    """Device-resident agents split Dirichlet(0.5) over the scenes, placed on
+    navigable cells of each scene's grid; returns (hsr.Agents, scene_of_agent)."""
+    split = wl.dirichlet_split(n_agents, len(scenes_np), 0.5, seed)
+    navs = [wl.navmap(sc, cell) for sc in scenes_np]
+    poses = np.concatenate([wl.navigable_poses(sc, nav, int(k), seed + si)
+                            for si, (sc, nav, k) in enumerate(zip(scenes_np, navs, split))])
+    soa = np.repeat(np.arange(len(scenes_np), dtype=np.uint32), split)
+    return hsr.Agents(handles, navs, poses, scene_of_agent=soa), soa
+
+
+def make_action_requests(n_requests: int, n_agents: int = 1024, res=(64, 128, 256, 512),
+                         weights=(0.2, 0.4, 0.3, 0.1), seed: int = 0) -> np.ndarray:
+    """Action requests: each advances one agent (uniform) by move_forward,
+    turn_left or turn_right (uniform), at a resolution drawn from the mix."""
+    rs = wl.Stream(seed, "serving-actions")
+    agent = rs.integers(n_requests, 0, n_agents)
+    action = rs.integers(n_requests, hsr.HSR_ACTION_MOVE_FORWARD, hsr.HSR_ACTION_TURN_RIGHT + 1)
+    cw = np.cumsum(np.asarray(weights, dtype=np.float64) / sum(weights))
+    ri = np.minimum(np.searchsorted(cw, rs.uniform(n_requests), side="right"), len(res) - 1)
+    req = np.zeros(n_requests, dtype=hsr.REQUEST_DTYPE)
+    req["tag"] = np.arange(n_requests)
+    req["res"] = np.asarray(res, dtype=np.uint32)[ri]
+    req["agent"] = agent
+    req["action"] = action
     return req
 
 

@@ -31,6 +31,7 @@ def scenes():
 def _requests(sc, n, seed):
     rng = np.random.default_rng(seed)
     req = np.zeros(n, dtype=hsr.REQUEST_DTYPE)
+    req["agent"] = -1                          # pose requests
     for i in range(n):
         s = int(rng.integers(0, len(sc)))
         req[i]["tag"] = i
@@ -107,3 +108,69 @@ def test_queue_overflow_and_bad_requests(scenes):
     st = srv.stats()
     assert st["rejected"] == statuses.count(hsr.HSR_ERR_OVERFLOW)
     srv.close()
+
+
+def test_action_requests_step_agents_in_order(scenes, oracle_mod):
+    """Action requests of a few agents, mixed with pose requests: every
+    agent's actions apply in submission order (its poses follow the oracle's
+    actuation), each result is the render of the pose its action reached, and
+    a second action of a busy agent waits for the first."""
+    sc, hs = scenes
+    navs = [wl.navmap(s, 0.05) for s in sc]
+    n_agents = 5
+    soa = np.array([0, 1, 0, 1, 0], dtype=np.uint32)
+    poses0 = np.stack([wl.navigable_poses(sc[int(s)], navs[int(s)], 1, 40 + a)[0] for a, s in enumerate(soa)])
+    ag = hsr.Agents(hs, navs, poses0, scene_of_agent=soa)
+    srv = serve.Server(hs, res=RES, weights=(1, 1, 1), fb_bytes=64 << 20, max_batch=8, n_streams=3,
+                       max_wait_us=50, with_ids=True)
+    srv.attach_agents(ag)
+    rng = np.random.default_rng(11)
+    n_act = 60
+    act = np.zeros(n_act, dtype=hsr.REQUEST_DTYPE)
+    act["tag"] = np.arange(n_act)
+    act["agent"] = rng.integers(0, n_agents, n_act)
+    act["action"] = rng.choice([0, 1, 1, 2, 3], n_act)
+    act["res"] = np.asarray(RES)[rng.integers(0, len(RES), n_act)]
+    pose_req = _requests(sc, 20, 5)
+    pose_req["tag"] += 1000
+    for k in range(0, n_act, 12):
+        srv.submit(act[k:k + 12])
+        srv.submit(pose_req[k // 3:k // 3 + 4])
+    got = _collect(srv, n_act + 20, True)
+    # expected pose after each action, by submission order per agent
+    cur = poses0.copy()
+    for i, rq in enumerate(act):
+        a = int(rq["agent"])
+        cur[a], _ = oracle_mod.actuate(cur[a], int(rq["action"]), navs[int(soa[a])])
+        st, fr = got[i]
+        assert st == 0
+        r = int(rq["res"])
+        ref = hsr.render(hs[int(soa[a])], cur[a][None], wl.pinhole_90(r, r), r, r, ids=True)
+        torch.cuda.synchronize()
+        for key in ("rgb", "depth", "ids"):
+            assert torch.equal(fr[key], ref[key][0]), (i, key)
+    assert np.array_equal(ag.poses().view(np.uint32), cur.view(np.uint32))
+    for i, rq in enumerate(pose_req):
+        assert got[int(rq["tag"])][0] == 0
+    srv.close()
+    ag.close()
+
+
+def test_action_requests_need_attached_agents(scenes):
+    sc, hs = scenes
+    srv = serve.Server(hs, res=RES, weights=(1, 1, 1), fb_bytes=8 << 20, max_batch=4, n_streams=1)
+    req = np.zeros(2, dtype=hsr.REQUEST_DTYPE)
+    req["tag"] = [0, 1]
+    req["res"] = RES[0]
+    req["agent"] = [0, 0]
+    req["action"] = [1, 7]
+    srv.submit(req)
+    got = _collect(srv, 2, False)
+    assert got[0][0] == hsr.HSR_ERR_INVALID_ARG and got[1][0] == hsr.HSR_ERR_INVALID_ARG
+    # agents over another scene list cannot be attached
+    navs = [wl.navmap(sc[1], 0.05)]
+    ag = hsr.Agents([hs[1]], navs, wl.navigable_poses(sc[1], navs[0], 2, 0))
+    with pytest.raises(hsr.HsrError):
+        srv.attach_agents(ag)
+    srv.close()
+    ag.close()
