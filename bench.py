@@ -471,13 +471,103 @@ def run_serving(args):
             "clocks": clocks}
 
 
+def run_transfer(args):
+    """Frame-transfer strategies (Table 2 and the resolution figure beside it):
+    frames stay in device memory for a device consumer (GPU->GPU), are copied
+    to pinned host memory (GPU->CPU), or copied to the host and back into a
+    separate device buffer (GPU->CPU->GPU); for colour, colour + depth, and
+    colour + depth + semantic ids; with 1, 3 or 5 concurrent renderers (CUDA
+    streams, each with its own graph-captured batch) in place of the paper's
+    simulator processes, each rendering 1 agent per launch (as a simulator
+    process does) or 64. Copies are queued on each renderer's stream after
+    its render; frames/s over all renderers, wall clock, synchronised on both
+    sides."""
+    import torch
+    from paper_1904_01201_b300 import hsr
+    from paper_1904_01201_b300 import workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    sc = wl.make_house(args.seed, 1_000_000, 4096, semantic=True)
+    h = hsr.SceneHandle(sc)
+    sensors = {"rgb": (False, False), "rgbd": (True, False), "rgbds": (True, True)}
+    pool = wl.random_poses(sc, 512, args.seed + 7)
+
+    def measure(res, sensor, strategy, n_streams, per_launch):
+        depth, ids = sensors[sensor]
+        intr = wl.pinhole_90(res, res)
+        streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        batches = [hsr.Batch([h], per_launch, intr, res, res, ids=ids, depth=depth) for _ in streams]
+        host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in b.out.items() if v is not None}
+                for b in batches]
+        back = [{k: torch.empty_like(v) for k, v in b.out.items() if v is not None} for b in batches] \
+            if strategy == "gpu-cpu-gpu" else None
+        n_pose = len(pool) // per_launch
+
+        def step(i):
+            for j, (b, s) in enumerate(zip(batches, streams)):
+                k0 = ((i * n_streams + j) % n_pose) * per_launch
+                b.render(pool[k0:k0 + per_launch], stream=s)
+                if strategy == "gpu-gpu":
+                    continue
+                with torch.cuda.stream(s):
+                    for key, dst in host[j].items():
+                        dst.copy_(b.out[key], non_blocking=True)
+                    if back is not None:
+                        for key, dst in back[j].items():
+                            dst.copy_(host[j][key], non_blocking=True)
+
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(3)
+        torch.cuda.synchronize()
+        steps = int(min(400, max(5, 0.25 / max(1e-6, time.perf_counter() - t0))))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            step(4 + i)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for b in batches:
+            b.close()
+        return n_streams * per_launch * steps / dt
+
+    clk = ClockSampler()
+    table = []
+    for per_launch in (1, 64):
+        for sensor in ("rgb", "rgbd", "rgbds"):
+            for strategy in ("gpu-cpu-gpu", "gpu-cpu", "gpu-gpu"):
+                for n_streams in (1, 3, 5):
+                    table.append({"res": 128, "sensors": sensor, "transfer": strategy, "renderers": n_streams,
+                                  "agents_per_launch": per_launch,
+                                  "frames_per_s": measure(128, sensor, strategy, n_streams, per_launch)})
+    sweep = []
+    for per_launch in (1, 64):
+        for res in (64, 128, 256, 512):
+            for strategy in ("gpu-cpu-gpu", "gpu-cpu", "gpu-gpu"):
+                sweep.append({"res": res, "sensors": "rgbd", "transfer": strategy, "renderers": 1,
+                              "agents_per_launch": per_launch,
+                              "frames_per_s": measure(res, "rgbd", strategy, 1, per_launch)})
+    clocks = clk.stop()
+    head = [r for r in table if r["sensors"] == "rgbd" and r["transfer"] == "gpu-gpu" and r["renderers"] == 1
+            and r["agents_per_launch"] == 64][0]
+    return {"metric": "RGB-D frames/sec by frame-transfer strategy", "value": head["frames_per_s"], "unit": UNIT,
+            "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/int",
+            "data": "synthetic",
+            "config": {"workload": "transfer-house-1M-atlas4096-sem", "tris": int(sc.n_tris),
+                       "value_is": "gpu-gpu, rgbd, 128x128, 1 renderer, 64 agents per launch"},
+            "table": table, "resolution_sweep": sweep, "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hsr", choices=["hsr", "reference"])
-    ap.add_argument("--workload", default="house", choices=["house", "room", "batching", "large", "serving"])
+    ap.add_argument("--workload", default="house",
+                    choices=["house", "room", "batching", "large", "serving", "transfer"])
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving: request rates (1/s)")
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-streams", type=int, default=3)
@@ -495,8 +585,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.workload == "serving":
-        res = run_serving(args)
+    if args.workload in ("serving", "transfer"):
+        res = run_serving(args) if args.workload == "serving" else run_transfer(args)
         if res is not None:
             print(json.dumps(res), flush=True)
         return

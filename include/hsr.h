@@ -111,8 +111,8 @@ HSR_API int hsr_scene_get_info(const hsr_scene *scene, hsr_scene_info *info);
  * Render n agents of one scene, one observation each (Sec. 4 "Sensory input":
  * colour + depth at the same pose and intrinsics; Sec. 3: one pass for all
  * outputs). poses: host [n]. intr: host, shared by all n views.
- * rgb: device [n][height][width][3]; depth: device [n][height][width];
- * ids: device [n][height][width] or NULL.
+ * rgb: device [n][height][width][3]; depth: device [n][height][width], or
+ * NULL for a colour-only sensor set; ids: device [n][height][width] or NULL.
  */
 HSR_API int hsr_render(const hsr_scene *scene, const hsr_pose *poses, uint32_t n,
                const hsr_intrinsics *intr, uint32_t width, uint32_t height,

@@ -411,7 +411,8 @@ cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const 
 bool validate_common(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_pose *poses, uint32_t n,
                      const hsr_intrinsics *intr, uint32_t width, uint32_t height, const void *rgb, const void *depth)
 {
-    if (!scenes || n_scenes == 0 || !poses || n == 0 || !rgb || !depth) return false;
+    (void)depth;   // optional: NULL renders the colour sensor only
+    if (!scenes || n_scenes == 0 || !poses || n == 0 || !rgb) return false;
     if (width == 0 || height == 0 || width > 4096 || height > 4096) return false;
     if (!intrinsics_ok(intr)) return false;
     for (uint32_t i = 0; i < n_scenes; i++)
@@ -457,8 +458,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
             nr2.noise = &tail;
         }
         return render_views(scenes, n_scenes, scene_of_agent ? scene_of_agent + h : nullptr, poses + h, n - h, intr,
-                            width, height, rgb + 3 * px * h, depth + px * h, ids ? ids + px * h : nullptr, stream_ptr,
-                            cfg_in, nr2);
+                            width, height, rgb + 3 * px * h, depth ? depth + px * h : nullptr,
+                            ids ? ids + px * h : nullptr, stream_ptr, cfg_in, nr2);
     }
     if (items >= 0xFFFFFFF0ull || list_entries >= 0xFFFFFFF0ull) return HSR_ERR_INVALID_ARG;
 

@@ -479,14 +479,14 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
             r32[0] = rgb[0] | (rgb[1] << 24);
             r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
             r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
-            *reinterpret_cast<float4 *>(p.depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
+            if (p.depth) *reinterpret_cast<float4 *>(p.depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
             if (p.ids) *reinterpret_cast<uint4 *>(p.ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
         } else {
             for (uint32_t k = 0; k < n; k++) {
                 p.rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
                 p.rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
                 p.rgb[3 * (o + k) + 2] = (uint8_t)((rgb[k] >> 16) & 255u);
-                p.depth[o + k] = dep[k];
+                if (p.depth) p.depth[o + k] = dep[k];
                 if (p.ids) p.ids[o + k] = id[k];
             }
         }

@@ -444,9 +444,9 @@ def hsr_batch_step(batch, agents, agent_idx, actions, frames=None, noise_sigma=N
 class Batch:
     """A persistent graph-captured render batch bound to output tensors."""
 
-    def __init__(self, scenes, n_cap, intr, width, height, ids=True, cfg=None, device="cuda"):
+    def __init__(self, scenes, n_cap, intr, width, height, ids=True, cfg=None, device="cuda", depth=True):
         self.scenes = list(scenes)
-        self.out = alloc_outputs(n_cap, width, height, ids, device)
+        self.out = alloc_outputs(n_cap, width, height, ids, device, depth)
         self.handle = hsr_batch_create([s.handle for s in self.scenes], n_cap, intr, width, height,
                                        self.out["rgb"], self.out["depth"], self.out.get("ids"), cfg)
 
@@ -502,11 +502,12 @@ class SceneHandle:
             pass
 
 
-def alloc_outputs(n: int, width: int, height: int, ids: bool = True, device="cuda"):
+def alloc_outputs(n: int, width: int, height: int, ids: bool = True, device="cuda", depth: bool = True):
     import torch
     rgb = torch.empty((n, height, width, 3), dtype=torch.uint8, device=device)
-    depth = torch.empty((n, height, width), dtype=torch.float32, device=device)
-    out = {"rgb": rgb, "depth": depth}
+    out = {"rgb": rgb, "depth": None}
+    if depth:
+        out["depth"] = torch.empty((n, height, width), dtype=torch.float32, device=device)
     if ids:
         out["ids"] = torch.empty((n, height, width), dtype=torch.int32, device=device)
     return out
