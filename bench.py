@@ -471,6 +471,57 @@ def run_serving(args):
             "clocks": clocks}
 
 
+def run_semantic(args):
+    """Semantic sensor from a separate, denser mesh (Table 2, third row and
+    footnote): 64 agents at 128x128 in a 1M-triangle textured house, colour +
+    depth from it, semantic ids from the same layout tessellated to 3M
+    triangles; frames/s of RGB-D alone and of RGB-D + semantics, both as one
+    graph-replayed batch per step (CUDA events, L2 flushed between steps)."""
+    import torch
+    from paper_1904_01201_b300 import hsr
+    from paper_1904_01201_b300 import workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    col = wl.make_house(args.seed, 1_000_000, 4096)
+    sem = wl.make_semantic_mesh(args.seed, 3_000_000)
+    hs = [hsr.SceneHandle(col), hsr.SceneHandle(sem)]
+    n, W = 64, 128
+    intr = wl.pinhole_90(W, W)
+    poses = wl.random_poses(col, n, args.seed)
+    f = np.arange(n, dtype=np.uint32)
+    rgbd = hsr.make_views(poses, 0, f, hsr.HSR_OUT_RGB | hsr.HSR_OUT_DEPTH)
+    both = np.concatenate([rgbd, hsr.make_views(poses, 1, f, hsr.HSR_OUT_IDS)])
+    b = hsr.Batch(hs, 2 * n, intr, W, W)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(views):
+        for _ in range(max(3, args.warmup)):
+            assert hsr.hsr_batch_render_views(b.handle, views, stream=stream) == hsr.HSR_OK
+        ts = []
+        for _ in range(max(5, min(args.steps, 50))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            assert hsr.hsr_batch_render_views(b.handle, views, stream=stream) == hsr.HSR_OK
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return n / (statistics.median(ts) * 1e-3)
+
+    clk = ClockSampler()
+    fps_rgbd = timed(rgbd)
+    fps_sem = timed(both)
+    clocks = clk.stop()
+    b.close()
+    return {"metric": "RGB-D + semantic frames/sec (semantic ids from a separate denser mesh)", "value": fps_sem,
+            "unit": UNIT, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/int", "data": "synthetic",
+            "config": {"workload": "semantic-house-1M-atlas4096+sem-3M-64x128", "tris": int(col.n_tris),
+                       "sem_tris": int(sem.n_tris), "agents": n, "res": W, "l2": "flushed between steps"},
+            "rgbd_frames_per_s": fps_rgbd, "semantic_slowdown": fps_rgbd / fps_sem, "clocks": clocks}
+
+
 def run_transfer(args):
     """Frame-transfer strategies (Table 2 and the resolution figure beside it):
     frames stay in device memory for a device consumer (GPU->GPU), are copied
@@ -567,7 +618,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hsr", choices=["hsr", "reference"])
     ap.add_argument("--workload", default="house",
-                    choices=["house", "room", "batching", "large", "serving", "transfer"])
+                    choices=["house", "room", "batching", "large", "serving", "transfer", "semantic"])
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving: request rates (1/s)")
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-streams", type=int, default=3)
@@ -585,8 +636,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.workload in ("serving", "transfer"):
-        res = run_serving(args) if args.workload == "serving" else run_transfer(args)
+    if args.workload in ("serving", "transfer", "semantic"):
+        res = {"serving": run_serving, "transfer": run_transfer, "semantic": run_semantic}[args.workload](args)
         if res is not None:
             print(json.dumps(res), flush=True)
         return

@@ -160,6 +160,30 @@ HSR_API int hsr_render_noisy(const hsr_scene *const *scenes, uint32_t n_scenes,
                      void *cuda_stream);
 
 /*
+ * General view lists: each view names its scene, pose, output frame and the
+ * outputs it writes, so one call can render several sensors per agent, such
+ * as the semantic sensor of Table 2 (footnote), whose ids come from a
+ * separate, denser semantic mesh: view (colour mesh, pose, frame f,
+ * HSR_OUT_RGB | HSR_OUT_DEPTH) plus view (semantic mesh, pose, frame f,
+ * HSR_OUT_IDS). views: host [n]; outputs 0 means every present buffer;
+ * frame < n_frames (the frames the output buffers hold); no output of a frame
+ * may be written by two views (HSR_ERR_INVALID_ARG). A buffer may be NULL
+ * when no view writes it (at least one buffer must be given). Noise streams
+ * are keyed by noise->agent_ids[i], else by the view's frame.
+ */
+enum { HSR_OUT_RGB = 1, HSR_OUT_DEPTH = 2, HSR_OUT_IDS = 4 };
+typedef struct {
+    hsr_pose pose;
+    uint32_t scene;            /* index into scenes */
+    uint32_t frame;            /* output frame */
+    uint32_t outputs;          /* HSR_OUT_* bits, or 0 for all */
+} hsr_view;
+HSR_API int hsr_render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_view *views, uint32_t n,
+                             uint32_t n_frames, const hsr_intrinsics *intr, uint32_t width, uint32_t height,
+                             uint8_t *rgb, float *depth, uint32_t *ids, const hsr_depth_noise *noise,
+                             void *cuda_stream);
+
+/*
  * Serving (continuous batching of render requests as rollout workers step).
  * A server keeps the scenes resident, owns a pool of output framebuffers per
  * served square resolution (its admission budget, fb_bytes, split by
@@ -270,6 +294,10 @@ HSR_API int hsr_batch_render(hsr_batch *batch, const uint32_t *scene_of_agent, c
 HSR_API int hsr_batch_render_noisy(hsr_batch *batch, const uint32_t *scene_of_agent, const hsr_pose *poses,
                                    uint32_t n, const uint32_t *frames, const hsr_depth_noise *noise,
                                    void *cuda_stream);
+/* View-list render on a batch (views as for hsr_render_views, n <= n_cap,
+ * frame < the batch's frame count). */
+HSR_API int hsr_batch_render_views(hsr_batch *batch, const hsr_view *views, uint32_t n,
+                                   const hsr_depth_noise *noise, void *cuda_stream);
 HSR_API int hsr_batch_destroy(hsr_batch *batch);
 
 /*

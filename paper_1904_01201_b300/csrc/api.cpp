@@ -260,6 +260,44 @@ struct StepReq {
     uint64_t agents_dev = 0;         // device address of the AgentsDev
 };
 
+// View lists: explicit output frames and per-view output masks.
+struct ViewsReq {
+    const uint32_t *frames = nullptr;
+    const uint32_t *outputs = nullptr;
+};
+
+// Unpacks a view list into per-view arrays (outputs 0 -> every present
+// buffer), checking scene and frame ranges, that each requested output has a
+// buffer, and that no output of a frame is written by two views.
+int unpack_views(const hsr_view *views, uint32_t n, uint32_t n_scenes, uint32_t n_frames, uint32_t present,
+                 std::vector<uint32_t> &soa, std::vector<hsr_pose> &poses, std::vector<uint32_t> &frames,
+                 std::vector<uint32_t> &outs)
+{
+    if (!views || n == 0 || present == 0 || n_frames == 0) return HSR_ERR_INVALID_ARG;
+    std::vector<uint8_t> used(n_frames, 0);
+    soa.resize(n);
+    poses.resize(n);
+    frames.resize(n);
+    outs.resize(n);
+    for (uint32_t i = 0; i < n; i++) {
+        const hsr_view &v = views[i];
+        if (v.scene >= n_scenes || v.frame >= n_frames || (v.outputs & ~present)) return HSR_ERR_INVALID_ARG;
+        const uint32_t o = v.outputs ? v.outputs : present;
+        if (used[v.frame] & o) return HSR_ERR_INVALID_ARG;
+        used[v.frame] |= (uint8_t)o;
+        soa[i] = v.scene;
+        poses[i] = v.pose;
+        frames[i] = v.frame;
+        outs[i] = o;
+    }
+    return HSR_OK;
+}
+
+uint32_t present_outputs(const void *rgb, const void *depth, const void *ids)
+{
+    return (rgb ? HSR_OUT_RGB : 0u) | (depth ? HSR_OUT_DEPTH : 0u) | (ids ? HSR_OUT_IDS : 0u);
+}
+
 bool noise_ok(const hsr_depth_noise *nz)
 {
     return !nz || (std::isfinite(nz->depth_sigma) && nz->depth_sigma >= 0.f && nz->reserved == 0);
@@ -272,7 +310,8 @@ bool noise_ok(const hsr_depth_noise *nz)
 // noise.agent_ids[i], else by agent_base + its output frame.
 int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint32_t *scene_of_agent,
                      const hsr_pose *poses, uint32_t n, const uint32_t *frames, const hsr_intrinsics &intr,
-                     unsigned char *hbuf, const NoiseReq &nr = NoiseReq{}, const StepReq *step = nullptr)
+                     unsigned char *hbuf, const NoiseReq &nr = NoiseReq{}, const StepReq *step = nullptr,
+                     const uint32_t *outputs = nullptr)
 {
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
     if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
@@ -317,6 +356,7 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
             for (int c = 0; c < 3; c++) v.pos[c] = poses[i].pos[c];
         }
         v.scene = sidx;
+        v.outputs = outputs ? outputs[i] : (uint32_t)(HSR_OUT_RGB | HSR_OUT_DEPTH | HSR_OUT_IDS);
         v.frame = frames ? frames[i] : i;
         v.agent = agent_ids ? agent_ids[i] : nr.agent_base + v.frame;
     }
@@ -408,11 +448,12 @@ cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const 
     return launch_render(p, pl.cfg, stream);
 }
 
+// Scenes, poses, intrinsics and size of a render; at least one output buffer
+// (any of colour, depth, ids may be absent).
 bool validate_common(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_pose *poses, uint32_t n,
-                     const hsr_intrinsics *intr, uint32_t width, uint32_t height, const void *rgb, const void *depth)
+                     const hsr_intrinsics *intr, uint32_t width, uint32_t height, bool has_output)
 {
-    (void)depth;   // optional: NULL renders the colour sensor only
-    if (!scenes || n_scenes == 0 || !poses || n == 0 || !rgb) return false;
+    if (!scenes || n_scenes == 0 || !poses || n == 0 || !has_output) return false;
     if (width == 0 || height == 0 || width > 4096 || height > 4096) return false;
     if (!intrinsics_ok(intr)) return false;
     for (uint32_t i = 0; i < n_scenes; i++)
@@ -425,9 +466,10 @@ bool validate_common(const hsr_scene *const *scenes, uint32_t n_scenes, const hs
 int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,
                  const hsr_pose *poses, uint32_t n, const hsr_intrinsics *intr, uint32_t width, uint32_t height,
                  uint8_t *rgb, float *depth, uint32_t *ids, void *stream_ptr, const LaunchCfg *cfg_in,
-                 const NoiseReq &nr = NoiseReq{})
+                 const NoiseReq &nr = NoiseReq{}, const ViewsReq &vr = ViewsReq{})
 {
-    if (!validate_common(scenes, n_scenes, poses, n, intr, width, height, rgb, depth)) return HSR_ERR_INVALID_ARG;
+    if (!validate_common(scenes, n_scenes, poses, n, intr, width, height, rgb || depth || ids))
+        return HSR_ERR_INVALID_ARG;
     if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
@@ -447,19 +489,27 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         const uint32_t h = n / 2;
         const size_t px = (size_t)width * height;
         int st = render_views(scenes, n_scenes, scene_of_agent, poses, h, intr, width, height, rgb, depth, ids,
-                              stream_ptr, cfg_in, nr);
+                              stream_ptr, cfg_in, nr, vr);
         if (st != HSR_OK) return st;
         hsr_depth_noise tail{};
         NoiseReq nr2 = nr;
-        nr2.agent_base += h;
         if (nr.noise && nr.noise->agent_ids) {
             tail = *nr.noise;
             tail.agent_ids += h;
             nr2.noise = &tail;
         }
+        ViewsReq vr2;
+        vr2.outputs = vr.outputs ? vr.outputs + h : nullptr;
+        if (vr.frames) {
+            // explicit frames index the whole output buffers
+            vr2.frames = vr.frames + h;
+            return render_views(scenes, n_scenes, scene_of_agent ? scene_of_agent + h : nullptr, poses + h, n - h,
+                                intr, width, height, rgb, depth, ids, stream_ptr, cfg_in, nr2, vr2);
+        }
+        nr2.agent_base += h;
         return render_views(scenes, n_scenes, scene_of_agent ? scene_of_agent + h : nullptr, poses + h, n - h, intr,
-                            width, height, rgb + 3 * px * h, depth ? depth + px * h : nullptr,
-                            ids ? ids + px * h : nullptr, stream_ptr, cfg_in, nr2);
+                            width, height, rgb ? rgb + 3 * px * h : nullptr, depth ? depth + px * h : nullptr,
+                            ids ? ids + px * h : nullptr, stream_ptr, cfg_in, nr2, vr2);
     }
     if (items >= 0xFFFFFFF0ull || list_entries >= 0xFFFFFFF0ull) return HSR_ERR_INVALID_ARG;
 
@@ -486,7 +536,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     }
     if (!st.done && cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) return HSR_ERR_CUDA;
     auto *hbuf = static_cast<unsigned char *>(st.host);
-    int status = fill_descriptors(pl, scenes, scene_of_agent, poses, n, nullptr, *intr, hbuf, nr);
+    int status = fill_descriptors(pl, scenes, scene_of_agent, poses, n, vr.frames, *intr, hbuf, nr, nullptr,
+                                  vr.outputs);
     if (status != HSR_OK) return status;
 
     void *dbuf = nullptr, *sbuf = nullptr;
@@ -844,7 +895,8 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
     if (n_frames < n_cap) return HSR_ERR_INVALID_ARG;
     *out = nullptr;
     hsr_pose dummy{};
-    if (!validate_common(scenes, n_scenes, &dummy, n_cap, intr, width, height, rgb, depth)) return HSR_ERR_INVALID_ARG;
+    if (!validate_common(scenes, n_scenes, &dummy, n_cap, intr, width, height, rgb || depth || ids))
+        return HSR_ERR_INVALID_ARG;
     uint64_t max_m = 0, max_g = 0;
     for (uint32_t i = 0; i < n_scenes; i++) {
         max_m = std::max<uint64_t>(max_m, scenes[i]->dev.n_meshlets);
@@ -997,6 +1049,33 @@ int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, 
     int st = fill_descriptors(pl, b->scenes.data(), soa.data(), nullptr, n, frames, b->intr, b->h_desc[k], nr, &sr);
     if (st != HSR_OK) return st;
     if (cudaGraphLaunch(b->step_exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    b->launched[k] = true;
+    b->cur ^= 1;
+    return HSR_OK;
+}
+
+int hsr_batch_render_views(hsr_batch *b, const hsr_view *views, uint32_t n, const hsr_depth_noise *noise,
+                           void *cuda_stream)
+{
+    if (!b || !noise_ok(noise)) return HSR_ERR_INVALID_ARG;
+    const Plan &pl = b->plan;
+    if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
+    std::vector<uint32_t> soa, frames, outs;
+    std::vector<hsr_pose> poses;
+    int st = unpack_views(views, n, (uint32_t)b->scenes.size(), b->n_frames, present_outputs(b->rgb, b->depth, b->ids),
+                          soa, poses, frames, outs);
+    if (st != HSR_OK) return st;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lock(b->mu);
+    const int k = b->cur;
+    if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
+    NoiseReq nr;
+    nr.noise = noise;
+    st = fill_descriptors(pl, b->scenes.data(), soa.data(), poses.data(), n, frames.data(), b->intr, b->h_desc[k], nr,
+                          nullptr, outs.data());
+    if (st != HSR_OK) return st;
+    if (cudaGraphLaunch(b->exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
     b->cur ^= 1;
@@ -1162,6 +1241,24 @@ int hsr_render_batch(const hsr_scene *const *scenes, uint32_t n_scenes, const ui
     if (!scene_of_agent) return HSR_ERR_INVALID_ARG;
     return render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
                         cuda_stream, nullptr);
+}
+
+int hsr_render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_view *views, uint32_t n,
+                     uint32_t n_frames, const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb,
+                     float *depth, uint32_t *ids, const hsr_depth_noise *noise, void *cuda_stream)
+{
+    std::vector<uint32_t> soa, frames, outs;
+    std::vector<hsr_pose> poses;
+    const int st = unpack_views(views, n, n_scenes, n_frames, present_outputs(rgb, depth, ids), soa, poses, frames,
+                                outs);
+    if (st != HSR_OK) return st;
+    NoiseReq nr;
+    nr.noise = noise;
+    ViewsReq vr;
+    vr.frames = frames.data();
+    vr.outputs = outs.data();
+    return render_views(scenes, n_scenes, soa.data(), poses.data(), n, intr, width, height, rgb, depth, ids,
+                        cuda_stream, nullptr, nr, vr);
 }
 
 int hsr_render_noisy(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32_t *scene_of_agent,

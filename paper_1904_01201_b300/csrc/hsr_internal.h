@@ -61,9 +61,11 @@ struct alignas(16) View {
     uint32_t agent;            // key of the depth-noise stream
     uint32_t state;            // agent-state slot moved by the actuation pass (step batches)
     uint32_t action;           // action applied to that slot first (hsr_action)
+    uint32_t outputs;          // HSR_OUT_* bits this view writes (with its buffer present)
+    uint32_t pad_[3];
 };
 
-static_assert(sizeof(View) == 176, "View is 11 x 16 bytes");
+static_assert(sizeof(View) == 192, "View is 12 x 16 bytes");
 
 // Navigability grid of one scene on the device, with the scene's bounding box
 // (the fixed-point range check of a moved camera).

@@ -199,7 +199,7 @@ __device__ __forceinline__ float noisy_depth(float sigma, uint32_t k0, uint32_t 
 template <int NA>
 __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S, const float *M, const Params &p,
                                             int px, int py, unsigned long long key, uint32_t &rgb, float &depth,
-                                            uint32_t &id)
+                                            uint32_t &id, bool colour)
 {
     if (key == ~0ull) {
         rgb = 0;
@@ -210,6 +210,11 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
     const uint32_t tri = (uint32_t)key;
     const float qk = __uint_as_float(~(uint32_t)(key >> 32));
     depth = __frcp_rn(qk);
+    if (!colour) {             // depth / id views: no attribute work
+        rgb = 0;
+        id = S.tri[tri].w;
+        return;
+    }
     if (tri != st.tri) build_shade_tri<NA>(st, S, M, p, tri);
     id = st.T.w;
     const int Px = 256 * px + 128, Py = 256 * py + 128;

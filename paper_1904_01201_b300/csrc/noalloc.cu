@@ -125,6 +125,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
         v.scene = 0;
         v.frame = i;
         v.agent = i;
+        v.outputs = HSR_OUT_RGB | HSR_OUT_DEPTH | HSR_OUT_IDS;
     }
     // Pageable source: the copy has consumed `h` when this call returns.
     if (cudaMemcpyAsync(d, h, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HSR_ERR_CUDA;

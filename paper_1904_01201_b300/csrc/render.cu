@@ -430,9 +430,12 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
 // --------------------------------------------------------------------- shade
 template <int NA>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
-                                           uint32_t frame, uint32_t agent)
+                                           uint32_t frame, uint32_t agent, uint32_t outputs)
 {
     const uint32_t W = p.width, H = p.height;
+    uint8_t *const out_rgb = (outputs & HSR_OUT_RGB) ? p.rgb : nullptr;
+    float *const out_depth = (outputs & HSR_OUT_DEPTH) ? p.depth : nullptr;
+    uint32_t *const out_ids = (outputs & HSR_OUT_IDS) ? p.ids : nullptr;
     const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
     unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
     const size_t fbase = (size_t)frame * W * H;
@@ -463,8 +466,9 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
         uint32_t rgb[4], id[4];
         float dep[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k]);
-        if (sigma > 0.f) {
+        for (int k = 0; k < 4; k++)
+            shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k], out_rgb != nullptr);
+        if (sigma > 0.f && out_depth) {
             const uint32_t k0 = p.dyn[4], k1 = p.dyn[5];
 #pragma unroll
             for (int k = 0; k < 4; k++)
@@ -474,20 +478,24 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
         }
         const size_t o = fbase + pi;
         if (vec) {
-            // four packed 24-bit RGB values -> three little-endian words
-            uint32_t *r32 = reinterpret_cast<uint32_t *>(p.rgb + 3 * o);
-            r32[0] = rgb[0] | (rgb[1] << 24);
-            r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
-            r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
-            if (p.depth) *reinterpret_cast<float4 *>(p.depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
-            if (p.ids) *reinterpret_cast<uint4 *>(p.ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
+            if (out_rgb) {
+                // four packed 24-bit RGB values -> three little-endian words
+                uint32_t *r32 = reinterpret_cast<uint32_t *>(out_rgb + 3 * o);
+                r32[0] = rgb[0] | (rgb[1] << 24);
+                r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
+                r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
+            }
+            if (out_depth) *reinterpret_cast<float4 *>(out_depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
+            if (out_ids) *reinterpret_cast<uint4 *>(out_ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
         } else {
             for (uint32_t k = 0; k < n; k++) {
-                p.rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
-                p.rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
-                p.rgb[3 * (o + k) + 2] = (uint8_t)((rgb[k] >> 16) & 255u);
-                if (p.depth) p.depth[o + k] = dep[k];
-                if (p.ids) p.ids[o + k] = id[k];
+                if (out_rgb) {
+                    out_rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
+                    out_rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
+                    out_rgb[3 * (o + k) + 2] = (uint8_t)((rgb[k] >> 16) & 255u);
+                }
+                if (out_depth) out_depth[o + k] = dep[k];
+                if (out_ids) out_ids[o + k] = id[k];
             }
         }
     }
@@ -497,7 +505,7 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
 {
     __shared__ float sM[12];
     __shared__ SceneDev sS;
-    __shared__ uint32_t s_frame, s_agent;
+    __shared__ uint32_t s_frame, s_agent, s_outputs;
     const uint32_t vi = view0 + blockIdx.y;
     if (vi >= p.dyn[0]) return;
     if (threadIdx.x < 12) sM[threadIdx.x] = p.views[vi].M[threadIdx.x];
@@ -505,14 +513,18 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
         sS = p.scenes[p.views[vi].scene];
         s_frame = p.views[vi].frame;
         s_agent = p.views[vi].agent;
+        s_outputs = p.views[vi].outputs;
     }
     __syncthreads();
-    if (sS.color_mode == kColorTexture)
-        shade_rows<2>(p, sS, sM, vi, s_frame, s_agent);
+    const uint32_t outputs = s_outputs;
+    if (!(outputs & HSR_OUT_RGB))
+        shade_rows<0>(p, sS, sM, vi, s_frame, s_agent, outputs);
+    else if (sS.color_mode == kColorTexture)
+        shade_rows<2>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else if (sS.color_mode == kColorVertex)
-        shade_rows<3>(p, sS, sM, vi, s_frame, s_agent);
+        shade_rows<3>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else
-        shade_rows<0>(p, sS, sM, vi, s_frame, s_agent);
+        shade_rows<0>(p, sS, sM, vi, s_frame, s_agent, outputs);
 }
 
 constexpr size_t kRasterSmem = kRasterWarps * kMeshletVerts * (sizeof(EyeHot) + sizeof(EyeCold)) +

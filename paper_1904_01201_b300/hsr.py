@@ -59,6 +59,15 @@ class hsr_depth_noise(ctypes.Structure):
                 ("agent_ids", ctypes.c_void_p)]
 
 
+class hsr_view(ctypes.Structure):
+    _fields_ = [("pose", hsr_pose), ("scene", ctypes.c_uint32), ("frame", ctypes.c_uint32),
+                ("outputs", ctypes.c_uint32)]
+
+
+HSR_OUT_RGB, HSR_OUT_DEPTH, HSR_OUT_IDS = 1, 2, 4
+VIEW_DTYPE = np.dtype([("pose", np.float32, 7), ("scene", np.uint32), ("frame", np.uint32), ("outputs", np.uint32)])
+
+
 class hsr_navmap(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_float), ("z0", ctypes.c_float), ("cell", ctypes.c_float), ("nx", ctypes.c_uint32),
                 ("nz", ctypes.c_uint32), ("grid", ctypes.c_void_p)]
@@ -128,6 +137,9 @@ def _load():
                               ctypes.POINTER(hsr_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
         "hsr_batch_destroy": ([P], ctypes.c_int),
+        "hsr_render_views": ([P, U32, P, U32, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
+                              ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
+        "hsr_batch_render_views": ([P, P, U32, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_agents_create": ([P, U32, P, U32, P, P, ctypes.POINTER(hsr_actuation), ctypes.POINTER(P)],
                               ctypes.c_int),
         "hsr_agents_get_poses": ([P, P, P], ctypes.c_int),
@@ -307,6 +319,40 @@ def hsr_render_noisy(handles: Sequence[int], scene_of_agent, poses, intr, width,
                                ctypes.byref(as_intrinsics(intr)), int(width), int(height), _dev_ptr(rgb),
                                _dev_ptr(depth), _dev_ptr(ids), None if nz is None else ctypes.byref(nz),
                                _stream_ptr(stream))
+    del keep
+    return st
+
+
+def make_views(poses, scene, frames, outputs=0) -> np.ndarray:
+    """A view list (VIEW_DTYPE) from poses [N,7] and per-view (or scalar) scene,
+    frame and output mask."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    v = np.zeros(poses.shape[0], dtype=VIEW_DTYPE)
+    v["pose"] = poses
+    v["scene"] = scene
+    v["frame"] = frames
+    v["outputs"] = outputs
+    return v
+
+
+def hsr_render_views(handles: Sequence[int], views, n_frames, intr, width, height, rgb, depth, ids=None,
+                     noise_sigma=None, noise_seed=0, agent_ids=None, stream=None) -> int:
+    views = np.ascontiguousarray(views, dtype=VIEW_DTYPE)
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    nz, keep = _noise(noise_sigma, noise_seed, agent_ids)
+    st = _lib.hsr_render_views(arr, len(handles), _np_ptr(views), len(views), int(n_frames),
+                               ctypes.byref(as_intrinsics(intr)), int(width), int(height), _dev_ptr(rgb),
+                               _dev_ptr(depth), _dev_ptr(ids), None if nz is None else ctypes.byref(nz),
+                               _stream_ptr(stream))
+    del keep
+    return st
+
+
+def hsr_batch_render_views(batch, views, noise_sigma=None, noise_seed=0, agent_ids=None, stream=None) -> int:
+    views = np.ascontiguousarray(views, dtype=VIEW_DTYPE)
+    nz, keep = _noise(noise_sigma, noise_seed, agent_ids)
+    st = _lib.hsr_batch_render_views(ctypes.c_void_p(batch), _np_ptr(views), len(views),
+                                     None if nz is None else ctypes.byref(nz), _stream_ptr(stream))
     del keep
     return st
 
@@ -537,6 +583,22 @@ def render_batch(scenes: Sequence[SceneHandle], scene_of_agent, poses, intr, wid
                           out["depth"], out.get("ids"), stream)
     if st != HSR_OK:
         raise HsrError(st, "hsr_render_batch")
+    return out
+
+
+def render_semantic(scene: SceneHandle, sem_scene: SceneHandle, poses, intr, width: int, height: int, out=None,
+                    stream=None):
+    """Colour and depth from `scene`, ids from a separate semantic mesh
+    `sem_scene`, at the same poses, in one call (two views per frame)."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    n = poses.shape[0]
+    out = out or alloc_outputs(n, width, height, True)
+    f = np.arange(n, dtype=np.uint32)
+    views = np.concatenate([make_views(poses, 0, f, HSR_OUT_RGB | HSR_OUT_DEPTH), make_views(poses, 1, f, HSR_OUT_IDS)])
+    st = hsr_render_views([scene.handle, sem_scene.handle], views, n, intr, width, height, out["rgb"], out["depth"],
+                          out["ids"], stream=stream)
+    if st != HSR_OK:
+        raise HsrError(st, "hsr_render_views")
     return out
 
 

@@ -568,6 +568,14 @@ def make_house(seed: int = 0, target_tris: int = 1_000_000, atlas_size: int = 40
                   atlas_kind, name=f"house{seed}-{target_tris}")
 
 
+def make_semantic_mesh(seed: int = 0, target_tris: int = 3_000_000, n_objects: int = 300) -> Scene:
+    """The semantic mesh of make_house(seed): the same layout tessellated to
+    `target_tris` triangles, no colour, a per-object semantic id per triangle
+    (Table 2 footnote: semantic sensors read separate, denser meshes)."""
+    return _build(_layout_house(seed, n_objects), target_tris, seed, None, False, True,
+                  name=f"house{seed}-sem-{target_tris}")
+
+
 def _free(scene: Scene, x: float, z: float, clear: float) -> bool:
     inside = any(r[0] + clear <= x <= r[2] - clear and r[1] + clear <= z <= r[3] - clear for r in scene.rooms)
     if not inside:
