@@ -56,6 +56,8 @@ def lib():
         _lib.oracle_render.restype = ctypes.c_int
         _lib.oracle_render_noisy.argtypes = _lib.oracle_render.argtypes + [ctypes.c_float, ctypes.c_uint64, P]
         _lib.oracle_render_noisy.restype = ctypes.c_int
+        _lib.oracle_render_full.argtypes = _lib.oracle_render_noisy.argtypes + [ctypes.c_int, P]
+        _lib.oracle_render_full.restype = ctypes.c_int
         _lib.oracle_philox4x32_10.argtypes = [P, P, P]
         _lib.oracle_philox4x32_10.restype = None
         _lib.oracle_actuate.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_float,
@@ -108,13 +110,15 @@ def camera(pose) -> np.ndarray:
 
 def render(scene, poses, intr, width: int, height: int, nthreads: int = 0,
            ids: bool = True, coverage: bool = False, noise_sigma: float = 0.0, noise_seed: int = 0,
-           agent_ids=None) -> dict:
+           agent_ids=None, trilinear: bool = False, lod: bool = False) -> dict:
     """Render every pose of `poses` ([N,7]) and return numpy outputs.
 
     `scene` has attributes xyz, idx, uv, vrgb, atlas, sem (see workloads.Scene);
     `intr` is (fx, fy, cx, cy, znear, zfar).  Returns rgb [N,H,W,3] u8,
     depth [N,H,W] f32, ids [N,H,W] u32 and, if asked, cover [N,H,W] u32, the
-    number of fragments that passed the coverage test at each pixel.
+    number of fragments that passed the coverage test at each pixel, and lod
+    [N,H,W] f32, the mip level-of-detail lambda of each textured pixel (NaN
+    elsewhere; trilinear sampling only).
     """
     xyz = np.ascontiguousarray(scene.xyz, dtype=np.float32)
     idx = np.ascontiguousarray(scene.idx, dtype=np.uint32)
@@ -133,10 +137,12 @@ def render(scene, poses, intr, width: int, height: int, nthreads: int = 0,
     if atlas is not None:
         ah, aw = atlas.shape[0], atlas.shape[1]
     agents = None if agent_ids is None else np.ascontiguousarray(agent_ids, dtype=np.uint32).reshape(n)
-    st = lib().oracle_render_noisy(_ptr(xyz), xyz.shape[0], _ptr(idx), idx.shape[0], _ptr(uv), _ptr(vrgb),
-                                   _ptr(atlas), aw, ah, _ptr(sem), _ptr(poses), n, _ptr(intr), width, height,
-                                   _ptr(rgb), _ptr(depth), _ptr(out_ids), _ptr(cover), int(nthreads),
-                                   float(noise_sigma), int(noise_seed) & ((1 << 64) - 1), _ptr(agents))
+    out_lod = np.full((n, height, width), np.nan, dtype=np.float32) if lod else None
+    st = lib().oracle_render_full(_ptr(xyz), xyz.shape[0], _ptr(idx), idx.shape[0], _ptr(uv), _ptr(vrgb),
+                                  _ptr(atlas), aw, ah, _ptr(sem), _ptr(poses), n, _ptr(intr), width, height,
+                                  _ptr(rgb), _ptr(depth), _ptr(out_ids), _ptr(cover), int(nthreads),
+                                  float(noise_sigma), int(noise_seed) & ((1 << 64) - 1), _ptr(agents),
+                                  1 if trilinear else 0, _ptr(out_lod))
     if st != OK:
         raise ValueError(f"oracle_render failed with status {st}")
     out = {"rgb": rgb, "depth": depth}
@@ -144,4 +150,6 @@ def render(scene, poses, intr, width: int, height: int, nthreads: int = 0,
         out["ids"] = out_ids
     if coverage:
         out["cover"] = cover
+    if lod:
+        out["lod"] = out_lod
     return out

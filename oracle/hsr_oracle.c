@@ -40,6 +40,17 @@
  *              vertex colours; channel = min(255, floor(c + 0.5)).
  *   outputs  : RGB u8, depth 1/q (float), id = semantic[tri] or tri;
  *              background RGB 0, depth 0, id 0xFFFFFFFF.
+ *   mipmaps  : optional trilinear sampling of minified textures: level l+1
+ *              is max(1, W_l >> 1) x max(1, H_l >> 1) texels, each the
+ *              rounded mean (a + b + c + d + 2) >> 2 of its 2x2 block of level
+ *              l (block coordinates clamped to level l); lambda = log2(rho),
+ *              rho = max over x and y of the texel-space length of the
+ *              perspective-correct uv derivative at the pixel centre (from the
+ *              exact derivatives of the weights E_k q_k); lambda <= 0 samples
+ *              level 0 bilinearly (the plain rule above); otherwise the
+ *              bilinear samples of levels floor(lambda) and floor(lambda) + 1
+ *              (the last level beyond it) blend with weight frac(lambda),
+ *              each level sampled at (u W_l - 0.5, v H_l - 0.5), then round.
  *   noise    : optional noisy depth (Appendix C: iid Gaussian, mean 0,
  *              std sigma, added to inverse depth per pixel): for a hit pixel
  *              q' = q + sigma z, z = sqrt(-2 ln u1) cos(2 pi u2) (fp64), with
@@ -183,6 +194,10 @@ typedef struct {
     const uint32_t *idx; uint32_t nt;
     const float *uv; const uint8_t *vrgb;
     const uint8_t *atlas; uint32_t aw, ah;
+    /* mip chain (trilinear sampling): level 0 is the atlas */
+    int nlev;
+    const uint8_t *mip[16]; uint32_t mw[16], mh[16];
+    float *lod;             /* optional per-pixel lambda of the shaded fragment */
     const uint32_t *sem;
     /* views */
     const float *poses; uint32_t n;
@@ -201,13 +216,50 @@ typedef struct {
 static int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 static int64_t ceildiv(int64_t a, int64_t b) { return -floordiv(-a, b); }
 
-static double texel(const ojob *J, int64_t x, int64_t y, int c)
+static double texel_of(const uint8_t *img, uint32_t w, uint32_t h, int64_t x, int64_t y, int c)
 {
     if (x < 0) x = 0;
-    if (x > (int64_t)J->aw - 1) x = J->aw - 1;
+    if (x > (int64_t)w - 1) x = w - 1;
     if (y < 0) y = 0;
-    if (y > (int64_t)J->ah - 1) y = J->ah - 1;
-    return (double)J->atlas[((size_t)y * J->aw + (size_t)x) * 4 + c];
+    if (y > (int64_t)h - 1) y = h - 1;
+    return (double)img[((size_t)y * w + (size_t)x) * 4 + c];
+}
+
+/* bilinear sample (unrounded, channels 0..2) of an RGBA8 image at (u, v),
+   clamp to edge, texel centres at half-integers */
+static void bilinear(const uint8_t *img, uint32_t w, uint32_t h, double u, double vv, double out[3])
+{
+    double sx = u * w - 0.5, sy = vv * h - 0.5;
+    if (!(sx >= -1.0)) sx = -1.0;
+    if (sx > w) sx = w;
+    if (!(sy >= -1.0)) sy = -1.0;
+    if (sy > h) sy = h;
+    double x0 = floor(sx), y0 = floor(sy);
+    double ax = sx - x0, ay = sy - y0;
+    int64_t ix = (int64_t)x0, iy = (int64_t)y0;
+    for (int c = 0; c < 3; c++) {
+        double c00 = texel_of(img, w, h, ix, iy, c), c10 = texel_of(img, w, h, ix + 1, iy, c);
+        double c01 = texel_of(img, w, h, ix, iy + 1, c), c11 = texel_of(img, w, h, ix + 1, iy + 1, c);
+        out[c] = (1 - ax) * (1 - ay) * c00 + ax * (1 - ay) * c10 + (1 - ax) * ay * c01 + ax * ay * c11;
+    }
+}
+
+/* level l+1 of a mip chain from level l (w x h): rounded 2x2 means */
+static void mip_down(const uint8_t *src, uint32_t w, uint32_t h, uint8_t *dst, uint32_t w2, uint32_t h2)
+{
+    for (uint32_t y = 0; y < h2; y++)
+        for (uint32_t x = 0; x < w2; x++)
+            for (int c = 0; c < 4; c++) {
+                unsigned sum = 2;
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++) {
+                        uint32_t sx = 2 * x + dx, sy = 2 * y + dy;
+                        if (sx > w - 1) sx = w - 1;
+                        if (sy > h - 1) sy = h - 1;
+                        sum += src[((size_t)sy * w + sx) * 4 + c];
+                    }
+                dst[((size_t)y * w2 + x) * 4 + c] = (uint8_t)(sum >> 2);
+            }
 }
 
 static uint8_t round_channel(double c)
@@ -219,37 +271,67 @@ static uint8_t round_channel(double c)
 }
 
 /* shade one fragment in fp64: weights E_k * q_k (perspective-correct) */
-static void shade(const ojob *J, int mode, const overt *v[3], const float q[3], const int64_t E[3],
-                  uint8_t out[3])
+/* shade one fragment in fp64: weights E_k * q_k (perspective-correct);
+   dEx[k], dEy[k]: change of E_k per sub-pixel step in x and in y.  Returns
+   lambda for trilinear sampling (NAN when not computed). */
+static double shade(const ojob *J, int mode, const overt *v[3], const float q[3], const int64_t E[3],
+                    const int64_t dEx[3], const int64_t dEy[3], uint8_t out[3])
 {
     double w0 = (double)E[0] * (double)q[0];
     double w1 = (double)E[1] * (double)q[1];
     double w2 = (double)E[2] * (double)q[2];
     double s = w0 + w1 + w2;
     double l0 = w0 / s, l1 = w1 / s, l2 = w2 / s;
+    double lambda = NAN;
     if (mode == 1) {
         double u = l0 * v[0]->attr[0] + l1 * v[1]->attr[0] + l2 * v[2]->attr[0];
         double vv = l0 * v[0]->attr[1] + l1 * v[1]->attr[1] + l2 * v[2]->attr[1];
-        double sx = u * J->aw - 0.5, sy = vv * J->ah - 0.5;
-        if (!(sx >= -1.0)) sx = -1.0;
-        if (sx > J->aw) sx = J->aw;
-        if (!(sy >= -1.0)) sy = -1.0;
-        if (sy > J->ah) sy = J->ah;
-        double x0 = floor(sx), y0 = floor(sy);
-        double ax = sx - x0, ay = sy - y0;
-        int64_t ix = (int64_t)x0, iy = (int64_t)y0;
-        for (int c = 0; c < 3; c++) {
-            double c00 = texel(J, ix, iy, c), c10 = texel(J, ix + 1, iy, c);
-            double c01 = texel(J, ix, iy + 1, c), c11 = texel(J, ix + 1, iy + 1, c);
-            double val = (1 - ax) * (1 - ay) * c00 + ax * (1 - ay) * c10 + (1 - ax) * ay * c01 + ax * ay * c11;
-            out[c] = round_channel(val);
+        double val[3];
+        if (J->nlev > 0) {
+            /* d(l_k)/dx = (dw_k/dx - l_k dS/dx) / S, one pixel = 256 sub-pixels */
+            const double l[3] = {l0, l1, l2};
+            double dwx[3], dwy[3], dsx = 0, dsy = 0;
+            for (int k = 0; k < 3; k++) {
+                dwx[k] = 256.0 * (double)dEx[k] * (double)q[k];
+                dwy[k] = 256.0 * (double)dEy[k] * (double)q[k];
+                dsx += dwx[k];
+                dsy += dwy[k];
+            }
+            double dudx = 0, dvdx = 0, dudy = 0, dvdy = 0;
+            for (int k = 0; k < 3; k++) {
+                const double gx = (dwx[k] - l[k] * dsx) / s, gy = (dwy[k] - l[k] * dsy) / s;
+                dudx += gx * v[k]->attr[0];
+                dvdx += gx * v[k]->attr[1];
+                dudy += gy * v[k]->attr[0];
+                dvdy += gy * v[k]->attr[1];
+            }
+            const double rx = sqrt((dudx * J->aw) * (dudx * J->aw) + (dvdx * J->ah) * (dvdx * J->ah));
+            const double ry = sqrt((dudy * J->aw) * (dudy * J->aw) + (dvdy * J->ah) * (dvdy * J->ah));
+            lambda = log2(rx > ry ? rx : ry);
+            if (!(lambda > 0.0)) {
+                bilinear(J->mip[0], J->mw[0], J->mh[0], u, vv, val);
+            } else if (lambda >= (double)(J->nlev - 1)) {
+                const int L = J->nlev - 1;
+                bilinear(J->mip[L], J->mw[L], J->mh[L], u, vv, val);
+            } else {
+                const int l0i = (int)floor(lambda);
+                const double f = lambda - (double)l0i;
+                double a[3], b[3];
+                bilinear(J->mip[l0i], J->mw[l0i], J->mh[l0i], u, vv, a);
+                bilinear(J->mip[l0i + 1], J->mw[l0i + 1], J->mh[l0i + 1], u, vv, b);
+                for (int c = 0; c < 3; c++) val[c] = (1.0 - f) * a[c] + f * b[c];
+            }
+        } else {
+            bilinear(J->atlas, J->aw, J->ah, u, vv, val);
         }
+        for (int c = 0; c < 3; c++) out[c] = round_channel(val[c]);
     } else if (mode == 2) {
         for (int c = 0; c < 3; c++)
             out[c] = round_channel(l0 * v[0]->attr[c] + l1 * v[1]->attr[c] + l2 * v[2]->attr[c]);
     } else {
         out[0] = out[1] = out[2] = 255;
     }
+    return lambda;
 }
 
 static overt clip_point(const overt *p, const overt *r, float znear, int nattr)
@@ -354,9 +436,12 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
             const int32_t ex[3][2] = {{X1, X2}, {X2, X0}, {X0, X1}};
             const int32_t ey[3][2] = {{Y1, Y2}, {Y2, Y0}, {Y0, Y1}};
             int tl[3];
+            int64_t dEx[3], dEy[3];
             for (int k = 0; k < 3; k++) {
                 int64_t dx = (int64_t)ex[k][1] - ex[k][0], dy = (int64_t)ey[k][1] - ey[k][0];
                 tl[k] = (dy < 0) || (dy == 0 && dx > 0);
+                dEx[k] = -dy;
+                dEy[k] = dx;
             }
             int32_t mnx = X0, mxx = X0, mny = Y0, mxy = Y0;
             if (X1 < mnx) mnx = X1;
@@ -398,7 +483,8 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
                     const uint64_t key = ((uint64_t)(~f2u(qq)) << 32) | t;
                     if (key < best[pix]) {
                         best[pix] = key;
-                        shade(J, mode, sv, sq, E, rgb + 3 * pix);
+                        const double lam = shade(J, mode, sv, sq, E, dEx, dEy, rgb + 3 * pix);
+                        if (J->lod) J->lod[(size_t)f * npx + pix] = (float)lam;
                         dep[pix] = dd;
                         if (ids) ids[pix] = J->sem ? J->sem[t] : t;
                     }
@@ -450,11 +536,15 @@ int oracle_render(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t n
                                ids, cover, nthreads, 0.0f, 0, NULL);
 }
 
-int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
-                        const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
-                        const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
-                        uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
-                        int nthreads, float noise_sigma, uint64_t noise_seed, const uint32_t *agent_ids)
+/* The full entry: trilinear != 0 samples textures through a mip chain of the
+   atlas; lod (optional, [n][H][W], caller-initialised) receives lambda of
+   each shaded textured pixel. */
+int oracle_render_full(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
+                       const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
+                       const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
+                       uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
+                       int nthreads, float noise_sigma, uint64_t noise_seed, const uint32_t *agent_ids,
+                       int trilinear, float *lod)
 {
     if (!xyz || !idx || !poses || !intr || !rgb || !depth || n == 0 || W == 0 || H == 0) return OR_ERR_ARG;
     for (size_t i = 0; i < 3 * (size_t)nt; i++)
@@ -462,9 +552,34 @@ int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint
     if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (nthreads < 1) nthreads = 1;
     if ((uint32_t)nthreads > n) nthreads = (int)n;
+    /* mip chain: level 0 is the atlas, halving down to 1 x 1 */
+    int nlev = 0;
+    uint8_t *levels[16] = {0};
+    uint32_t mw[16], mh[16];
+    if (trilinear && atlas && aw && ah) {
+        mw[0] = aw; mh[0] = ah;
+        nlev = 1;
+        while ((mw[nlev - 1] > 1 || mh[nlev - 1] > 1) && nlev < 16) {
+            mw[nlev] = mw[nlev - 1] > 1 ? mw[nlev - 1] >> 1 : 1;
+            mh[nlev] = mh[nlev - 1] > 1 ? mh[nlev - 1] >> 1 : 1;
+            levels[nlev] = (uint8_t *)malloc((size_t)mw[nlev] * mh[nlev] * 4);
+            if (!levels[nlev]) {
+                for (int l = 1; l < nlev; l++) free(levels[l]);
+                return OR_ERR_OOM;
+            }
+            mip_down(nlev == 1 ? atlas : levels[nlev - 1], mw[nlev - 1], mh[nlev - 1], levels[nlev], mw[nlev],
+                     mh[nlev]);
+            nlev++;
+        }
+    }
     ojob *jobs = (ojob *)calloc((size_t)nthreads, sizeof(ojob));
     pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
-    if (!jobs || !th) { free(jobs); free(th); return OR_ERR_OOM; }
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        for (int l = 1; l < nlev; l++) free(levels[l]);
+        return OR_ERR_OOM;
+    }
     for (int i = 0; i < nthreads; i++) {
         ojob *J = &jobs[i];
         J->xyz = xyz; J->nv = nv; J->idx = idx; J->nt = nt;
@@ -474,6 +589,13 @@ int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint
         J->znear = intr[4]; J->zfar = intr[5];
         J->W = W; J->H = H; J->rgb = rgb; J->depth = depth; J->ids = ids; J->cover = cover;
         J->noise_sigma = noise_sigma; J->noise_seed = noise_seed; J->agent_ids = agent_ids;
+        J->nlev = nlev;
+        for (int l = 0; l < nlev; l++) {
+            J->mip[l] = l == 0 ? atlas : levels[l];
+            J->mw[l] = mw[l];
+            J->mh[l] = mh[l];
+        }
+        J->lod = lod;
         J->f0 = (uint32_t)((uint64_t)n * i / nthreads);
         J->f1 = (uint32_t)((uint64_t)n * (i + 1) / nthreads);
     }
@@ -490,5 +612,16 @@ int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint
     }
     free(jobs);
     free(th);
+    for (int l = 1; l < nlev; l++) free(levels[l]);
     return st;
+}
+
+int oracle_render_noisy(const float *xyz, uint32_t nv, const uint32_t *idx, uint32_t nt,
+                        const float *uv, const uint8_t *vrgb, const uint8_t *atlas, uint32_t aw, uint32_t ah,
+                        const uint32_t *sem, const float *poses, uint32_t n, const float *intr,
+                        uint32_t W, uint32_t H, uint8_t *rgb, float *depth, uint32_t *ids, uint32_t *cover,
+                        int nthreads, float noise_sigma, uint64_t noise_seed, const uint32_t *agent_ids)
+{
+    return oracle_render_full(xyz, nv, idx, nt, uv, vrgb, atlas, aw, ah, sem, poses, n, intr, W, H, rgb, depth,
+                              ids, cover, nthreads, noise_sigma, noise_seed, agent_ids, 0, NULL);
 }
