@@ -160,6 +160,25 @@ HSR_API int hsr_render_noisy(const hsr_scene *const *scenes, uint32_t n_scenes,
                      void *cuda_stream);
 
 /*
+ * Texture sampling of a textured scene (the paper does not state its
+ * filtering): HSR_SAMPLE_BILINEAR (default) samples the atlas bilinearly;
+ * HSR_SAMPLE_TRILINEAR samples minified textures through a mip chain built
+ * from the atlas on the first call: level l+1 is max(1, W_l >> 1) x
+ * max(1, H_l >> 1) texels, each the rounded mean (a + b + c + d + 2) >> 2 of
+ * its 2x2 block of level l (reads past the last row or column repeat it).
+ * Per pixel, lambda = log2(rho), rho the larger texel-space length of the
+ * perspective-correct uv derivative along x and along y at the pixel centre;
+ * lambda <= 0 samples level 0 bilinearly (as HSR_SAMPLE_BILINEAR); otherwise
+ * the bilinear samples of levels floor(lambda) and floor(lambda) + 1 (the
+ * last level beyond it) are blended with weight frac(lambda), each level
+ * sampled at (u W_l - 0.5, v H_l - 0.5), and rounded. Applies to renders
+ * issued after the call returns; HSR_ERR_INVALID_ARG for an untextured scene
+ * or an unknown mode.
+ */
+enum { HSR_SAMPLE_BILINEAR = 0, HSR_SAMPLE_TRILINEAR = 1 };
+HSR_API int hsr_scene_set_sampling(hsr_scene *scene, int mode);
+
+/*
  * General view lists: each view names its scene, pose, output frame and the
  * outputs it writes, so one call can render several sensors per agent, such
  * as the semantic sensor of Table 2 (footnote), whose ids come from a

@@ -1213,6 +1213,55 @@ int hsr_get_stage_stats(uint32_t *counts)
     return e == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
 }
 
+int hsr_scene_set_sampling(hsr_scene *s, int mode)
+{
+    if (!s || (mode != HSR_SAMPLE_BILINEAR && mode != HSR_SAMPLE_TRILINEAR)) return HSR_ERR_INVALID_ARG;
+    SceneDev &d = s->dev;
+    if (mode == HSR_SAMPLE_TRILINEAR && d.color_mode != kColorTexture) return HSR_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    cudaError_t e = cudaSuccess;
+    if (mode == HSR_SAMPLE_TRILINEAR && d.n_levels == 0) {
+        // level sizes and offsets: halve (at least 1) down to 1 x 1
+        uint32_t w = d.atlas_w, h = d.atlas_h, n = 1;
+        uint32_t off[16] = {0};
+        uint64_t total = 0;
+        while ((w > 1 || h > 1) && n < 16) {
+            w = w > 1 ? w >> 1 : 1;
+            h = h > 1 ? h >> 1 : 1;
+            off[n] = (uint32_t)total;
+            total += (uint64_t)w * h;
+            n++;
+        }
+        uint32_t *mips = nullptr;
+        if (total) {
+            e = cudaMalloc(&mips, total * sizeof(uint32_t));
+            if (e == cudaSuccess) s->allocs.push_back(mips);
+            uint32_t pw = d.atlas_w, ph = d.atlas_h;
+            for (uint32_t l = 1; l < n && e == cudaSuccess; l++) {
+                const uint32_t lw = pw > 1 ? pw >> 1 : 1, lh = ph > 1 ? ph >> 1 : 1;
+                const uint32_t *src = l == 1 ? d.atlas : mips + off[l - 1];
+                e = launch_mip_down(src, pw, ph, mips + off[l], lw, lh, nullptr);
+                pw = lw;
+                ph = lh;
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+        }
+        if (e == cudaSuccess) {
+            d.mips = mips;
+            d.n_levels = n;
+            for (int l = 0; l < 16; l++) d.mip_off[l] = off[l];
+        }
+    }
+    if (e == cudaSuccess) {
+        d.sample_mode = (uint32_t)mode;
+        e = cudaMemcpy(s->dev_desc, &d, sizeof(SceneDev), cudaMemcpyHostToDevice);
+    }
+    cudaSetDevice(prev);
+    return e == cudaSuccess ? HSR_OK : cuda_status(e);
+}
+
 int hsr_scene_free(hsr_scene *scene)
 {
     free_scene(scene);

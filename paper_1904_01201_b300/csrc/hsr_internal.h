@@ -46,7 +46,10 @@ struct SceneDev {
     uint32_t atlas_w, atlas_h;
     uint32_t n_groups, n_meshlets, n_tris, n_verts;
     int color_mode;
-    int pad_;
+    uint32_t sample_mode;      // HSR_SAMPLE_BILINEAR or HSR_SAMPLE_TRILINEAR
+    const uint32_t *mips;      // mip levels 1.. of the atlas, RGBA8 texels (trilinear sampling)
+    uint32_t n_levels;         // levels including the atlas itself (level 0)
+    uint32_t mip_off[16];      // texel offset of level l in `mips` (l >= 1); level l is max(1, W >> l) x max(1, H >> l)
 };
 
 // One rendered view: world-to-eye matrix (rows of a 3x4), the six world-space
@@ -181,6 +184,11 @@ struct AgentsView {
     const hsr_scene_info *info;        // [n_scenes]
 };
 bool agents_view(const hsr_agents *a, AgentsView &out);
+
+// Mip level l+1 (w2 x h2) of level l (w x h): per channel the rounded mean
+// (a + b + c + d + 2) >> 2 of each 2x2 block, block reads clamped to level l.
+cudaError_t launch_mip_down(const uint32_t *src, uint32_t w, uint32_t h, uint32_t *dst, uint32_t w2, uint32_t h2,
+                            cudaStream_t stream);
 
 // Actuation pass of a step batch: applies each view's action to its agent
 // state and writes the view's camera (n_cap: capacity, the grid size).

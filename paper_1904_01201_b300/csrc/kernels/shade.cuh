@@ -48,6 +48,58 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     return out;
 }
 
+// Unrounded bilinear sample (channels 0..2) of mip level l: level 0 is the
+// atlas, level l is max(1, W >> l) x max(1, H >> l), same addressing rules.
+__device__ __forceinline__ void sample_level(const SceneDev &S, uint32_t l, float u, float v, float (&c)[3])
+{
+    const uint32_t Wl = max(1u, S.atlas_w >> l), Hl = max(1u, S.atlas_h >> l);
+    const uint32_t *img = l == 0 ? S.atlas : S.mips + S.mip_off[l];
+    const float aw = (float)Wl, ah = (float)Hl;
+    float s = __fmaf_rn(u, aw, -0.5f), t = __fmaf_rn(v, ah, -0.5f);
+    s = fminf(fmaxf(s, -1.0f), aw);
+    t = fminf(fmaxf(t, -1.0f), ah);
+    const float fs = floorf(s), ft = floorf(t);
+    const float ax = __fsub_rn(s, fs), ay = __fsub_rn(t, ft);
+    const int ix = (int)fs, iy = (int)ft;
+    const int W = (int)Wl, H = (int)Hl;
+    const int x0 = min(max(ix, 0), W - 1), x1 = min(max(ix + 1, 0), W - 1);
+    const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
+    const uint32_t c00 = __ldg(img + (size_t)y0 * W + x0), c10 = __ldg(img + (size_t)y0 * W + x1);
+    const uint32_t c01 = __ldg(img + (size_t)y1 * W + x0), c11 = __ldg(img + (size_t)y1 * W + x1);
+    const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const float v00 = (float)((c00 >> (8 * ch)) & 255u), v10 = (float)((c10 >> (8 * ch)) & 255u);
+        const float v01 = (float)((c01 >> (8 * ch)) & 255u), v11 = (float)((c11 >> (8 * ch)) & 255u);
+        const float top = __fmaf_rn(ax, v10, __fmul_rn(gx, v00));
+        const float bot = __fmaf_rn(ax, v11, __fmul_rn(gx, v01));
+        c[ch] = __fmaf_rn(ay, bot, __fmul_rn(gy, top));
+    }
+}
+
+// Trilinear sample at level of detail lambda: lambda <= 0 is the plain
+// bilinear rule; beyond the last level, that level; otherwise the two
+// neighbouring levels blended by frac(lambda), then rounded.
+__device__ __forceinline__ uint32_t sample_trilinear(const SceneDev &S, float u, float v, float lambda)
+{
+    if (!(lambda > 0.0f)) return sample_bilinear(S, u, v);
+    const uint32_t last = S.n_levels - 1;
+    float c[3];
+    if (lambda >= (float)last) {
+        sample_level(S, last, u, v, c);
+    } else {
+        const float fl = floorf(lambda);
+        const uint32_t l0 = (uint32_t)fl;
+        const float f = __fsub_rn(lambda, fl), g = __fsub_rn(1.0f, f);
+        float a[3], b[3];
+        sample_level(S, l0, u, v, a);
+        sample_level(S, l0 + 1, u, v, b);
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) c[ch] = __fmaf_rn(f, b[ch], __fmul_rn(g, a[ch]));
+    }
+    return round_channel(c[0]) | (round_channel(c[1]) << 8) | (round_channel(c[2]) << 16);
+}
+
 // Vertices of a triangle with NA attributes, in eye space.
 template <int NA>
 __device__ __forceinline__ void load_tri(const SceneDev &S, const float *M, const uint4 &T, CVert<NA> (&v)[3])
@@ -89,6 +141,41 @@ __device__ __forceinline__ void interp(const Tri2D &t, int Px, int Py, const flo
     for (int c = 0; c < NA; c++) attr[c] = __fmaf_rn(l0, a0[c], __fmaf_rn(l1, a1[c], __fmul_rn(l2, a2[c])));
 }
 
+// Level of detail at P of an oriented triangle with uv a0, a1, a2: lambda =
+// log2 of the larger texel-space length of the uv derivative along x and
+// along y, from the exact derivatives of the perspective-correct weights
+// w_k = E_k q_k (one pixel is 256 sub-pixel steps of each edge function).
+__device__ __forceinline__ float lod_lambda(const SceneDev &S, const Tri2D &t, int Px, int Py, const float *a0,
+                                            const float *a1, const float *a2)
+{
+    const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
+    const long long e1 = (long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2);
+    const long long e2 = (long long)(t.X1 - t.X0) * (Py - t.Y0) - (long long)(t.Y1 - t.Y0) * (Px - t.X0);
+    const float w0 = __fmul_rn(__ll2float_rn(e0), t.q0);
+    const float w1 = __fmul_rn(__ll2float_rn(e1), t.q1);
+    const float w2 = __fmul_rn(__ll2float_rn(e2), t.q2);
+    const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
+    const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
+    const float x0 = __fmul_rn(-256.0f * __ll2float_rn((long long)t.Y2 - t.Y1), t.q0);
+    const float x1 = __fmul_rn(-256.0f * __ll2float_rn((long long)t.Y0 - t.Y2), t.q1);
+    const float x2 = __fmul_rn(-256.0f * __ll2float_rn((long long)t.Y1 - t.Y0), t.q2);
+    const float y0 = __fmul_rn(256.0f * __ll2float_rn((long long)t.X2 - t.X1), t.q0);
+    const float y1 = __fmul_rn(256.0f * __ll2float_rn((long long)t.X0 - t.X2), t.q1);
+    const float y2 = __fmul_rn(256.0f * __ll2float_rn((long long)t.X1 - t.X0), t.q2);
+    const float sx = __fadd_rn(__fadd_rn(x0, x1), x2), sy = __fadd_rn(__fadd_rn(y0, y1), y2);
+    const float gx0 = __fmul_rn(__fmaf_rn(-l0, sx, x0), r), gy0 = __fmul_rn(__fmaf_rn(-l0, sy, y0), r);
+    const float gx1 = __fmul_rn(__fmaf_rn(-l1, sx, x1), r), gy1 = __fmul_rn(__fmaf_rn(-l1, sy, y1), r);
+    const float gx2 = __fmul_rn(__fmaf_rn(-l2, sx, x2), r), gy2 = __fmul_rn(__fmaf_rn(-l2, sy, y2), r);
+    const float aw = (float)S.atlas_w, ah = (float)S.atlas_h;
+    const float ux = __fmul_rn(__fmaf_rn(gx0, a0[0], __fmaf_rn(gx1, a1[0], __fmul_rn(gx2, a2[0]))), aw);
+    const float vx = __fmul_rn(__fmaf_rn(gx0, a0[1], __fmaf_rn(gx1, a1[1], __fmul_rn(gx2, a2[1]))), ah);
+    const float uy = __fmul_rn(__fmaf_rn(gy0, a0[0], __fmaf_rn(gy1, a1[0], __fmul_rn(gy2, a2[0]))), aw);
+    const float vy = __fmul_rn(__fmaf_rn(gy0, a0[1], __fmaf_rn(gy1, a1[1], __fmul_rn(gy2, a2[1]))), ah);
+    const float rx = sqrtf(__fmaf_rn(ux, ux, __fmul_rn(vx, vx)));
+    const float ry = sqrtf(__fmaf_rn(uy, uy, __fmul_rn(vy, vy)));
+    return log2f(fmaxf(rx, ry));
+}
+
 // Setup of the last triangle a thread shaded (neighbouring pixels often share it).
 template <int NA>
 struct ShadeTri {
@@ -127,7 +214,7 @@ __device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev
 // sub-triangle whose fragment at P has inverse depth qk.
 template <int NA>
 __device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M, const Params &p, const uint4 &T,
-                                              int Px, int Py, float qk, float (&attr)[3])
+                                              int Px, int Py, float qk, float (&attr)[3], float &lambda)
 {
     CVert<NA> v[3];
     load_tri<NA>(S, M, T, v);
@@ -152,15 +239,20 @@ __device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M,
         if (__float_as_uint(qq) != __float_as_uint(qk)) continue;
         // oriented order is (poly 0, poly f+2, poly f+1)
         interp<NA>(t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a, attr);
+        if constexpr (NA == 2)
+            if (S.sample_mode == HSR_SAMPLE_TRILINEAR)
+                lambda = lod_lambda(S, t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a);
         return true;
     }
     return false;
 }
 
 template <int NA>
-__device__ __forceinline__ uint32_t shade_colour(const SceneDev &S, const float (&a)[3])
+__device__ __forceinline__ uint32_t shade_colour(const SceneDev &S, const float (&a)[3], float lambda = 0.0f)
 {
-    if (NA == 2) return sample_bilinear(S, a[0], a[1]);
+    if (NA == 2)
+        return S.sample_mode == HSR_SAMPLE_TRILINEAR ? sample_trilinear(S, a[0], a[1], lambda)
+                                                     : sample_bilinear(S, a[0], a[1]);
     if (NA == 3) return round_channel(a[0]) | (round_channel(a[1]) << 8) | (round_channel(a[2]) << 16);
     return 0xFFFFFFu;
 }
@@ -219,11 +311,14 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
     id = st.T.w;
     const int Px = 256 * px + 128, Py = 256 * py + 128;
     float a[3] = {0.f, 0.f, 0.f};
+    float lambda = 0.0f;
     if (!st.clipped) {
         interp<NA>(st.t, Px, Py, st.a[0], st.a[1], st.a[2], a);
-        rgb = shade_colour<NA>(S, a);
+        if constexpr (NA == 2)
+            if (S.sample_mode == HSR_SAMPLE_TRILINEAR) lambda = lod_lambda(S, st.t, Px, Py, st.a[0], st.a[1], st.a[2]);
+        rgb = shade_colour<NA>(S, a, lambda);
     } else {
-        rgb = shade_clipped<NA>(S, M, p, st.T, Px, Py, qk, a) ? shade_colour<NA>(S, a) : 0u;
+        rgb = shade_clipped<NA>(S, M, p, st.T, Px, Py, qk, a, lambda) ? shade_colour<NA>(S, a, lambda) : 0u;
     }
 }
 

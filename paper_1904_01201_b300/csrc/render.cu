@@ -427,6 +427,36 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
     }
 }
 
+// ----------------------------------------------------------------- mip chain
+__global__ void mip_down_kernel(const uint32_t *__restrict__ src, uint32_t w, uint32_t h, uint32_t *__restrict__ dst,
+                                uint32_t w2, uint32_t h2)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w2 * h2) return;
+    const uint32_t x = i % w2, y = i / w2;
+    const uint32_t xa = min(2 * x, w - 1), xb = min(2 * x + 1, w - 1);
+    const uint32_t ya = min(2 * y, h - 1), yb = min(2 * y + 1, h - 1);
+    const uint32_t t[4] = {src[(size_t)ya * w + xa], src[(size_t)ya * w + xb], src[(size_t)yb * w + xa],
+                           src[(size_t)yb * w + xb]};
+    uint32_t out = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        uint32_t sum = 2;
+#pragma unroll
+        for (int k = 0; k < 4; k++) sum += (t[k] >> (8 * c)) & 255u;
+        out |= (sum >> 2) << (8 * c);
+    }
+    dst[i] = out;
+}
+
+cudaError_t launch_mip_down(const uint32_t *src, uint32_t w, uint32_t h, uint32_t *dst, uint32_t w2, uint32_t h2,
+                            cudaStream_t stream)
+{
+    const uint32_t n = w2 * h2;
+    mip_down_kernel<<<(n + 255) / 256, 256, 0, stream>>>(src, w, h, dst, w2, h2);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------- shade
 template <int NA>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,

@@ -65,6 +65,7 @@ class hsr_view(ctypes.Structure):
 
 
 HSR_OUT_RGB, HSR_OUT_DEPTH, HSR_OUT_IDS = 1, 2, 4
+HSR_SAMPLE_BILINEAR, HSR_SAMPLE_TRILINEAR = 0, 1
 VIEW_DTYPE = np.dtype([("pose", np.float32, 7), ("scene", np.uint32), ("frame", np.uint32), ("outputs", np.uint32)])
 
 
@@ -137,6 +138,7 @@ def _load():
                               ctypes.POINTER(hsr_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
         "hsr_batch_destroy": ([P], ctypes.c_int),
+        "hsr_scene_set_sampling": ([P, ctypes.c_int], ctypes.c_int),
         "hsr_render_views": ([P, U32, P, U32, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
                               ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_batch_render_views": ([P, P, U32, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
@@ -535,6 +537,12 @@ class SceneHandle:
     def __init__(self, scene):
         self.handle = hsr_scene_load(scene.xyz, scene.idx, scene.uv, scene.vrgb, scene.atlas, scene.sem)
         self.info = hsr_scene_get_info(self.handle)
+
+    def set_sampling(self, mode: int) -> None:
+        """HSR_SAMPLE_BILINEAR or HSR_SAMPLE_TRILINEAR (mip chain built on first use)."""
+        st = _lib.hsr_scene_set_sampling(ctypes.c_void_p(self.handle), int(mode))
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_scene_set_sampling")
 
     def close(self):
         if self.handle:
