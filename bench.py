@@ -30,7 +30,11 @@ import numpy as np  # noqa: E402
 
 METRIC = "RGB-D frames/sec (batched vs plain)"
 # kernels per render call: cull, 3 raster phases, 2 hierarchical-z builds, shade
-KERNELS_PER_CALL = 7
+def kernels_per_call(n_phases: int) -> int:
+    """Kernels one render call launches: z clear, cull, per occlusion phase a
+    raster and a large-triangle raster (and a tile-z build before every phase
+    after the first), shade."""
+    return 2 + 3 * max(1, int(n_phases))
 UNIT = "frames/s"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6400.0
@@ -283,6 +287,7 @@ def run_gpu(args, wk):
         cfg, source = tuning.ensure_tuned(wk["scenes"], handles, soa, poses, wk["intr"], W, H, out, stream,
                                           use_cache=not args.retune)
         tuned = dict(cfg, source=source)
+    launch_phases = tuned["n_phases"] if tuned else hsr.hsr_config_default().n_phases
     graph = hsr.hsr_batch_create([h.handle for h in handles], n, wk["intr"], W, H, out["rgb"], out["depth"],
                                  out.get("ids"))
 
@@ -408,7 +413,7 @@ def run_gpu(args, wk):
                           "ms_per_launch": kernel_ms_per_launch},
         "stages_ms": stages,
         "e2e": e2e,
-        "gpu_launches": KERNELS_PER_CALL * launches,
+        "gpu_launches": kernels_per_call(launch_phases) * launches,
         "render_calls": launches,
         "clocks": clocks,
         "kernel_sha": kernel_source_hash(),

@@ -380,7 +380,7 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
 
 // Kernel parameters for descriptors at `desc` and scratch at `scratch`.
 Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, const hsr_intrinsics &intr,
-                   uint8_t *rgb, float *depth, uint32_t *ids, bool reset_zbuf)
+                   uint8_t *rgb, float *depth, uint32_t *ids)
 {
     Params p{};
     uint32_t *hdr = reinterpret_cast<uint32_t *>(desc);
@@ -426,23 +426,18 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
     p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
     p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
     p.stats = stage_stats_buffer();
-    p.reset_zbuf = reset_zbuf ? 1u : 0u;
     return p;
 }
 
 // Stream work of one render: upload descriptors, optionally preset the
 // z-buffer, launch the kernels.
-cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const void *h_desc, bool preset_z,
-                           cudaStream_t stream, bool actuate = false)
+cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const void *h_desc, cudaStream_t stream,
+                           bool actuate = false)
 {
     cudaError_t e = cudaMemcpyAsync(d_desc, h_desc, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return e;
     if (actuate) {
         e = launch_actuate(p, pl.n_cap, stream);
-        if (e != cudaSuccess) return e;
-    }
-    if (preset_z) {
-        e = cudaMemsetAsync(p.zbuf, 0xFF, pl.zbytes, stream);
         if (e != cudaSuccess) return e;
     }
     return launch_render(p, pl.cfg, stream);
@@ -549,11 +544,10 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         return cuda_status(e);
     }
     const Params p = make_params(pl, static_cast<unsigned char *>(dbuf), static_cast<unsigned char *>(sbuf), *intr,
-                                 rgb, depth, ids, false);
+                                 rgb, depth, ids);
     e = cudaMemcpyAsync(dbuf, hbuf, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
     if (e == cudaSuccess) st.pending = true;
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.zbuf, 0xFF, pl.zbytes, stream);
     if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream);
     cudaError_t e1 = cudaFreeAsync(sbuf, stream);
     cudaError_t e2 = cudaFreeAsync(dbuf, stream);
@@ -935,9 +929,9 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
         if ((e = cudaHostAlloc(&b->h_desc[k], pl.desc_bytes, cudaHostAllocDefault)) != cudaSuccess) return fail(e);
         std::memset(b->h_desc[k], 0, pl.desc_bytes);
         if ((e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, *intr, rgb, depth, ids, true);
+        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, *intr, rgb, depth, ids);
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
-        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], false, cs);
+        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs);
         e = cudaStreamEndCapture(cs, &b->graph[k]);
         if (er != cudaSuccess) return fail(er);
         if (e != cudaSuccess) return fail(e);
@@ -1024,10 +1018,10 @@ int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, 
     if (!b->step_exec[k]) {
         cudaStream_t cs = nullptr;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSR_ERR_CUDA;
-        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, b->intr, b->rgb, b->depth, b->ids, true);
+        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, b->intr, b->rgb, b->depth, b->ids);
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], false, cs, true);
+            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, true);
             e = cudaStreamEndCapture(cs, &b->step_graph[k]);
             if (er != cudaSuccess) e = er;
         }

@@ -120,7 +120,6 @@ struct Params {
     // read by the kernels from device memory, so one captured graph can replay
     // batches of different sizes and scene mixes
     const uint32_t *dyn;
-    uint32_t reset_zbuf;       // shade writes ~0 back to every key it reads (persistent z-buffers)
     float inv_far;             // 1/far: a noisy inverse depth at or below it reports depth 0
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar

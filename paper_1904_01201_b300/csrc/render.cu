@@ -427,6 +427,19 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
     }
 }
 
+// ------------------------------------------------------------------ z clear
+// Every key of the active views' z-buffers set to empty (~0), 16 bytes per
+// store (the z-buffer starts on a 256-byte boundary).
+__global__ void __launch_bounds__(256) zclear_kernel(const Params p)
+{
+    const size_t n = (size_t)p.dyn[0] * p.width * p.height;
+    ulonglong2 *z2 = reinterpret_cast<ulonglong2 *>(p.zbuf);
+    const size_t n2 = n / 2;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x)
+        z2[i] = make_ulonglong2(~0ull, ~0ull);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) p.zbuf[n - 1] = ~0ull;
+}
+
 // ----------------------------------------------------------------- mip chain
 __global__ void mip_down_kernel(const uint32_t *__restrict__ src, uint32_t w, uint32_t h, uint32_t *__restrict__ dst,
                                 uint32_t w2, uint32_t h2)
@@ -482,16 +495,9 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
             const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(zb + pi);
             const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(zb + pi + 2);
             key[0] = k01.x; key[1] = k01.y; key[2] = k23.x; key[3] = k23.y;
-            if (p.reset_zbuf) {
-                *reinterpret_cast<ulonglong2 *>(zb + pi) = make_ulonglong2(~0ull, ~0ull);
-                *reinterpret_cast<ulonglong2 *>(zb + pi + 2) = make_ulonglong2(~0ull, ~0ull);
-            }
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                key[k] = k < (int)n ? zb[pi + k] : ~0ull;
-                if (p.reset_zbuf && k < (int)n) zb[pi + k] = ~0ull;
-            }
+            for (int k = 0; k < 4; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
         }
         uint32_t rgb[4], id[4];
         float dep[4];
@@ -672,6 +678,11 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         e = cudaMemsetAsync(p.stats, 0, 6 * sizeof(uint32_t), stream);
         if (e != cudaSuccess) return e;
     }
+    // empty z-buffers for the active views, just before the raster: they stay
+    // resident in L2 for its atomics
+    zclear_kernel<<<(uint32_t)sms * 4, 256, 0, stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
         const uint32_t cull_blocks = std::min<uint32_t>((p.total_items + 7) / 8, (uint32_t)sms * 8);
         cull_kernel<<<cull_blocks, 256, 0, stream>>>(p);
