@@ -436,7 +436,7 @@ HSR_API int hsr_get_stage_stats(uint32_t *counts);
  * cannot afford an allocator call, and hosts that route every allocation
  * through their own allocator.
  *   - A call needing more than 32 MiB of scratch (about 8 B per output pixel
- *     per view + 16 B per meshlet per view + 176 B per view) returns
+ *     per view + 48 B per meshlet per view + 192 B per view) returns
  *     HSR_ERR_OVERFLOW; split such batches or use hsr_render.
  *   - All calls share the array and it keeps the last call's contents (each
  *     call re-initialises what it needs). Calls whose work overlaps on the
@@ -449,6 +449,22 @@ HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose *poses, ui
                        uint8_t *rgb, float *depth, uint32_t *ids, void *cuda_stream);
 
 /* Static description of a status code. */
+/*
+ * Device status: the raster kernels stage geometry with asynchronous bulk
+ * copies and wait for them with a time limit (one second); a wait that
+ * expires makes the kernel stop, record the failure and return, leaving the
+ * context usable (the frame is then incomplete). hsr_device_status waits for
+ * the current device and returns HSR_ERR_TIMEOUT if any kernel recorded such
+ * a failure since the last clear (clear != 0 resets the record), HSR_OK
+ * otherwise, HSR_ERR_CUDA if the device cannot be queried.
+ */
+HSR_API int hsr_device_status(int clear);
+/* Test hook for the failure path above: renders launched while extra_bytes
+ * is non-zero arm every geometry staging for extra_bytes more than their
+ * copies deliver, so each wait expires (about one second per raster warp).
+ * 0 restores normal operation. Not for production use. */
+HSR_API int hsr_debug_inject_wait_fault(uint32_t extra_bytes);
+
 HSR_API const char *hsr_status_string(int status);
 
 /* Library version, "major.minor.patch". */

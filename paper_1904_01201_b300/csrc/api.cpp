@@ -208,15 +208,15 @@ struct Plan {
     LaunchCfg cfg;
     uint64_t list_cap = 1;           // visible pairs per list (worst case over the capacity)
     uint64_t item_cap = 0;           // (view, group) work items (worst case)
-    uint32_t hiz_w = 0, hiz_h = 0;
+    uint32_t hiz_w = 0, hiz_h = 0, hiz_total = 0;
     size_t off_scenes = 0, off_slots = 0, off_views = 0, desc_bytes = 0;
-    size_t z_off = 0, l_off = 0, h_off = 0, r_off = 0, i_off = 0, scratch_bytes = 0, zbytes = 0;
+    size_t z_off = 0, l_off = 0, h_off = 0, r_off = 0, i_off = 0, s_off = 0, scratch_bytes = 0, zbytes = 0;
 };
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Header words of the descriptor buffer.
-constexpr int kHdrVisCount = 0, kHdrWork = 4, kHdrBigRec = 8, kHdrBigInst = 12, kHdrDyn = 16;
+constexpr int kHdrVisCount = 0, kHdrWork = 4, kHdrBigRec = 8, kHdrBigInst = 12, kHdrDyn = 16, kHdrSurv = 24;
 
 // max_meshlets / max_groups: per-view worst case (largest scene that may be rendered)
 void make_plan(Plan &pl, uint32_t n_scenes, uint32_t n_cap, uint32_t width, uint32_t height,
@@ -231,6 +231,7 @@ void make_plan(Plan &pl, uint32_t n_scenes, uint32_t n_cap, uint32_t width, uint
     pl.item_cap = items;
     pl.hiz_w = (width + kHizTile - 1) / kHizTile;
     pl.hiz_h = (height + kHizTile - 1) / kHizTile;
+    pl.hiz_total = hiz_pyramid_texels(pl.hiz_w, pl.hiz_h, nullptr);
     pl.off_scenes = 256;
     pl.off_slots = pl.off_scenes + al256(sizeof(SceneDev) * n_scenes);
     pl.off_views = pl.off_slots + al256(sizeof(uint32_t) * (3 * (size_t)n_scenes + 1));
@@ -238,10 +239,11 @@ void make_plan(Plan &pl, uint32_t n_scenes, uint32_t n_cap, uint32_t width, uint
     pl.zbytes = al256((size_t)n_cap * width * height * sizeof(unsigned long long));
     pl.z_off = 0;
     pl.l_off = pl.z_off + pl.zbytes;
-    pl.h_off = pl.l_off + al256(2 * (size_t)pl.list_cap * sizeof(uint2));
-    pl.r_off = pl.h_off + al256((size_t)n_cap * pl.hiz_w * pl.hiz_h * sizeof(uint32_t));
+    pl.h_off = pl.l_off + al256(2 * (size_t)pl.list_cap * sizeof(uint4));
+    pl.r_off = pl.h_off + al256((size_t)n_cap * pl.hiz_total * sizeof(uint32_t));
     pl.i_off = pl.r_off + al256((size_t)kBigRecCap * sizeof(BigTriStorage));
-    pl.scratch_bytes = pl.i_off + al256(3 * (size_t)kBigInstCap * sizeof(uint2));
+    pl.s_off = pl.i_off + al256(3 * (size_t)kBigInstCap * sizeof(uint2));
+    pl.scratch_bytes = pl.s_off + al256((size_t)pl.list_cap * sizeof(uint4));
 }
 
 // Depth-noise request of one call: the public struct (or none) plus the
@@ -398,9 +400,13 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
     p.slot_scene = dslot + 2 * S + 1;
     p.n_slots = S;
     p.zbuf = reinterpret_cast<unsigned long long *>(scratch + pl.z_off);
-    p.vis = reinterpret_cast<uint2 *>(scratch + pl.l_off);
+    p.vis = reinterpret_cast<uint4 *>(scratch + pl.l_off);
     p.vis_cap = (uint32_t)pl.list_cap;
     p.hiz = reinterpret_cast<uint32_t *>(scratch + pl.h_off);
+    p.hiz_total = pl.hiz_total;
+    p.surv = reinterpret_cast<uint4 *>(scratch + pl.s_off);
+    p.surv_count = hdr + kHdrSurv;
+    p.fault_tx = debug_fault_tx();
     p.hiz_w = pl.hiz_w;
     p.hiz_h = pl.hiz_h;
     p.big_rec = reinterpret_cast<BigTri *>(scratch + pl.r_off);
@@ -448,7 +454,7 @@ cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const 
 bool validate_common(const hsr_scene *const *scenes, uint32_t n_scenes, const hsr_pose *poses, uint32_t n,
                      const hsr_intrinsics *intr, uint32_t width, uint32_t height, bool has_output)
 {
-    if (!scenes || n_scenes == 0 || !poses || n == 0 || !has_output) return false;
+    if (!scenes || n_scenes == 0 || !poses || n == 0 || n >= kMaxViews || !has_output) return false;
     if (width == 0 || height == 0 || width > 4096 || height > 4096) return false;
     if (!intrinsics_ok(intr)) return false;
     for (uint32_t i = 0; i < n_scenes; i++)
@@ -468,8 +474,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
 
-    // scratch: z-buffer (8 B / pixel / view) + visible lists (16 B per meshlet
-    // per view) + tile z; large calls are split into halves
+    // scratch: z-buffer (8 B / pixel / view) + visible and survivor lists
+    // (48 B per meshlet per view) + tile-z pyramid; large calls are split into halves
     uint64_t list_entries = 0, items = 0;
     for (uint32_t i = 0; i < n; i++) {
         const uint32_t s = scene_of_agent ? scene_of_agent[i] : 0u;
@@ -478,8 +484,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         items += scenes[s]->dev.n_groups;
     }
     const uint64_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
-    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 16ull +
-                             (uint64_t)n * hiz_w * hiz_h * 4ull;
+    const uint64_t scratch = (uint64_t)n * width * height * 8ull + list_entries * 48ull +
+                             (uint64_t)n * hiz_pyramid_texels((uint32_t)hiz_w, (uint32_t)hiz_h, nullptr) * 4ull;
     if (scratch > kMaxScratchBytes && n > 1) {
         const uint32_t h = n / 2;
         const size_t px = (size_t)width * height;
@@ -781,6 +787,10 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         sentinel.vbase = (uint32_t)mvert.size();
         sentinel.tbase = (uint32_t)mtri.size();
         meshlets.push_back(sentinel);
+        // two spare entries: triangle blocks are copied in 16-byte units that
+        // may run one entry past a meshlet's last triangle
+        mtri.push_back(make_uint2(0u, 0u));
+        mtri.push_back(make_uint2(0u, 0u));
         // groups of 32 meshlets
         std::vector<Group> groups;
         for (uint32_t m0 = 0; m0 < n_meshlets; m0 += kGroupMeshlets) {
@@ -1142,7 +1152,7 @@ int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     status = measure(cur, cur_ms);
     const uint32_t small_v[] = {8, 16, 24, 32};
     const uint32_t bin_v[] = {16, 32, 64, 128, 256, 512, 4096};
-    const uint32_t chunk_v[] = {1, 2, 4, 8, 16};
+    const uint32_t chunk_v[] = {1, 2, 4, 8, 16, 32};
     const uint32_t phase_v[] = {1, 2, 3};
     const float radius_v[][2] = {{2.f, 5.f}, {3.f, 7.f}, {4.f, 10.f}, {6.f, 14.f}};
     const uint32_t cta_v[] = {2, 3};
@@ -1254,6 +1264,19 @@ int hsr_scene_set_sampling(hsr_scene *s, int mode)
     }
     cudaSetDevice(prev);
     return e == cudaSuccess ? HSR_OK : cuda_status(e);
+}
+
+int hsr_device_status(int clear)
+{
+    uint32_t flags = 0;
+    if (read_device_errors(&flags, clear != 0) != cudaSuccess) return HSR_ERR_CUDA;
+    return (flags & kErrWaitTimeout) ? HSR_ERR_TIMEOUT : HSR_OK;
+}
+
+int hsr_debug_inject_wait_fault(uint32_t extra_bytes)
+{
+    set_debug_fault_tx(extra_bytes);
+    return HSR_OK;
 }
 
 int hsr_scene_free(hsr_scene *scene)

@@ -90,6 +90,52 @@ struct AgentsDev {
     double c_turn[2], s_turn[2];   // cos, sin of half the left [0] / right [1] turn angle
 };
 
+// Texels of the tile-z pyramid over a w x h tile grid (levels halve, rounding
+// up, down to 1 x 1); *levels receives the level count.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t hiz_pyramid_texels(uint32_t w, uint32_t h, uint32_t *levels)
+{
+    uint32_t total = 0, n = 0;
+    for (;;) {
+        total += w * h;
+        n++;
+        if (w <= 1 && h <= 1) break;
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    if (levels) *levels = n;
+    return total;
+}
+
+// A visible (view, meshlet) pair as the raster consumes it, self-contained so
+// that no meshlet record is read on the raster path:
+//   x = view | (n_verts - 1) << 21 | (n_tris - 1) << 27, y = meshlet,
+//   z = first vertex, w = first triangle of the meshlet's ranges.
+constexpr uint32_t kMaxViews = 1u << 21;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint4 pair_entry(uint32_t view, uint32_t meshlet, uint32_t vbase, uint32_t nv, uint32_t tbase, uint32_t nt)
+{
+    return uint4{view | (nv - 1u) << 21 | (nt - 1u) << 27, meshlet, vbase, tbase};
+}
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t pair_view(const uint4 &e) { return e.x & (kMaxViews - 1u); }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t pair_nv(const uint4 &e) { return ((e.x >> 21) & 63u) + 1u; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t pair_nt(const uint4 &e) { return (e.x >> 27) + 1u; }
+
+constexpr uint32_t kErrWaitTimeout = 1u;    // a bounded wait for a bulk copy gave up
+
 struct Params {
     const SceneDev *scenes;    // device array
     const View *views;         // device array, n_views (sorted by scene)
@@ -97,11 +143,12 @@ struct Params {
     uint8_t *rgb;
     float *depth;
     uint32_t *ids;             // may be null
-    // Visible (view, meshlet) pairs written by the cull kernel, one list per
-    // occlusion phase in a buffer of 2 * vis_cap entries: phase 0 grows up
-    // from vis[0], phase 2 grows down from vis[vis_cap - 1], phase 1 grows up
-    // from vis[vis_cap] (vis_cap = worst case, every meshlet in every view).
-    uint2 *vis;
+    // Visible (view, meshlet) pairs written by the cull kernel (pair_entry
+    // layout), one list per occlusion phase in a buffer of 2 * vis_cap
+    // entries: phase 0 grows up from vis[0], phase 2 grows down from
+    // vis[vis_cap - 1], phase 1 grows up from vis[vis_cap] (vis_cap = worst
+    // case, every meshlet in every view).
+    uint4 *vis;
     uint32_t *vis_count;       // [3] pairs per phase (preset to 0)
     uint32_t *work_counter;    // [3] raster work cursor per phase (preset to 0)
     uint32_t vis_cap;
@@ -131,7 +178,18 @@ struct Params {
     // phases after the first skip meshlets the hierarchical z-buffer proves hidden
     uint32_t n_phases;         // 1 (no occlusion culling) .. 3
     float phase_r2[2];         // squared band radii, metres^2
-    uint32_t *hiz;             // [n_views][hiz_h][hiz_w]: max key >> 32 over each 8x8 tile
+    // Tile-z pyramid per view (hiz_total texels): level 0 is the hiz_w x
+    // hiz_h grid of 8x8-pixel tiles, each the largest stored key >> 32 (the
+    // farthest fragment, or 0xFFFFFFFF for background); level l+1 halves
+    // level l (rounding up), each texel the max of its up to 2x2 children,
+    // down to 1 x 1.
+    uint32_t *hiz;
+    uint32_t hiz_total;
+    // Pairs of phases 1 and 2 that the pyramid does not prove hidden,
+    // compacted by occl_kernel for the raster of that phase.
+    uint4 *surv;
+    uint32_t *surv_count;      // [2] survivors of phase 1, phase 2 (preset to 0)
+    uint32_t fault_tx;         // test hook: extra bytes each meshlet staging waits for (0 in normal operation)
     uint32_t *stats;           // diagnostic counters or null: [0..2] pairs per phase, [3..5] skipped per phase
     // Tile bins of large triangles: a triangle with more than small_px
     // candidate pixels is stored once in `big_rec` and binned to every 8x8
@@ -172,6 +230,12 @@ cudaError_t prepare_kernels();
 
 // Launches the cull, raster and shade kernels on `stream`.
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream);
+// Device error flags (kErrWaitTimeout, ...) raised by kernels on the current
+// device since the last clear; waits for the device.
+cudaError_t read_device_errors(uint32_t *flags, bool clear);
+// Test hook for the bounded waits (see hsr_debug_inject_wait_fault).
+uint32_t debug_fault_tx();
+void set_debug_fault_tx(uint32_t bytes);
 // What a step batch needs to know about an agent set (agents.cpp).
 struct AgentsView {
     int device;

@@ -41,13 +41,15 @@ __device__ __forceinline__ void zmin(unsigned long long *z, unsigned long long k
     atomicMin(z, key);
 }
 
-// One thread, one small triangle (at most 32 candidate pixels). Coverage is
-// found first; the depth plane (two divisions) is only built when at least
-// one sample is covered. Exactness: |X_j - X_i| and |P - X_i| are below 2^15
-// inside the bounding box, so every product is below 2^30 and every edge
-// value below 2^31.
-__device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0, int x1, int y0, int y1,
-                                             float q_far, unsigned long long *zbuf, int W)
+// Coverage of a small triangle (at most 32 candidate pixels, bounding box
+// under 2^15 sub-pixels per axis): bit k of the result is candidate k, row
+// k / w, column k % w of [x0, x1] x [y0, y1]. Exactness: |X_j - X_i| and
+// |P - X_i| are below 2^15 inside the bounding box, so every edge value at a
+// candidate sample is below 2^31 in magnitude. The values are evaluated once
+// at the first candidate and then stepped (one pixel right: -256 dy, one row
+// down: +256 dx) in wrap-around unsigned arithmetic, which is exact wherever
+// the true value fits in 32 bits, as it does at every evaluated sample.
+__device__ __forceinline__ uint32_t small_coverage(const Tri2D &t, int x0, int x1, int y0, int y1)
 {
     const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
     const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
@@ -55,31 +57,153 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0
     const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
     const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
     const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
+    const int Px = 256 * x0 + 128, Py = 256 * y0 + 128;
+    // biased edge values at the first candidate: inside iff all three >= 0
+    uint32_t r0 = (uint32_t)(dx0 * (Py - t.Y1) - dy0 * (Px - t.X1) - b0);
+    uint32_t r1 = (uint32_t)(dx1 * (Py - t.Y2) - dy1 * (Px - t.X2) - b1);
+    uint32_t r2 = (uint32_t)(dx2 * (Py - t.Y0) - dy2 * (Px - t.X0) - b2);
+    const uint32_t sx0 = 256u * (uint32_t)dy0, sx1 = 256u * (uint32_t)dy1, sx2 = 256u * (uint32_t)dy2;
+    const uint32_t sy0 = 256u * (uint32_t)dx0, sy1 = 256u * (uint32_t)dx1, sy2 = 256u * (uint32_t)dx2;
     const int w = x1 - x0 + 1;
     uint32_t mask = 0;
     int k = 0;
     for (int py = y0; py <= y1; ++py) {
-        const int Py = 256 * py + 128;
-        for (int px = x0; px <= x1; ++px, ++k) {
-            const int Px = 256 * px + 128;
-            const int e0 = dx0 * (Py - t.Y1) - dy0 * (Px - t.X1);
-            const int e1 = dx1 * (Py - t.Y2) - dy1 * (Px - t.X2);
-            const int e2 = dx2 * (Py - t.Y0) - dy2 * (Px - t.X0);
-            if (((e0 - b0) | (e1 - b1) | (e2 - b2)) >= 0) mask |= 1u << k;
+        uint32_t e0 = r0, e1 = r1, e2 = r2;
+        for (int i = 0; i < w; ++i, ++k) {
+            if ((int)(e0 | e1 | e2) >= 0) mask |= 1u << k;
+            e0 -= sx0;
+            e1 -= sx1;
+            e2 -= sx2;
+        }
+        r0 += sy0;
+        r1 += sy1;
+        r2 += sy2;
+    }
+    return mask;
+}
+
+// Position of the k-th (from 0) set bit of m, k < popcount(m): binary search
+// on the popcounts of the low halves.
+__device__ __forceinline__ int select_bit(uint32_t m, uint32_t k)
+{
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t c = (uint32_t)__popc(m & ((1u << s) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= s;
+            pos += s;
         }
     }
+    return pos;
+}
+
+// A small triangle's covered samples and depth plane, held by the lane that
+// set it up until the warp rasterises the fragments of all its lanes.
+struct SmallFrag {
+    uint32_t mask;            // covered candidates (0: nothing to raster)
+    int X0, Y0;               // vertex 0 (sub-pixels): origin of the depth plane
+    int x0, y0, w;            // candidate rectangle origin and width (pixels)
+    float pa, pb, q0, qlo, qhi;
+    float rw;                 // 1 / w
+    uint32_t id;
+};
+
+__device__ __forceinline__ void small_setup(const Tri2D &t, uint32_t id, int x0, int x1, int y0, int y1,
+                                            SmallFrag &f)
+{
+    f.mask = small_coverage(t, x0, x1, y0, y1);
+    if (!f.mask) return;
+    depth_plane(t, f.pa, f.pb);
+    f.q0 = t.q0;
+    f.qlo = tri_qlo(t);
+    f.qhi = tri_qhi(t);
+    f.X0 = t.X0;
+    f.Y0 = t.Y0;
+    f.x0 = x0;
+    f.y0 = y0;
+    f.w = x1 - x0 + 1;
+    f.rw = __frcp_rn((float)f.w);
+    f.id = id;
+}
+
+// Fragments of the small triangles of all lanes, spread over the warp (every
+// lane calls it): covered samples are numbered consecutively across lanes
+// (warp prefix sum of the mask popcounts), lane i takes fragment base + i,
+// finds the lane owning it (binary search of the prefix) and the candidate
+// bit (its k-th covered bit), and merges the fragment exactly as a per-lane
+// loop would: same plane evaluation, same far test, same key. Row and column
+// of candidate bit b < 32 of a rectangle w <= 32 wide: row = floor((b + 1/2)
+// / w) computed as (b + 0.5) * (1/w) in fp32, exact because (b + 1/2) / w is
+// at least 1/(2w) >= 1/64 away from an integer.
+__device__ __forceinline__ void raster_fragments_warp(const SmallFrag &f, int lane, float q_far,
+                                                      unsigned long long *zbuf, int W)
+{
+    const uint32_t cnt = (uint32_t)__popc(f.mask);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t excl = incl - cnt;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t g = base + (uint32_t)lane;
+        int j = 0;                                   // last lane whose range starts at or before g
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            const int c = j + s;
+            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, c & 31);
+            if (c < 32 && e <= g) j = c;
+        }
+        const uint32_t ej = __shfl_sync(0xFFFFFFFFu, excl, j);
+        const uint32_t mj = __shfl_sync(0xFFFFFFFFu, f.mask, j);
+        const int X0 = __shfl_sync(0xFFFFFFFFu, f.X0, j), Y0 = __shfl_sync(0xFFFFFFFFu, f.Y0, j);
+        const int x0 = __shfl_sync(0xFFFFFFFFu, f.x0, j), y0 = __shfl_sync(0xFFFFFFFFu, f.y0, j);
+        const int w = __shfl_sync(0xFFFFFFFFu, f.w, j);
+        const float rw = __shfl_sync(0xFFFFFFFFu, f.rw, j);
+        const float pa = __shfl_sync(0xFFFFFFFFu, f.pa, j), pb = __shfl_sync(0xFFFFFFFFu, f.pb, j);
+        const float q0 = __shfl_sync(0xFFFFFFFFu, f.q0, j);
+        const float qlo = __shfl_sync(0xFFFFFFFFu, f.qlo, j), qhi = __shfl_sync(0xFFFFFFFFu, f.qhi, j);
+        const uint32_t id = __shfl_sync(0xFFFFFFFFu, f.id, j);
+        if (g >= total) continue;
+        const int b = select_bit(mj, g - ej);
+        if (!((mj >> b) & 1u)) continue;            // never: g lies in lane j's range
+        const int row = (int)(((float)b + 0.5f) * rw);
+        const int px = x0 + (b - row * w), py = y0 + row;
+        const float q = plane_q(pa, pb, q0, 256 * px + 128 - X0, 256 * py + 128 - Y0, qlo, qhi);
+        if (!(q >= q_far)) continue;
+        zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
+    }
+}
+
+// One thread, one small triangle (the per-lane form of the two functions
+// above, for triangles set up outside the warp's common path).
+__device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0, int x1, int y0, int y1,
+                                             float q_far, unsigned long long *zbuf, int W)
+{
+    uint32_t mask = small_coverage(t, x0, x1, y0, y1);
     if (!mask) return;
     float pa, pb;
     depth_plane(t, pa, pb);
     const float qlo = tri_qlo(t), qhi = tri_qhi(t);
-    while (mask) {
-        const int b = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int px = x0 + b % w, py = y0 + b / w;
-        const int Px = 256 * px + 128, Py = 256 * py + 128;
-        const float q = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0, qlo, qhi);
-        if (!(q >= q_far)) continue;
-        zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
+    const int w = x1 - x0 + 1;
+    // covered samples row by row (bit k of the mask is row k / w, column k % w)
+    const uint32_t rowbits = w >= 32 ? 0xFFFFFFFFu : ((1u << w) - 1u);
+    for (int py = y0; mask; ++py) {
+        uint32_t row = mask & rowbits;
+        mask = w >= 32 ? 0u : mask >> w;
+        const int Pyr = 256 * py + 128;
+        while (row) {
+            const int b = __ffs(row) - 1;
+            row &= row - 1;
+            const int px = x0 + b;
+            const float q = plane_q(pa, pb, t.q0, 256 * px + 128 - t.X0, Pyr - t.Y0, qlo, qhi);
+            if (!(q >= q_far)) continue;
+            zmin(zbuf + (size_t)py * W + px, depth_key(q, id));
+        }
     }
 }
 

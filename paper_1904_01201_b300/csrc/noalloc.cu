@@ -14,8 +14,8 @@
 //
 // Limits and rules (also stated in include/hsr.h):
 //  * the array holds kNoAllocScratchBytes = 32 MiB; a call needing more
-//    (about 8 bytes per output pixel per view plus 16 bytes per meshlet per
-//    view, plus 176 bytes per view) is rejected with HSR_ERR_OVERFLOW;
+//    (about 8 bytes per output pixel per view plus 48 bytes per meshlet per
+//    view, plus 192 bytes per view) is rejected with HSR_ERR_OVERFLOW;
 //  * the host-side descriptors are staged in a fixed 1 MiB host buffer
 //    (at most ~6500 views per call);
 //  * every GPU that loads the library keeps the 32 MiB array until the
@@ -72,7 +72,8 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     if (!host_intrinsics_ok(intr)) return HSR_ERR_INVALID_ARG;
     const SceneDev &sd = host_scene_dev(scene);
 
-    // layout of the scratch array: [counters | scene | slot | views | z-buffer | visible list | tile z]
+    // layout of the scratch array:
+    // [counters | scene | slot | views | z-buffer | visible lists | tile-z pyramid | survivor list]
     const size_t off_scene = 256;
     const size_t off_slots = off_scene + align256(sizeof(SceneDev));
     const size_t off_views = off_slots + 256;
@@ -82,9 +83,11 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     const uint64_t list_entries = (uint64_t)n * sd.n_meshlets;
     const uint64_t items = (uint64_t)n * sd.n_groups;
     const uint32_t hiz_w = (width + kHizTile - 1) / kHizTile, hiz_h = (height + kHizTile - 1) / kHizTile;
-    const uint64_t hbytes = (uint64_t)n * hiz_w * hiz_h * sizeof(uint32_t);
-    const uint64_t lbytes = align256(2 * list_entries * sizeof(uint2));
-    const uint64_t need = (uint64_t)off_z + zbytes + lbytes + hbytes;
+    const uint32_t hiz_total = hiz_pyramid_texels(hiz_w, hiz_h, nullptr);
+    const uint64_t hbytes = align256((uint64_t)n * hiz_total * sizeof(uint32_t));
+    const uint64_t lbytes = align256(2 * list_entries * sizeof(uint4));
+    const uint64_t sbytes = list_entries * sizeof(uint4);
+    const uint64_t need = (uint64_t)off_z + zbytes + lbytes + hbytes + sbytes;
     if (need > kNoAllocScratchBytes || desc_bytes > kNoAllocHostBytes) return HSR_ERR_OVERFLOW;
     if (items >= 0xFFFFFFF0ull) return HSR_ERR_OVERFLOW;
 
@@ -143,7 +146,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.dyn = reinterpret_cast<const uint32_t *>(d) + 16;
     p.views = reinterpret_cast<const View *>(d + off_views);
     p.zbuf = reinterpret_cast<unsigned long long *>(d + off_z);
-    p.vis = reinterpret_cast<uint2 *>(d + off_z + zbytes);
+    p.vis = reinterpret_cast<uint4 *>(d + off_z + zbytes);
     p.vis_cap = (uint32_t)list_entries;
     p.rgb = rgb;
     p.depth = depth;
@@ -160,6 +163,9 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;
     p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + lbytes);
+    p.hiz_total = hiz_total;
+    p.surv = reinterpret_cast<uint4 *>(d + off_z + zbytes + lbytes + hbytes);
+    p.surv_count = reinterpret_cast<uint32_t *>(d) + 24;
     p.hiz_w = hiz_w;
     p.hiz_h = hiz_h;
     p.n_phases = cfg.n_phases;

@@ -24,6 +24,7 @@
 
 #include "hsr_internal.h"
 #include "kernels/bin.cuh"
+#include "kernels/bulk.cuh"
 #include "kernels/raster.cuh"
 #include "kernels/setup.cuh"
 #include "kernels/shade.cuh"
@@ -38,6 +39,9 @@ constexpr int kShadeThreads = 256;
 static_assert(sizeof(BigTri) == sizeof(BigTriStorage), "binned triangle storage size");
 constexpr uint32_t kTilesPerInst = 8;
 constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
+
+// Error flags raised by kernels of this device (kErrWaitTimeout, ...).
+__device__ uint32_t g_device_err;
 
 // --------------------------------------------------------------------- cull
 // Decode a (view, group) work item: views are sorted by scene, slot k holds
@@ -84,9 +88,12 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         const uint32_t m = grp.m0 + lane;
         bool vis = false;
         uint32_t phase = 0;
+        uint4 entry = make_uint4(0u, 0u, 0u, 0u);
         if (m < grp.m1) {
             const Meshlet ml = S.meshlets[m];
             vis = aabb_visible(pl, ml.bmin, ml.bmax);
+            const Meshlet nx = S.meshlets[m + 1];
+            entry = pair_entry(vi, m, ml.vbase, nx.vbase - ml.vbase, ml.tbase, nx.tbase - ml.tbase);
             // distance band of the box from the camera -> occlusion phase
             const float *cp = p.views[vi].pos;
             float d2 = 0.f;
@@ -107,23 +114,29 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             if (lane == 0) base = atomicAdd(p.vis_count + ph, (uint32_t)__popc(mask));
             base = __shfl_sync(0xFFFFFFFFu, base, 0);
             const uint32_t k = base + __popc(mask & ((1u << lane) - 1u));
-            if (mine) p.vis[vis_index(p, ph, k)] = make_uint2(vi, m);
+            if (mine) p.vis[vis_index(p, ph, k)] = entry;
         }
     }
 }
 
 // --------------------------------------------------------------------- raster
-struct WarpCtx {
-    // view-dependent, warp-uniform
-    unsigned long long *zbuf;
-    const float4 *mvert;
-    const uint2 *mtri;
+// Per-warp staging buffer of one meshlet: its view's matrix, its vertex
+// block and its triangle block, the latter widened to start on a 16-byte
+// boundary (the first triangle sits at tri[first_tri & 1]). Filled by the
+// bulk-copy engine while the warp works on the previous meshlet.
+struct alignas(16) MeshletStage {
+    float M[12];
+    float4 vert[kMeshletVerts];
+    uint2 tri[kMeshletTris + 2];
 };
 
 // Emit one front-facing (sub-)triangle: clip its pixel range to the image,
 // raster it here when small, else queue it for the warp.
+// With `small` non-null a small triangle is only set up there (the warp
+// rasterises the fragments of all lanes together); else this lane rasterises it.
 __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Params &p, unsigned long long *zbuf,
-                                         BigTri *bigq, uint32_t *bign, uint32_t view, uint32_t phase)
+                                         BigTri *bigq, uint32_t *bign, uint32_t view, uint32_t phase,
+                                         SmallFrag *small = nullptr)
 {
     int x0, x1, y0, y1, spanx, spany;
     pixel_range(t, x0, x1, y0, y1, spanx, spany);
@@ -134,7 +147,10 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     if (x0 > x1 || y0 > y1) return;            // no sample on screen
     const int npx = (x1 - x0 + 1) * (y1 - y0 + 1);
     if (spanx < 32768 && spany < 32768 && npx <= (int)p.small_px) {
-        raster_small(t, id, x0, x1, y0, y1, p.q_far, zbuf, (int)p.width);
+        if (small)
+            small_setup(t, id, x0, x1, y0, y1, *small);
+        else
+            raster_small(t, id, x0, x1, y0, y1, p.q_far, zbuf, (int)p.width);
         return;
     }
     float pa, pb;
@@ -192,41 +208,36 @@ __global__ void __launch_bounds__(256) big_raster_kernel(const Params p, uint32_
     }
 }
 
-// A meshlet's vertex / triangle ranges and bounding box, held in registers.
-struct MeshletRef {
-    uint32_t vbase, tbase, vend, tend;
-    float box[6];     // bmin xyz, bmax xyz
-};
-
-__device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M, const Params &p,
-                                                const MeshletRef &ml, EyeHot *vh, EyeCold *vcold, BigTri *bigq,
+// One staged meshlet (whole warp): K1 transform + snap its vertices into the
+// warp's vertex cache, K2 per-lane triangle setup, K4 raster.
+__device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Params &p, uint32_t nv, uint32_t nt,
+                                                uint32_t toff, unsigned long long *zbuf, EyeHot *vh, BigTri *bigq,
                                                 uint32_t *bign, int lane, uint32_t view, uint32_t phase)
 {
-    const int nv = (int)(ml.vend - ml.vbase), nt = (int)(ml.tend - ml.tbase);
     const float zn = p.znear, zf = p.zfar;
+    const float *M = st.M;
 
     // K1: transform + snap this meshlet's vertices
-    for (int v = lane; v < nv; v += 32) {
-        const float4 P = __ldg(c.mvert + ml.vbase + v);
+    for (uint32_t v = lane; v < nv; v += 32) {
+        const float4 P = st.vert[v];
         EyeHot h;
-        EyeCold cd;
-        eye_transform(M, P.x, P.y, P.z, cd.xe, cd.ye, h.d);
-        cd.gid = __float_as_uint(P.w);
-        cd.pad_ = 0;
+        float xe, ye;
+        eye_transform(M, P.x, P.y, P.z, xe, ye, h.d);
         if (h.d >= zn) {
-            project_snap(cd.xe, cd.ye, h.d, p.fx, p.fy, p.cx, p.cy, h.q, h.X, h.Y);
+            project_snap(xe, ye, h.d, p.fx, p.fy, p.cx, p.cy, h.q, h.X, h.Y);
         } else {
             h.q = 0.f;
             h.X = h.Y = 0;
         }
         vh[v] = h;
-        vcold[v] = cd;
     }
     __syncwarp();
 
     // K2 + K4: one triangle per lane
-    if (lane < nt) {
-        const uint2 mt = __ldg(c.mtri + ml.tbase + lane);
+    SmallFrag sf;
+    sf.mask = 0u;
+    if ((uint32_t)lane < nt) {
+        const uint2 mt = st.tri[toff + lane];
         const uint32_t ia = mt.x & 255u, ib = (mt.x >> 8) & 255u, ic = (mt.x >> 16) & 255u;
         const EyeHot a = vh[ia], b = vh[ib], cc = vh[ic];
         const uint32_t id = mt.y;
@@ -236,13 +247,17 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
             Tri2D t;
             if (a.d >= zn && b.d >= zn && cc.d >= zn) {
                 if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, cc.X, cc.Y, cc.q, t))
-                    emit_tri(t, id, p, c.zbuf, bigq, bign, view, phase);
+                    emit_tri(t, id, p, zbuf, bigq, bign, view, phase, &sf);
             } else {
-                const EyeCold ca = vcold[ia], cb = vcold[ib], ccc = vcold[ic];
+                // near-clipped: eye-space positions again from the staged vertices
+                const uint32_t li[3] = {ia, ib, ic};
                 CVert<0> v[3];
-                v[0].xe = ca.xe; v[0].ye = ca.ye; v[0].d = a.d; v[0].gid = ca.gid;
-                v[1].xe = cb.xe; v[1].ye = cb.ye; v[1].d = b.d; v[1].gid = cb.gid;
-                v[2].xe = ccc.xe; v[2].ye = ccc.ye; v[2].d = cc.d; v[2].gid = ccc.gid;
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float4 P = st.vert[li[k]];
+                    eye_transform(M, P.x, P.y, P.z, v[k].xe, v[k].ye, v[k].d);
+                    v[k].gid = __float_as_uint(P.w);
+                }
                 CVert<0> poly[4];
                 const int np = clip_near<0>(v, zn, poly);
                 int X[4], Y[4];
@@ -251,76 +266,69 @@ __device__ __forceinline__ void process_meshlet(const WarpCtx &c, const float *M
                     project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
                 for (int f = 0; f + 2 < np; f++)
                     if (orient_cull(X[0], Y[0], q[0], X[f + 1], Y[f + 1], q[f + 1], X[f + 2], Y[f + 2], q[f + 2], t))
-                        emit_tri(t, id, p, c.zbuf, bigq, bign, view, phase);
+                        emit_tri(t, id, p, zbuf, bigq, bign, view, phase);
             }
         }
     }
     __syncwarp();
+    raster_fragments_warp(sf, lane, p.q_far, zbuf, (int)p.width);
     const uint32_t nb = *bign;
-    for (uint32_t r = 0; r < nb; r++) raster_big_warp(bigq[r], lane, p.q_far, c.zbuf, (int)p.width);
+    for (uint32_t r = 0; r < nb; r++) raster_big_warp(bigq[r], lane, p.q_far, zbuf, (int)p.width);
     __syncwarp();
     if (lane == 0) *bign = 0;
     __syncwarp();
 }
 
-// Conservative occlusion test of a meshlet against the hierarchical z-buffer
-// of phases already rasterised (whole warp). Every fragment of the meshlet has
-// inverse depth at most 1/d_min of its (inflated) box, because interpolated q
-// is clamped to the vertices' range; if every 8x8 tile under the box's
-// projected rectangle already stores keys strictly nearer than that bound,
-// none of its fragments can win any pixel, and skipping it changes nothing.
-__device__ __forceinline__ float warp_min(float v)
+// Conservative occlusion test of a meshlet box against the tile-z pyramid of
+// the phases already rasterised (one thread). Every fragment of the meshlet
+// has inverse depth at most 1/d_min of its (inflated) box, because
+// interpolated q is clamped to the vertices' range; if every pyramid texel
+// over the box's projected rectangle (grown by a pixel) already holds only
+// keys strictly nearer than that bound, none of its fragments can win any
+// pixel, and skipping it changes nothing. The level is the first at which the
+// rectangle spans at most 2 x 2 texels.
+__device__ __forceinline__ bool box_occluded(const float *bmin, const float *bmax, const float *M, const Params &p,
+                                             const uint32_t *pyr)
 {
+    float xe[8], ye[8], de[8];
+    float dmin = 3.0e38f;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-    return v;
-}
-
-__device__ __forceinline__ bool meshlet_occluded(const float *bmin, const float *bmax, const float *M,
-                                                 const Params &p, const uint32_t *hiz_v, int lane)
-{
-    float d = 3.0e38f, xe = 0.f, ye = 0.f;
-    if (lane < 8) {
-        const float x = (lane & 1) ? bmax[0] : bmin[0];
-        const float y = (lane & 2) ? bmax[1] : bmin[1];
-        const float z = (lane & 4) ? bmax[2] : bmin[2];
-        eye_transform(M, x, y, z, xe, ye, d);
+    for (int c = 0; c < 8; c++) {
+        eye_transform(M, (c & 1) ? bmax[0] : bmin[0], (c & 2) ? bmax[1] : bmin[1], (c & 4) ? bmax[2] : bmin[2],
+                      xe[c], ye[c], de[c]);
+        dmin = fminf(dmin, de[c]);
     }
-    const float dmin = warp_min(d);
     if (!(dmin > p.znear + 1e-3f)) return false;        // box reaches the near plane: keep
     float sx0 = 3.0e38f, sx1 = -3.0e38f, sy0 = 3.0e38f, sy1 = -3.0e38f;
-    if (lane < 8) {
-        const float r = __frcp_rn(d);
-        const float sx = __fmaf_rn(p.fx, __fmul_rn(xe, r), p.cx);
-        const float sy = __fmaf_rn(-p.fy, __fmul_rn(ye, r), p.cy);
-        sx0 = sx1 = sx;
-        sy0 = sy1 = sy;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const float r = __frcp_rn(de[c]);
+        const float sx = __fmaf_rn(p.fx, __fmul_rn(xe[c], r), p.cx);
+        const float sy = __fmaf_rn(-p.fy, __fmul_rn(ye[c], r), p.cy);
+        sx0 = fminf(sx0, sx);
+        sx1 = fmaxf(sx1, sx);
+        sy0 = fminf(sy0, sy);
+        sy1 = fmaxf(sy1, sy);
     }
-    sx0 = warp_min(sx0);
-    sx1 = warp_max(sx1);
-    sy0 = warp_min(sy0);
-    sy1 = warp_max(sy1);
     const float Wf = (float)p.width, Hf = (float)p.height;
-    const int x0 = (int)fminf(fmaxf(floorf(sx0 - 1.f), 0.f), Wf - 1.f);
-    const int x1 = (int)fminf(fmaxf(ceilf(sx1 + 1.f), 0.f), Wf - 1.f);
-    const int y0 = (int)fminf(fmaxf(floorf(sy0 - 1.f), 0.f), Hf - 1.f);
-    const int y1 = (int)fminf(fmaxf(ceilf(sy1 + 1.f), 0.f), Hf - 1.f);
-    const int tx0 = x0 / kHizTile, tx1 = x1 / kHizTile, ty0 = y0 / kHizTile, ty1 = y1 / kHizTile;
-    const int ntx = tx1 - tx0 + 1, n = ntx * (ty1 - ty0 + 1);
-    if (n > 1024) return false;
-    const uint32_t hb = ~__float_as_uint(__frcp_rn(dmin * (1.0f - 1e-5f)));
-    bool occ = true;
-    for (int i = lane; i < n; i += 32) {
-        const int tx = tx0 + i % ntx, ty = ty0 + i / ntx;
-        if (hiz_v[ty * p.hiz_w + tx] >= hb) occ = false;
+    if (sx1 + 1.f < 0.f || sy1 + 1.f < 0.f || sx0 - 1.f > Wf || sy0 - 1.f > Hf) return false;   // culled elsewhere
+    const uint32_t x0 = (uint32_t)fminf(fmaxf(floorf(sx0 - 1.f), 0.f), Wf - 1.f);
+    const uint32_t x1 = (uint32_t)fminf(fmaxf(ceilf(sx1 + 1.f), 0.f), Wf - 1.f);
+    const uint32_t y0 = (uint32_t)fminf(fmaxf(floorf(sy0 - 1.f), 0.f), Hf - 1.f);
+    const uint32_t y1 = (uint32_t)fminf(fmaxf(ceilf(sy1 + 1.f), 0.f), Hf - 1.f);
+    uint32_t tx0 = x0 / kHizTile, tx1 = x1 / kHizTile, ty0 = y0 / kHizTile, ty1 = y1 / kHizTile;
+    uint32_t w = p.hiz_w, h = p.hiz_h, off = 0;
+    while (tx1 - tx0 > 1 || ty1 - ty0 > 1) {
+        off += w * h;
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+        tx0 >>= 1; tx1 >>= 1; ty0 >>= 1; ty1 >>= 1;
     }
-    return __all_sync(0xFFFFFFFFu, occ);
+    const uint32_t hb = ~__float_as_uint(__frcp_rn(dmin * (1.0f - 1e-5f)));
+    for (uint32_t ty = ty0; ty <= ty1; ty++)
+        for (uint32_t tx = tx0; tx <= tx1; tx++)
+            if (pyr[off + ty * w + tx] >= hb) return false;
+    return true;
 }
 
 // Hierarchical z: per 8x8 tile of each view, the largest stored key >> 32
@@ -347,83 +355,225 @@ __global__ void __launch_bounds__(256) hiz_kernel(const Params p)
         mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
         mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
         mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 4));
-        if (g < total && row == 0) p.hiz[t] = mx;
+        if (g < total && row == 0) p.hiz[(size_t)(t / per_view) * p.hiz_total + t % per_view] = mx;
     }
 }
 
+// Coarser pyramid levels of each active view (one block per view).
+__global__ void __launch_bounds__(256) hiz_pyramid_kernel(const Params p)
+{
+    const uint32_t v = blockIdx.x;
+    if (v >= p.dyn[0]) return;
+    uint32_t *pyr = p.hiz + (size_t)v * p.hiz_total;
+    uint32_t w = p.hiz_w, h = p.hiz_h, off = 0;
+    while (w > 1 || h > 1) {
+        const uint32_t w2 = (w + 1) / 2, h2 = (h + 1) / 2, off2 = off + w * h;
+        for (uint32_t i = threadIdx.x; i < w2 * h2; i += blockDim.x) {
+            const uint32_t x = i % w2, y = i / w2;
+            const uint32_t xa = 2 * x, xb = min(2 * x + 1, w - 1), ya = 2 * y, yb = min(2 * y + 1, h - 1);
+            pyr[off2 + i] = max(max(pyr[off + ya * w + xa], pyr[off + ya * w + xb]),
+                                max(pyr[off + yb * w + xa], pyr[off + yb * w + xb]));
+        }
+        __syncthreads();
+        off = off2;
+        w = w2;
+        h = h2;
+    }
+}
+
+// Occlusion test of the pairs of a phase after the first (one thread per
+// pair); the pairs not proven hidden are compacted into the survivor list.
+__global__ void __launch_bounds__(256) occl_kernel(const Params p, uint32_t phase)
+{
+    const uint32_t count = min(p.vis_count[phase], p.vis_cap);
+    const int lane = threadIdx.x & 31;
+    const uint32_t rounded = (count + 31u) & ~31u;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < rounded; k += gridDim.x * blockDim.x) {
+        bool keep = false;
+        uint4 pr = make_uint4(0u, 0u, 0u, 0u);
+        if (k < count) {
+            pr = p.vis[vis_index(p, phase, k)];
+            const uint32_t vi = pair_view(pr);
+            const View &V = p.views[vi];
+            const Meshlet &ml = p.scenes[V.scene].meshlets[pr.y];
+            float M[12];
+#pragma unroll
+            for (int i = 0; i < 12; i++) M[i] = V.M[i];
+            keep = !box_occluded(ml.bmin, ml.bmax, M, p, p.hiz + (size_t)vi * p.hiz_total);
+        }
+        const unsigned mask = __ballot_sync(0xFFFFFFFFu, keep);
+        const unsigned tested = __ballot_sync(0xFFFFFFFFu, k < count);
+        uint32_t base = 0;
+        if (lane == 0) {
+            if (mask) base = atomicAdd(p.surv_count + (phase - 1), (uint32_t)__popc(mask));
+            if (p.stats) {
+                atomicAdd(p.stats + phase, (uint32_t)__popc(tested));
+                atomicAdd(p.stats + 3 + phase, (uint32_t)__popc(tested & ~mask));
+            }
+        }
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (keep) p.surv[base + __popc(mask & ((1u << lane) - 1u))] = pr;
+    }
+}
+
+// Scene geometry pointers of the first kSlotCache slots, cached per CTA.
+constexpr uint32_t kSlotCache = 32;
+
+// Global addresses of a pair's view matrix and geometry, and the bulk copies
+// that stage them (issued by one lane).
+__device__ __forceinline__ void stage_meshlet(MeshletStage &st, uint64_t *bar, const Params &p, const uint4 &e,
+                                              const float4 *mvert, const uint2 *mtri)
+{
+    const uint32_t nv = pair_nv(e), nt = pair_nt(e);
+    const uint32_t t0 = e.w & ~1u;                              // 16-byte aligned start
+    const uint32_t tn = (e.w + nt - t0 + 1u) & ~1u;             // even count covering the range
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, 48u + nv * 16u + tn * 8u + p.fault_tx);
+    bulk_g2s(st.M, p.views[pair_view(e)].M, 48u, bar);
+    bulk_g2s(st.vert, mvert + e.z, nv * 16u, bar);
+    bulk_g2s(st.tri, mtri + t0, tn * 8u, bar);
+}
+
+// Raster of one phase. Warps take chunks of consecutive pairs from a shared
+// cursor; within a warp the next meshlet's matrix, vertices and triangles are
+// staged by bulk copies (double buffer) while the current one is rasterised,
+// and the next chunk is claimed and read one meshlet ahead, so no global load
+// latency sits on the warp's path.
 __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p, uint32_t phase)
 {
-    // dynamic shared memory: per warp a hot and a cold vertex cache and a
-    // big-triangle queue (raster_smem_bytes)
-    extern __shared__ __align__(16) unsigned char smem[];
-    EyeHot(*s_vh)[kMeshletVerts] = reinterpret_cast<EyeHot(*)[kMeshletVerts]>(smem);
-    EyeCold(*s_vcold)[kMeshletVerts] = reinterpret_cast<EyeCold(*)[kMeshletVerts]>(s_vh + kRasterWarps);
-    BigTri(*s_big)[kBigCap] = reinterpret_cast<BigTri(*)[kBigCap]>(s_vcold + kRasterWarps);
-    __shared__ float s_view[kRasterWarps][12];
+    // dynamic shared memory per warp: two meshlet stages, the vertex cache and
+    // the big-triangle queue (kRasterSmem)
+    extern __shared__ __align__(128) unsigned char smem[];
+    MeshletStage(*s_stage)[2] = reinterpret_cast<MeshletStage(*)[2]>(smem);
+    EyeHot(*s_vh)[kMeshletVerts] = reinterpret_cast<EyeHot(*)[kMeshletVerts]>(s_stage + kRasterWarps);
+    BigTri(*s_big)[kBigCap] = reinterpret_cast<BigTri(*)[kBigCap]>(s_vh + kRasterWarps);
+    __shared__ __align__(8) uint64_t s_bar[kRasterWarps][2];
     __shared__ uint32_t s_bign[kRasterWarps];
+    __shared__ uint32_t s_slot_view[kSlotCache + 1];
+    __shared__ const float4 *s_slot_mvert[kSlotCache];
+    __shared__ const uint2 *s_slot_mtri[kSlotCache];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *vw = s_view[warp];
-    if (lane == 0) s_bign[warp] = 0;
-    __syncwarp();
-    const uint32_t count = min(p.vis_count[phase], p.vis_cap);
+    const uint32_t n_slots = p.dyn[2];
+    if (threadIdx.x < kSlotCache && threadIdx.x < n_slots) {
+        const SceneDev &S = p.scenes[p.slot_scene[threadIdx.x]];
+        s_slot_view[threadIdx.x] = p.slot_view_base[threadIdx.x];
+        s_slot_mvert[threadIdx.x] = S.mvert;
+        s_slot_mtri[threadIdx.x] = S.mtri;
+    }
+    if (threadIdx.x == 0) s_slot_view[min(n_slots, kSlotCache)] = 0xFFFFFFFFu;
+    if (lane == 0) {
+        s_bign[warp] = 0;
+        mbar_init(&s_bar[warp][0]);
+        mbar_init(&s_bar[warp][1]);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    // phase 0 rasterises its list; later phases the survivors of occl_kernel
+    const uint4 *list = phase == 0 ? p.vis : p.surv;
+    const uint32_t count = min(phase == 0 ? p.vis_count[0] : p.surv_count[phase - 1], p.vis_cap);
     // chunk shrinks when the phase has few pairs, so that every warp gets work
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t CH = max(1u, min(p.chunk, count / (2 * n_warps)));
-    WarpCtx c{};
-    uint32_t cur_view = 0xFFFFFFFFu, cur_scene = 0xFFFFFFFFu;
-    for (;;) {
-        // dynamic work distribution: the next CH pairs of this phase's list
-        uint32_t e0 = 0;
-        if (lane == 0) e0 = atomicAdd(p.work_counter + phase, CH);
-        e0 = __shfl_sync(0xFFFFFFFFu, e0, 0);
-        if (e0 >= count) break;
-        const uint32_t ne = min(CH, count - e0);
-        // prefetch: lane j loads entry e0 + j and its meshlet record
-        uint32_t pv = 0, pm = 0, pvb = 0, ptb = 0, pve = 0, pte = 0;
-        float pb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if ((uint32_t)lane < ne) {
-            const uint2 pr = p.vis[vis_index(p, phase, e0 + lane)];
-            pv = pr.x;
-            pm = pr.y;
-            const Meshlet *mls = p.scenes[p.views[pv].scene].meshlets;
-            const Meshlet ml = mls[pm];
-            const Meshlet nx = mls[pm + 1];
-            pvb = ml.vbase; ptb = ml.tbase; pve = nx.vbase; pte = nx.tbase;
-            pb[0] = ml.bmin[0]; pb[1] = ml.bmin[1]; pb[2] = ml.bmin[2];
-            pb[3] = ml.bmax[0]; pb[4] = ml.bmax[1]; pb[5] = ml.bmax[2];
+
+    // geometry of the scene a view belongs to (slot cache, else the records)
+    auto geometry = [&](uint32_t vi, const float4 *&mv, const uint2 *&mt) {
+        if (n_slots <= kSlotCache) {
+            uint32_t k = 0;
+            while (s_slot_view[k + 1] <= vi) k++;
+            mv = s_slot_mvert[k];
+            mt = s_slot_mtri[k];
+        } else {
+            const SceneDev &S = p.scenes[p.views[vi].scene];
+            mv = S.mvert;
+            mt = S.mtri;
         }
-        for (uint32_t j = 0; j < ne; j++) {
-            const uint32_t vi = __shfl_sync(0xFFFFFFFFu, pv, j);
-            MeshletRef r;
-            r.vbase = __shfl_sync(0xFFFFFFFFu, pvb, j);
-            r.tbase = __shfl_sync(0xFFFFFFFFu, ptb, j);
-            r.vend = __shfl_sync(0xFFFFFFFFu, pve, j);
-            r.tend = __shfl_sync(0xFFFFFFFFu, pte, j);
-#pragma unroll
-            for (int k = 0; k < 6; k++) r.box[k] = __shfl_sync(0xFFFFFFFFu, pb[k], j);
-            if (vi != cur_view) {
-                cur_view = vi;
-                const View &V = p.views[vi];
-                __syncwarp();
-                if (lane < 12) vw[lane] = V.M[lane];
-                c.zbuf = p.zbuf + (size_t)vi * p.width * p.height;
-                if (V.scene != cur_scene) {
-                    cur_scene = V.scene;
-                    const SceneDev &S = p.scenes[cur_scene];
-                    c.mvert = S.mvert;
-                    c.mtri = S.mtri;
-                }
-                __syncwarp();
-            }
-            if (p.stats && lane == 0) atomicAdd(p.stats + phase, 1u);
-            if (phase > 0 && meshlet_occluded(r.box, r.box + 3, vw, p,
-                                              p.hiz + (size_t)vi * p.hiz_w * p.hiz_h, lane)) {
-                if (p.stats && lane == 0) atomicAdd(p.stats + 3 + phase, 1u);
-                continue;
-            }
-            process_meshlet(c, vw, p, r, s_vh[warp], s_vcold[warp], s_big[warp], &s_bign[warp], lane, vi, phase);
+    };
+
+    uint32_t c0 = 0;
+    if (lane == 0) c0 = atomicAdd(p.work_counter + phase, CH);
+    c0 = __shfl_sync(0xFFFFFFFFu, c0, 0);
+    uint32_t ne = c0 < count ? min(CH, count - c0) : 0u;
+    uint4 ent = make_uint4(0u, 0u, 0u, 0u);
+    if ((uint32_t)lane < ne) ent = list[c0 + lane];
+    uint32_t nclaim = 0;                     // claim of the chunk after this one (lane 0)
+    if (lane == 0 && ne) nclaim = atomicAdd(p.work_counter + phase, CH);
+    uint32_t ne_nx = 0;
+    uint4 ent_nx = make_uint4(0u, 0u, 0u, 0u);
+    bool nx_read = false;
+
+    uint32_t par = 0;                        // bit s: parity of the next phase of stage s
+    uint32_t stg = 0;
+    bool failed = false;
+    bool pending[2] = {false, false};
+    if (ne) {
+        const uint4 e = make_uint4(__shfl_sync(0xFFFFFFFFu, ent.x, 0), __shfl_sync(0xFFFFFFFFu, ent.y, 0),
+                                   __shfl_sync(0xFFFFFFFFu, ent.z, 0), __shfl_sync(0xFFFFFFFFu, ent.w, 0));
+        if (lane == 0) {
+            const float4 *mv;
+            const uint2 *mt;
+            geometry(pair_view(e), mv, mt);
+            stage_meshlet(s_stage[warp][0], &s_bar[warp][0], p, e, mv, mt);
         }
+        pending[0] = true;
+    }
+    uint32_t j = 0;
+    while (ne) {
+        // the pair after (chunk, j): read the next chunk first when needed
+        if (!nx_read && (j + 1 >= ne || j == 0)) {
+            const uint32_t c1 = __shfl_sync(0xFFFFFFFFu, nclaim, 0);
+            ne_nx = c1 < count ? min(CH, count - c1) : 0u;
+            if ((uint32_t)lane < ne_nx) ent_nx = list[c1 + lane];
+            nx_read = true;
+        }
+        const bool in_chunk = j + 1 < ne;
+        const bool has_next = in_chunk || ne_nx > 0;
+        if (has_next) {
+            const uint32_t src = in_chunk ? j + 1 : 0u;
+            const uint4 sel = in_chunk ? ent : ent_nx;
+            const uint4 e = make_uint4(__shfl_sync(0xFFFFFFFFu, sel.x, src), __shfl_sync(0xFFFFFFFFu, sel.y, src),
+                                       __shfl_sync(0xFFFFFFFFu, sel.z, src), __shfl_sync(0xFFFFFFFFu, sel.w, src));
+            if (lane == 0) {
+                const float4 *mv;
+                const uint2 *mt;
+                geometry(pair_view(e), mv, mt);
+                stage_meshlet(s_stage[warp][stg ^ 1], &s_bar[warp][stg ^ 1], p, e, mv, mt);
+            }
+            pending[stg ^ 1] = true;
+        }
+        // this pair
+        const uint4 e = make_uint4(__shfl_sync(0xFFFFFFFFu, ent.x, j), __shfl_sync(0xFFFFFFFFu, ent.y, j),
+                                   __shfl_sync(0xFFFFFFFFu, ent.z, j), __shfl_sync(0xFFFFFFFFu, ent.w, j));
+        const bool ok = mbar_wait_bounded(&s_bar[warp][stg], (par >> stg) & 1u);
+        par ^= 1u << stg;
+        pending[stg] = false;
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+            failed = true;
+            break;
+        }
+        const uint32_t vi = pair_view(e);
+        if (phase == 0 && p.stats && lane == 0) atomicAdd(p.stats, 1u);
+        process_meshlet(s_stage[warp][stg], p, pair_nv(e), pair_nt(e), e.w & 1u,
+                        p.zbuf + (size_t)vi * p.width * p.height, s_vh[warp], s_big[warp], &s_bign[warp], lane, vi,
+                        phase);
+        stg ^= 1;
+        if (in_chunk) {
+            j++;
+        } else {
+            if (!ne_nx) break;
+            ne = ne_nx;
+            ent = ent_nx;
+            j = 0;
+            nx_read = false;
+            if (lane == 0) nclaim = atomicAdd(p.work_counter + phase, CH);
+        }
+    }
+    if (failed) {
+        if (lane == 0) atomicOr(&g_device_err, kErrWaitTimeout);
+        // let copies still in flight land before the CTA's shared memory goes away
+        for (int k = 0; k < 2; k++)
+            if (pending[k]) mbar_wait_bounded(&s_bar[warp][k], (par >> k) & 1u);
     }
 }
 
@@ -563,7 +713,7 @@ __global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, ui
         shade_rows<0>(p, sS, sM, vi, s_frame, s_agent, outputs);
 }
 
-constexpr size_t kRasterSmem = kRasterWarps * kMeshletVerts * (sizeof(EyeHot) + sizeof(EyeCold)) +
+constexpr size_t kRasterSmem = kRasterWarps * (2 * sizeof(MeshletStage) + kMeshletVerts * sizeof(EyeHot)) +
                                kRasterWarps * kBigCap * sizeof(BigTri);
 
 static cudaError_t set_raster_smem_attr(int dev)
@@ -659,6 +809,21 @@ static inline void mark(int k, cudaStream_t stream)
 // --------------------------------------------------------------------- launch
 static cudaError_t set_raster_smem_attr(int dev);
 
+cudaError_t read_device_errors(uint32_t *flags, bool clear)
+{
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(flags, g_device_err, sizeof(uint32_t));
+    if (e == cudaSuccess && clear) {
+        const uint32_t zero = 0;
+        e = cudaMemcpyToSymbol(g_device_err, &zero, sizeof(uint32_t));
+    }
+    return e;
+}
+
+static uint32_t g_fault_tx = 0;
+uint32_t debug_fault_tx() { return g_fault_tx; }
+void set_debug_fault_tx(uint32_t b) { g_fault_tx = b; }
+
 cudaError_t prepare_kernels()
 {
     int dev = 0;
@@ -696,6 +861,13 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
             if (ph > 0) {
                 hiz_kernel<<<hiz_blocks, 256, 0, stream>>>(p);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+                hiz_pyramid_kernel<<<p.n_views, 256, 0, stream>>>(p);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+                const uint32_t occl_blocks = std::min<uint32_t>((p.vis_cap + 255) / 256, (uint32_t)sms * 16);
+                occl_kernel<<<std::max(occl_blocks, 1u), 256, 0, stream>>>(p, ph);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) return e;
             }

@@ -139,6 +139,8 @@ def _load():
         "hsr_batch_render": ([P, P, P, U32, P, P], ctypes.c_int),
         "hsr_batch_destroy": ([P], ctypes.c_int),
         "hsr_scene_set_sampling": ([P, ctypes.c_int], ctypes.c_int),
+        "hsr_device_status": ([ctypes.c_int], ctypes.c_int),
+        "hsr_debug_inject_wait_fault": ([U32], ctypes.c_int),
         "hsr_render_views": ([P, U32, P, U32, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
                               ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_batch_render_views": ([P, P, U32, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
@@ -209,6 +211,16 @@ def hsr_get_stage_stats():
     if st != HSR_OK:
         raise HsrError(st, "hsr_get_stage_stats")
     return {"pairs": [int(v) for v in c[:3]], "skipped": [int(v) for v in c[3:]]}
+
+
+def hsr_device_status(clear: bool = True) -> int:
+    """HSR_ERR_TIMEOUT if a kernel's bounded wait expired since the last clear, else HSR_OK."""
+    return _lib.hsr_device_status(1 if clear else 0)
+
+
+def hsr_debug_inject_wait_fault(extra_bytes: int) -> None:
+    """Test hook: later renders wait for bytes that never arrive (0 restores normal operation)."""
+    _lib.hsr_debug_inject_wait_fault(int(extra_bytes))
 
 
 def hsr_version() -> str:
