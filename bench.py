@@ -42,7 +42,7 @@ FALLBACK_HBM_GBS = 6400.0
 KERNEL_SOURCES = ["paper_1904_01201_b300/csrc/render.cu", "paper_1904_01201_b300/csrc/hsr_internal.h",
                   "paper_1904_01201_b300/csrc/kernels/transform.cuh", "paper_1904_01201_b300/csrc/kernels/setup.cuh",
                   "paper_1904_01201_b300/csrc/kernels/bin.cuh", "paper_1904_01201_b300/csrc/kernels/raster.cuh",
-                  "paper_1904_01201_b300/csrc/kernels/shade.cuh"]
+                  "paper_1904_01201_b300/csrc/kernels/shade.cuh", "paper_1904_01201_b300/csrc/kernels/bulk.cuh"]
 
 
 def kernel_source_hash() -> str:
