@@ -419,8 +419,12 @@ HSR_API int hsr_get_stage_timing(float *ms);
  * While enabled, render calls count, per occlusion phase, the visible
  * (view, meshlet) pairs rasterised and the meshlets skipped as hidden;
  * hsr_get_stage_stats synchronises the device and writes counts[0..2] = pairs
- * per phase, counts[3..5] = skipped per phase, for the last call. Enabling
- * allocates 32 bytes of device memory once. Use from one thread at a time.
+ * per phase, counts[3..5] = skipped per phase, counts[6] = (view, meshlet)
+ * pairs inside the frustum, counts[7] = of those, planar meshlets facing away
+ * but kept (the margin did not prove every triangle culled), counts[8] =
+ * planar meshlets skipped as facing away, for the last call (counts: 9
+ * words). Enabling allocates 64 bytes of device memory once. Use from one
+ * thread at a time.
  */
 HSR_API int hsr_set_stage_stats(int enable);
 HSR_API int hsr_get_stage_stats(uint32_t *counts);

@@ -694,27 +694,58 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
                 bmin[k] = std::min(bmin[k], xyz[3 * i + k]);
                 bmax[k] = std::max(bmax[k], xyz[3 * i + k]);
             }
-        // Morton order of centroids
+        // Order: by the class of the face normal (the six axis directions, or
+        // one of 64 octahedral bins), then by the Morton code of the centroid,
+        // so meshlets are compact and, where the geometry allows, planar (a
+        // planar meshlet facing away is culled whole).
         std::vector<std::pair<uint64_t, uint32_t>> order(n_tris);
         double ext[3];
         for (int k = 0; k < 3; k++) ext[k] = std::max(1e-12, (double)bmax[k] - (double)bmin[k]);
         for (uint32_t t = 0; t < n_tris; t++) {
             uint64_t code = 0;
+            double v[3][3];
+            for (int j = 0; j < 3; j++)
+                for (int k = 0; k < 3; k++) v[j][k] = (double)xyz[3 * (size_t)canon[3 * (size_t)t + j] + k];
             for (int k = 0; k < 3; k++) {
-                const double c = ((double)xyz[3 * (size_t)canon[3 * (size_t)t] + k] +
-                                  (double)xyz[3 * (size_t)canon[3 * (size_t)t + 1] + k] +
-                                  (double)xyz[3 * (size_t)canon[3 * (size_t)t + 2] + k]) / 3.0;
+                const double c = (v[0][k] + v[1][k] + v[2][k]) / 3.0;
                 double f = (c - bmin[k]) / ext[k];
                 f = std::min(std::max(f, 0.0), 1.0);
-                code |= spread21((uint64_t)(f * 2097151.0)) << k;
+                code |= spread21((uint64_t)(f * 524287.0)) << k;           // 19 bits per axis
             }
-            order[t] = {code, t};
+            double n[3] = {(v[1][1] - v[0][1]) * (v[2][2] - v[0][2]) - (v[1][2] - v[0][2]) * (v[2][1] - v[0][1]),
+                           (v[1][2] - v[0][2]) * (v[2][0] - v[0][0]) - (v[1][0] - v[0][0]) * (v[2][2] - v[0][2]),
+                           (v[1][0] - v[0][0]) * (v[2][1] - v[0][1]) - (v[1][1] - v[0][1]) * (v[2][0] - v[0][0])};
+            const double nl = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            uint64_t cls = 127;
+            if (nl > 0) {
+                for (double &x : n) x /= nl;
+                int ax = 0;
+                for (int k = 1; k < 3; k++)
+                    if (std::fabs(n[k]) > std::fabs(n[ax])) ax = k;
+                if (std::fabs(n[ax]) > 0.999) {
+                    cls = (uint64_t)(2 * ax + (n[ax] < 0 ? 1 : 0));
+                } else {
+                    const double l1 = std::fabs(n[0]) + std::fabs(n[1]) + std::fabs(n[2]);
+                    double ox = n[0] / l1, oy = n[1] / l1;
+                    if (n[2] < 0) {
+                        const double tx = (1 - std::fabs(oy)) * (ox < 0 ? -1 : 1);
+                        const double ty = (1 - std::fabs(ox)) * (oy < 0 ? -1 : 1);
+                        ox = tx;
+                        oy = ty;
+                    }
+                    const int ix = std::min(7, std::max(0, (int)((ox + 1) * 4)));
+                    const int iy = std::min(7, std::max(0, (int)((oy + 1) * 4)));
+                    cls = (uint64_t)(6 + 8 * ix + iy);
+                }
+            }
+            order[t] = {(cls << 57) | code, t};
         }
         std::sort(order.begin(), order.end());
         // greedy meshlets: <= 32 triangles, <= 64 distinct vertices
         std::vector<Meshlet> meshlets;
         std::vector<float4> mvert;
         std::vector<uint2> mtri;
+        std::vector<float4> mplane;
         std::vector<uint32_t> stamp(n_verts, 0xFFFFFFFFu);
         std::vector<uint8_t> local(n_verts, 0);
         std::vector<uint32_t> cur_v;
@@ -743,6 +774,62 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
                       ((uint32_t)local[canon[3 * (size_t)t + 2]] << 16);
                 e.y = t;
                 mtri.push_back(e);
+            }
+            // the meshlet's common plane (when its triangles share one), for
+            // culling meshlets that face away as a whole
+            {
+                double nsum[3] = {0, 0, 0}, amin = 1e300, lmax = 0;
+                bool ok = true;
+                auto P = [&](uint32_t v, int k) { return (double)xyz[3 * (size_t)v + k]; };
+                for (uint32_t t : cur_t) {
+                    const uint32_t a = canon[3 * (size_t)t], b = canon[3 * (size_t)t + 1], c = canon[3 * (size_t)t + 2];
+                    double e1[3], e2[3], e3[3];
+                    for (int k = 0; k < 3; k++) {
+                        e1[k] = P(b, k) - P(a, k);
+                        e2[k] = P(c, k) - P(a, k);
+                        e3[k] = P(c, k) - P(b, k);
+                    }
+                    const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                         e1[0] * e2[1] - e1[1] * e2[0]};
+                    const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                    if (!(len > 0)) ok = false;
+                    for (int k = 0; k < 3; k++) nsum[k] += n[k];
+                    amin = std::min(amin, 0.5 * len);
+                    lmax = std::max({lmax, std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]),
+                                     std::sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
+                                     std::sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2])});
+                }
+                const double nl = std::sqrt(nsum[0] * nsum[0] + nsum[1] * nsum[1] + nsum[2] * nsum[2]);
+                double nh[3] = {0, 0, 0}, w = 0, eps = 0, rho = 0;
+                if (ok && nl > 0) {
+                    for (int k = 0; k < 3; k++) nh[k] = nsum[k] / nl;
+                    const uint32_t a0 = canon[3 * (size_t)cur_t[0]];
+                    w = nh[0] * P(a0, 0) + nh[1] * P(a0, 1) + nh[2] * P(a0, 2);
+                    for (uint32_t v : cur_v)
+                        eps = std::max(eps, std::fabs(nh[0] * P(v, 0) + nh[1] * P(v, 1) + nh[2] * P(v, 2) - w));
+                    for (uint32_t t : cur_t) {
+                        const uint32_t a = canon[3 * (size_t)t], b = canon[3 * (size_t)t + 1], c = canon[3 * (size_t)t + 2];
+                        double e1[3], e2[3];
+                        for (int k = 0; k < 3; k++) {
+                            e1[k] = P(b, k) - P(a, k);
+                            e2[k] = P(c, k) - P(a, k);
+                        }
+                        const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                             e1[0] * e2[1] - e1[1] * e2[0]};
+                        const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                        double d2 = 0;
+                        for (int k = 0; k < 3; k++) d2 += (n[k] / len - nh[k]) * (n[k] / len - nh[k]);
+                        rho = std::max(rho, std::sqrt(d2));
+                    }
+                } else {
+                    ok = false;
+                }
+                if (!(rho < 0.01)) ok = false;
+                // rounded outwards: area down, the slack terms up
+                mplane.push_back(make_float4((float)nh[0], (float)nh[1], (float)nh[2], (float)w));
+                mplane.push_back(make_float4(ok ? (float)(amin * (1 - 1e-6)) : 0.f,
+                                             ok ? (float)(lmax * (1 + 1e-6)) : -1.f, (float)(eps * 1.01 + 1e-9),
+                                             (float)(rho * 1.01 + 1e-9)));
             }
             // inflate so the float plane tests stay conservative
             for (int k = 0; k < 3; k++) {
@@ -830,6 +917,12 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         if ((e = upload(s, groups.data(), groups.size(), &dg)) != cudaSuccess) throw e;
         if ((e = upload(s, mvert.data(), mvert.size(), &dmv)) != cudaSuccess) throw e;
         if ((e = upload(s, mtri.data(), mtri.size(), &dmt)) != cudaSuccess) throw e;
+        const float4 *dmp;
+        if ((e = upload(s, mplane.data(), mplane.size(), &dmp)) != cudaSuccess) throw e;
+        d.mplane = dmp;
+        float cmax = 0.f;
+        for (size_t i = 0; i < 3 * (size_t)n_verts; i++) cmax = std::max(cmax, std::fabs(xyz[i]));
+        d.coord_max = cmax;
         if ((e = upload(s, tri.data(), tri.size(), &dt)) != cudaSuccess) throw e;
         if ((e = upload(s, vert.data(), vert.size(), &dv)) != cudaSuccess) throw e;
         d.meshlets = dm;

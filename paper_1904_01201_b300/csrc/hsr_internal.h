@@ -40,6 +40,12 @@ struct SceneDev {
     const uint2 *mtri;         // x: local indices (8 bits each, canonical order), y: triangle index
     const uint4 *tri;          // canonical (i0, i1, i2) + output id, per triangle index
     const float4 *vert;        // x, y, z, 0 per caller vertex
+    // per meshlet, two records: (unit normal n, plane offset w) of its triangles'
+    // common plane, and (minimum triangle area, longest edge, max |n.x - w| over
+    // its vertices, max |n_t - n| over its triangles); longest edge < 0 when the
+    // triangles are not one plane (never back-face culled as a whole)
+    const float4 *mplane;
+    float coord_max;           // largest |coordinate| of any vertex
     const float2 *uv;          // per vertex, or null
     const uint32_t *vrgb;      // r | g << 8 | b << 16 per vertex, or null
     const uint32_t *atlas;     // RGBA8 texels, row-major, or null

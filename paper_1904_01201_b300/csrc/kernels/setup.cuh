@@ -83,9 +83,34 @@ __device__ __forceinline__ bool orient_cull(int X0, int Y0, float q0, int X1, in
 
 // Plane of q over the snapped vertices, relative to vertex 0:
 //   a = fma(dq1, Y2-Y0, -(dq2*(Y1-Y0))) / A,  b = fma(dq2, X1-X0, -(dq1*(X2-X0))) / A.
+// int64 -> float rounded to nearest, ties to even (the result of
+// __ll2float_rn) in integer arithmetic: the leading 24 significant bits, the
+// discarded bits decide the rounding, and the scale by 2^shift is exact. The
+// 64-bit conversion instruction runs on a slow unit of this part.
+__device__ __forceinline__ float i64_to_float_rn(long long v)
+{
+    const bool neg = v < 0;
+    const unsigned long long a = neg ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int top = 63 - __clzll((long long)(a | 1ull));          // index of the leading bit
+    const int sh = max(top - 23, 0);                                // bits that do not fit a float
+    unsigned long long m = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull);
+    const unsigned long long half = sh > 0 ? 1ull << (sh - 1) : 0ull;
+    if (sh > 0 && (rem > half || (rem == half && (m & 1ull)))) m++;
+    const float f = __fmul_rn(__uint2float_rn((uint32_t)m), __int_as_float((sh + 127) << 23));
+    return neg ? -f : f;
+}
+
+// int64 -> float within 3 units in the last place (two 32-bit conversions):
+// for shading weights, which tolerate it.
+__device__ __forceinline__ float i64_to_float_approx(long long v)
+{
+    return __fmaf_rn(__int2float_rn((int)(v >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)v));
+}
+
 __device__ __forceinline__ void depth_plane(const Tri2D &t, float &pa, float &pb)
 {
-    const float fA = __ll2float_rn(t.A);
+    const float fA = i64_to_float_rn(t.A);
     const float dq1 = __fsub_rn(t.q1, t.q0), dq2 = __fsub_rn(t.q2, t.q0);
     pa = __fdiv_rn(__fmaf_rn(dq1, __int2float_rn(t.Y2 - t.Y0), -__fmul_rn(dq2, __int2float_rn(t.Y1 - t.Y0))), fA);
     pb = __fdiv_rn(__fmaf_rn(dq2, __int2float_rn(t.X1 - t.X0), -__fmul_rn(dq1, __int2float_rn(t.X2 - t.X0))), fA);

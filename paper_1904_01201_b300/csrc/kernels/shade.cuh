@@ -132,9 +132,9 @@ __device__ __forceinline__ void interp(const Tri2D &t, int Px, int Py, const flo
     const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
     const long long e1 = (long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2);
     const long long e2 = (long long)(t.X1 - t.X0) * (Py - t.Y0) - (long long)(t.Y1 - t.Y0) * (Px - t.X0);
-    const float w0 = __fmul_rn(__ll2float_rn(e0), t.q0);
-    const float w1 = __fmul_rn(__ll2float_rn(e1), t.q1);
-    const float w2 = __fmul_rn(__ll2float_rn(e2), t.q2);
+    const float w0 = __fmul_rn(i64_to_float_approx(e0), t.q0);
+    const float w1 = __fmul_rn(i64_to_float_approx(e1), t.q1);
+    const float w2 = __fmul_rn(i64_to_float_approx(e2), t.q2);
     const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
     const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
 #pragma unroll
@@ -151,17 +151,17 @@ __device__ __forceinline__ float lod_lambda(const SceneDev &S, const Tri2D &t, i
     const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
     const long long e1 = (long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2);
     const long long e2 = (long long)(t.X1 - t.X0) * (Py - t.Y0) - (long long)(t.Y1 - t.Y0) * (Px - t.X0);
-    const float w0 = __fmul_rn(__ll2float_rn(e0), t.q0);
-    const float w1 = __fmul_rn(__ll2float_rn(e1), t.q1);
-    const float w2 = __fmul_rn(__ll2float_rn(e2), t.q2);
+    const float w0 = __fmul_rn(i64_to_float_approx(e0), t.q0);
+    const float w1 = __fmul_rn(i64_to_float_approx(e1), t.q1);
+    const float w2 = __fmul_rn(i64_to_float_approx(e2), t.q2);
     const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
     const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
-    const float x0 = __fmul_rn(-256.0f * __ll2float_rn((long long)t.Y2 - t.Y1), t.q0);
-    const float x1 = __fmul_rn(-256.0f * __ll2float_rn((long long)t.Y0 - t.Y2), t.q1);
-    const float x2 = __fmul_rn(-256.0f * __ll2float_rn((long long)t.Y1 - t.Y0), t.q2);
-    const float y0 = __fmul_rn(256.0f * __ll2float_rn((long long)t.X2 - t.X1), t.q0);
-    const float y1 = __fmul_rn(256.0f * __ll2float_rn((long long)t.X0 - t.X2), t.q1);
-    const float y2 = __fmul_rn(256.0f * __ll2float_rn((long long)t.X1 - t.X0), t.q2);
+    const float x0 = __fmul_rn(-256.0f * __int2float_rn(t.Y2 - t.Y1), t.q0);
+    const float x1 = __fmul_rn(-256.0f * __int2float_rn(t.Y0 - t.Y2), t.q1);
+    const float x2 = __fmul_rn(-256.0f * __int2float_rn(t.Y1 - t.Y0), t.q2);
+    const float y0 = __fmul_rn(256.0f * __int2float_rn(t.X2 - t.X1), t.q0);
+    const float y1 = __fmul_rn(256.0f * __int2float_rn(t.X0 - t.X2), t.q1);
+    const float y2 = __fmul_rn(256.0f * __int2float_rn(t.X1 - t.X0), t.q2);
     const float sx = __fadd_rn(__fadd_rn(x0, x1), x2), sy = __fadd_rn(__fadd_rn(y0, y1), y2);
     const float gx0 = __fmul_rn(__fmaf_rn(-l0, sx, x0), r), gy0 = __fmul_rn(__fmaf_rn(-l0, sy, y0), r);
     const float gx1 = __fmul_rn(__fmaf_rn(-l1, sx, x1), r), gy1 = __fmul_rn(__fmaf_rn(-l1, sy, y1), r);

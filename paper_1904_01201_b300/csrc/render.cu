@@ -70,6 +70,56 @@ __device__ __forceinline__ size_t vis_index(const Params &p, uint32_t phase, uin
     return phase == 0 ? (size_t)k : (phase == 2 ? (size_t)p.vis_cap - 1 - k : (size_t)p.vis_cap + k);
 }
 
+// A planar meshlet that faces away from the camera by a margin: every one of
+// its triangles then snaps to a non-negative area and is culled by the exact
+// per-triangle test, so skipping the meshlet changes nothing. Bound: the
+// unsnapped doubled screen area of a triangle of world area a whose plane the
+// camera is behind by h is 2 fx fy a h / (d0 d1 d2) (sub-pixels: x 256^2);
+// snapping and float rounding move each vertex by at most eta sub-pixels per
+// coordinate, which changes the doubled area by at most
+// 2 sqrt2 eta (|e1| + |e2|) + 8 eta^2 for edges e1, e2. With the meshlet's
+// smallest area, longest edge, the depth range and lateral extent of its box
+// and the eye-transform error of its coordinates, the meshlet is skipped only
+// when the smallest unsnapped area exceeds twice the largest change.
+__device__ __forceinline__ int meshlet_backfacing(const Params &p, const SceneDev &S, const float *M,
+                                                   const float *cpos, const float *bmin, const float *bmax,
+                                                   uint32_t m)
+{
+    const float4 pl = S.mplane[2 * (size_t)m], bd = S.mplane[2 * (size_t)m + 1];
+    const float area = bd.x, lmax = bd.y, eps_p = bd.z, rho = bd.w;
+    if (!(lmax > 0.f) || !(area > 0.f)) return 0;
+    const float h = pl.x * cpos[0] + pl.y * cpos[1] + pl.z * cpos[2] - pl.w;
+    if (!(h < 0.f)) return 0;
+    float ctr[3], ext[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        ctr[k] = 0.5f * (bmin[k] + bmax[k]);
+        ext[k] = 0.5f * (bmax[k] - bmin[k]);
+    }
+    float xc, yc, dc;
+    eye_transform(M, ctr[0], ctr[1], ctr[2], xc, yc, dc);
+    const float rx = fabsf(M[0]) * ext[0] + fabsf(M[1]) * ext[1] + fabsf(M[2]) * ext[2];
+    const float ry = fabsf(M[4]) * ext[0] + fabsf(M[5]) * ext[1] + fabsf(M[6]) * ext[2];
+    const float rd = fabsf(M[8]) * ext[0] + fabsf(M[9]) * ext[1] + fabsf(M[10]) * ext[2];
+    const float dlo = (dc - rd) * (1.f - 1e-5f), dhi = (dc + rd) * (1.f + 1e-5f) + 1e-6f;
+    if (!(dlo > 1.5f * p.znear + 1e-3f)) return 1;            // near-clip path: keep
+    const float cmax = fmaxf(fmaxf(fabsf(cpos[0]), fabsf(cpos[1])), fabsf(cpos[2]));
+    float D = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) D += fabsf(cpos[k] - ctr[k]) + ext[k];
+    // distance behind every triangle's own plane, after the planarity slack
+    const float hneed = -h - (eps_p + rho * D + 2e-6f * (3.f * cmax + fabsf(pl.w) + 1.f));
+    if (!(hneed > 0.f)) return 1;
+    const float g = fmaxf(fabsf(xc) + rx, fabsf(yc) + ry) / dlo;
+    const float f = fmaxf(p.fx, p.fy), c = fmaxf(fabsf(p.cx), fabsf(p.cy));
+    const float eps_e = 6.f * 5.9604645e-8f * (3.f * S.coord_max + 1.7320508f * cmax);
+    const float eta = 0.5f + 256.f * (f * (1.f + g) * eps_e / dlo + 4.f * 5.9604645e-8f * (f * g + c));
+    const float emax = 256.f * f * (1.f + g) * lmax * 2.f / dlo;
+    const float change = 2.8284272f * eta * 2.f * emax + 8.f * eta * eta;
+    const float sub_area = 65536.f * p.fx * p.fy * 2.f * area * hneed / (dhi * dhi * dhi);
+    return sub_area > 2.f * change ? 2 : 1;
+}
+
 __global__ void __launch_bounds__(256) cull_kernel(const Params p)
 {
     const int lane = threadIdx.x & 31;
@@ -92,6 +142,14 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         if (m < grp.m1) {
             const Meshlet ml = S.meshlets[m];
             vis = aabb_visible(pl, ml.bmin, ml.bmax);
+            if (vis) {
+                const int bf = meshlet_backfacing(p, S, p.views[vi].M, p.views[vi].pos, ml.bmin, ml.bmax, m);
+                if (p.stats) {
+                    atomicAdd(p.stats + 6, 1u);
+                    if (bf) atomicAdd(p.stats + (bf == 2 ? 8 : 7), 1u);
+                }
+                if (bf == 2) vis = false;
+            }
             const Meshlet nx = S.meshlets[m + 1];
             entry = pair_entry(vi, m, ml.vbase, nx.vbase - ml.vbase, ml.tbase, nx.tbase - ml.tbase);
             // distance band of the box from the camera -> occlusion phase
@@ -625,65 +683,34 @@ template <int NA>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
                                            uint32_t frame, uint32_t agent, uint32_t outputs)
 {
-    const uint32_t W = p.width, H = p.height;
+    // one pixel per thread: each pixel's dependent loads (key, triangle,
+    // vertices, texels) form one chain, and many threads keep many chains in
+    // flight (the pixels of ~1-pixel triangles share little setup)
+    const uint32_t W = p.width, npx = W * p.height;
     uint8_t *const out_rgb = (outputs & HSR_OUT_RGB) ? p.rgb : nullptr;
     float *const out_depth = (outputs & HSR_OUT_DEPTH) ? p.depth : nullptr;
     uint32_t *const out_ids = (outputs & HSR_OUT_IDS) ? p.ids : nullptr;
-    const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
-    unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
-    const size_t fbase = (size_t)frame * W * H;
-    const bool vec = (W % 4 == 0) && (((uintptr_t)p.rgb & 3) == 0) && (((uintptr_t)p.depth & 15) == 0) &&
-                     (((uintptr_t)p.ids & 15) == 0);
+    const unsigned long long *zb = p.zbuf + (size_t)vi * npx;
+    const size_t fbase = (size_t)frame * npx;
     const float sigma = __uint_as_float(p.dyn[3]);
     ShadeTri<NA> st;
-    for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < quads; qi += gridDim.x * blockDim.x) {
-        const uint32_t y = qi / qpr, x0 = (qi % qpr) * 4;
-        const uint32_t n = min(4u, W - x0);
-        const size_t pi = (size_t)y * W + x0;
-        unsigned long long key[4];
-        if (vec) {
-            const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(zb + pi);
-            const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(zb + pi + 2);
-            key[0] = k01.x; key[1] = k01.y; key[2] = k23.x; key[3] = k23.y;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
-        }
-        uint32_t rgb[4], id[4];
-        float dep[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k], out_rgb != nullptr);
-        if (sigma > 0.f && out_depth) {
-            const uint32_t k0 = p.dyn[4], k1 = p.dyn[5];
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (key[k] != ~0ull)
-                    dep[k] = noisy_depth(sigma, k0, k1, p.inv_far, __uint_as_float(~(uint32_t)(key[k] >> 32)),
-                                         (uint32_t)(pi + k), agent);
-        }
+    for (uint32_t pi = blockIdx.x * blockDim.x + threadIdx.x; pi < npx; pi += gridDim.x * blockDim.x) {
+        const unsigned long long key = zb[pi];
+        const uint32_t y = pi / W, x = pi - y * W;
+        uint32_t rgb, id;
+        float dep;
+        shade_pixel<NA>(st, S, M, p, (int)x, (int)y, key, rgb, dep, id, out_rgb != nullptr);
+        if (sigma > 0.f && out_depth && key != ~0ull)
+            dep = noisy_depth(sigma, p.dyn[4], p.dyn[5], p.inv_far, __uint_as_float(~(uint32_t)(key >> 32)), pi,
+                              agent);
         const size_t o = fbase + pi;
-        if (vec) {
-            if (out_rgb) {
-                // four packed 24-bit RGB values -> three little-endian words
-                uint32_t *r32 = reinterpret_cast<uint32_t *>(out_rgb + 3 * o);
-                r32[0] = rgb[0] | (rgb[1] << 24);
-                r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
-                r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
-            }
-            if (out_depth) *reinterpret_cast<float4 *>(out_depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
-            if (out_ids) *reinterpret_cast<uint4 *>(out_ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
-        } else {
-            for (uint32_t k = 0; k < n; k++) {
-                if (out_rgb) {
-                    out_rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
-                    out_rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
-                    out_rgb[3 * (o + k) + 2] = (uint8_t)((rgb[k] >> 16) & 255u);
-                }
-                if (out_depth) out_depth[o + k] = dep[k];
-                if (out_ids) out_ids[o + k] = id[k];
-            }
+        if (out_rgb) {
+            out_rgb[3 * o + 0] = (uint8_t)(rgb & 255u);
+            out_rgb[3 * o + 1] = (uint8_t)((rgb >> 8) & 255u);
+            out_rgb[3 * o + 2] = (uint8_t)((rgb >> 16) & 255u);
         }
+        if (out_depth) out_depth[o] = dep;
+        if (out_ids) out_ids[o] = id;
     }
 }
 
@@ -777,7 +804,7 @@ cudaError_t stage_timing_read(float ms[4])
 }
 
 namespace {
-uint32_t *g_stats = nullptr;      // device counters (6 words), allocated when enabled
+uint32_t *g_stats = nullptr;      // device counters (9 words), allocated when enabled
 bool g_stats_on = false;
 }  // namespace
 
@@ -786,7 +813,7 @@ uint32_t *stage_stats_buffer() { return g_stats_on ? g_stats : nullptr; }
 cudaError_t stage_stats_enable(bool on)
 {
     if (on && !g_stats) {
-        cudaError_t e = cudaMalloc(&g_stats, 8 * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&g_stats, 16 * sizeof(uint32_t));
         if (e != cudaSuccess) return e;
     }
     g_stats_on = on;
@@ -798,7 +825,7 @@ cudaError_t stage_stats_read(uint32_t out[6])
     if (!g_stats) return cudaErrorNotReady;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(out, g_stats, 6 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    return cudaMemcpy(out, g_stats, 9 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
 }
 
 static inline void mark(int k, cudaStream_t stream)
@@ -840,7 +867,7 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
     if (e != cudaSuccess) return e;
     mark(0, stream);
     if (p.stats) {
-        e = cudaMemsetAsync(p.stats, 0, 6 * sizeof(uint32_t), stream);
+        e = cudaMemsetAsync(p.stats, 0, 9 * sizeof(uint32_t), stream);
         if (e != cudaSuccess) return e;
     }
     // empty z-buffers for the active views, just before the raster: they stay
@@ -884,8 +911,8 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         mark(1, stream);
     }
     mark(2, stream);
-    const uint32_t quads = ((p.width + 3) / 4) * p.height;
-    const uint32_t bx = std::min<uint32_t>((quads + kShadeThreads - 1) / kShadeThreads, 1024);
+    const uint32_t px = p.width * p.height;
+    const uint32_t bx = std::min<uint32_t>((px + kShadeThreads - 1) / kShadeThreads, 4096);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
         shade_kernel<<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);

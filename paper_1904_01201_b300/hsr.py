@@ -206,11 +206,12 @@ def hsr_set_stage_stats(enable: bool) -> None:
 
 def hsr_get_stage_stats():
     """Work counters of the last render call: pairs and skipped meshlets per occlusion phase."""
-    c = np.zeros(6, dtype=np.uint32)
+    c = np.zeros(9, dtype=np.uint32)
     st = _lib.hsr_get_stage_stats(_np_ptr(c))
     if st != HSR_OK:
         raise HsrError(st, "hsr_get_stage_stats")
-    return {"pairs": [int(v) for v in c[:3]], "skipped": [int(v) for v in c[3:]]}
+    return {"pairs": [int(v) for v in c[:3]], "skipped": [int(v) for v in c[3:6]],
+            "frustum_meshlets": int(c[6]), "backfacing_kept": int(c[7]), "backfacing_culled": int(c[8])}
 
 
 def hsr_device_status(clear: bool = True) -> int:
