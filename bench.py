@@ -31,10 +31,11 @@ import numpy as np  # noqa: E402
 METRIC = "RGB-D frames/sec (batched vs plain)"
 # kernels per render call: cull, 3 raster phases, 2 hierarchical-z builds, shade
 def kernels_per_call(n_phases: int) -> int:
-    """Kernels one render call launches: z clear, cull, per occlusion phase a
-    raster and a large-triangle raster (and a tile-z build before every phase
-    after the first), shade."""
-    return 2 + 3 * max(1, int(n_phases))
+    """Kernels one render call launches: cull (with the z-buffer clear), per
+    occlusion phase a raster and a large-triangle raster, before every phase
+    after the first a tile-z build, its pyramid and the occlusion test, shade."""
+    P = max(1, int(n_phases))
+    return 1 + 2 * P + 3 * (P - 1) + 1
 UNIT = "frames/s"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6400.0

@@ -122,6 +122,17 @@ __device__ __forceinline__ int meshlet_backfacing(const Params &p, const SceneDe
 
 __global__ void __launch_bounds__(256) cull_kernel(const Params p)
 {
+    // the active views' z-buffers set to empty (~0), 16 bytes per store (the
+    // z-buffer starts on a 256-byte boundary); done here, before the raster,
+    // so the clear overlaps the culling's record loads and the keys are still
+    // in L2 for the raster's atomics
+    {
+        const size_t n = (size_t)p.dyn[0] * p.width * p.height;
+        ulonglong2 *z2 = reinterpret_cast<ulonglong2 *>(p.zbuf);
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x)
+            z2[i] = make_ulonglong2(~0ull, ~0ull);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) p.zbuf[n - 1] = ~0ull;
+    }
     const int lane = threadIdx.x & 31;
     const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
@@ -389,31 +400,38 @@ __device__ __forceinline__ bool box_occluded(const float *bmin, const float *bma
     return true;
 }
 
-// Hierarchical z: per 8x8 tile of each view, the largest stored key >> 32
-// (the farthest fragment, or background = 0xFFFFFFFF). Eight threads per
-// tile, one row each, combined with shuffles.
+// Tile z, level 0 of the pyramid: per 8x8 tile of each view the largest
+// stored key >> 32 (the farthest fragment, or background = 0xFFFFFFFF). Four
+// lanes per tile, each a 16-byte column of its eight rows, so a warp's loads
+// cover 512 contiguous bytes of a row; the four are combined with shuffles.
 __global__ void __launch_bounds__(256) hiz_kernel(const Params p)
 {
     const uint32_t per_view = p.hiz_w * p.hiz_h;
-    const uint32_t total = p.dyn[0] * per_view * kHizTile;
+    const uint32_t total = p.dyn[0] * per_view * 4u;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ((total + 31) & ~31u);
          g += gridDim.x * blockDim.x) {
         uint32_t mx = 0;
-        const uint32_t t = g / kHizTile, row = g % kHizTile;
+        const uint32_t t = g >> 2, part = g & 3u;
         if (g < total) {
             const uint32_t v = t / per_view, r = t % per_view;
             const uint32_t ty = r / p.hiz_w, tx = r % p.hiz_w;
-            const uint32_t y = ty * kHizTile + row, x0 = tx * kHizTile;
-            const uint32_t x1 = min(x0 + kHizTile, p.width);
-            if (y < p.height) {
-                const unsigned long long *zr = p.zbuf + (size_t)v * p.width * p.height + (size_t)y * p.width;
-                for (uint32_t x = x0; x < x1; x++) mx = max(mx, (uint32_t)(zr[x] >> 32));
+            const uint32_t x = tx * kHizTile + 2 * part;
+            const uint32_t y0 = ty * kHizTile, y1 = min(y0 + kHizTile, p.height);
+            const unsigned long long *zv = p.zbuf + (size_t)v * p.width * p.height;
+            if (x + 1 < p.width && (p.width & 1u) == 0) {
+                for (uint32_t y = y0; y < y1; y++) {
+                    const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(zv + (size_t)y * p.width + x);
+                    mx = max(mx, max((uint32_t)(k.x >> 32), (uint32_t)(k.y >> 32)));
+                }
+            } else {
+                for (uint32_t y = y0; y < y1; y++)
+                    for (uint32_t xx = x; xx < min(x + 2, p.width); xx++)
+                        mx = max(mx, (uint32_t)(zv[(size_t)y * p.width + xx] >> 32));
             }
         }
         mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 1));
         mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 2));
-        mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, 4));
-        if (g < total && row == 0) p.hiz[(size_t)(t / per_view) * p.hiz_total + t % per_view] = mx;
+        if (g < total && part == 0) p.hiz[(size_t)(t / per_view) * p.hiz_total + t % per_view] = mx;
     }
 }
 
@@ -635,19 +653,6 @@ __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params 
     }
 }
 
-// ------------------------------------------------------------------ z clear
-// Every key of the active views' z-buffers set to empty (~0), 16 bytes per
-// store (the z-buffer starts on a 256-byte boundary).
-__global__ void __launch_bounds__(256) zclear_kernel(const Params p)
-{
-    const size_t n = (size_t)p.dyn[0] * p.width * p.height;
-    ulonglong2 *z2 = reinterpret_cast<ulonglong2 *>(p.zbuf);
-    const size_t n2 = n / 2;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x)
-        z2[i] = make_ulonglong2(~0ull, ~0ull);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) p.zbuf[n - 1] = ~0ull;
-}
-
 // ----------------------------------------------------------------- mip chain
 __global__ void mip_down_kernel(const uint32_t *__restrict__ src, uint32_t w, uint32_t h, uint32_t *__restrict__ dst,
                                 uint32_t w2, uint32_t h2)
@@ -683,34 +688,65 @@ template <int NA>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
                                            uint32_t frame, uint32_t agent, uint32_t outputs)
 {
-    // one pixel per thread: each pixel's dependent loads (key, triangle,
-    // vertices, texels) form one chain, and many threads keep many chains in
-    // flight (the pixels of ~1-pixel triangles share little setup)
-    const uint32_t W = p.width, npx = W * p.height;
+    const uint32_t W = p.width, H = p.height;
     uint8_t *const out_rgb = (outputs & HSR_OUT_RGB) ? p.rgb : nullptr;
     float *const out_depth = (outputs & HSR_OUT_DEPTH) ? p.depth : nullptr;
     uint32_t *const out_ids = (outputs & HSR_OUT_IDS) ? p.ids : nullptr;
-    const unsigned long long *zb = p.zbuf + (size_t)vi * npx;
-    const size_t fbase = (size_t)frame * npx;
+    const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
+    unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
+    const size_t fbase = (size_t)frame * W * H;
+    const bool vec = (W % 4 == 0) && (((uintptr_t)p.rgb & 3) == 0) && (((uintptr_t)p.depth & 15) == 0) &&
+                     (((uintptr_t)p.ids & 15) == 0);
     const float sigma = __uint_as_float(p.dyn[3]);
     ShadeTri<NA> st;
-    for (uint32_t pi = blockIdx.x * blockDim.x + threadIdx.x; pi < npx; pi += gridDim.x * blockDim.x) {
-        const unsigned long long key = zb[pi];
-        const uint32_t y = pi / W, x = pi - y * W;
-        uint32_t rgb, id;
-        float dep;
-        shade_pixel<NA>(st, S, M, p, (int)x, (int)y, key, rgb, dep, id, out_rgb != nullptr);
-        if (sigma > 0.f && out_depth && key != ~0ull)
-            dep = noisy_depth(sigma, p.dyn[4], p.dyn[5], p.inv_far, __uint_as_float(~(uint32_t)(key >> 32)), pi,
-                              agent);
-        const size_t o = fbase + pi;
-        if (out_rgb) {
-            out_rgb[3 * o + 0] = (uint8_t)(rgb & 255u);
-            out_rgb[3 * o + 1] = (uint8_t)((rgb >> 8) & 255u);
-            out_rgb[3 * o + 2] = (uint8_t)((rgb >> 16) & 255u);
+    for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < quads; qi += gridDim.x * blockDim.x) {
+        const uint32_t y = qi / qpr, x0 = (qi % qpr) * 4;
+        const uint32_t n = min(4u, W - x0);
+        const size_t pi = (size_t)y * W + x0;
+        unsigned long long key[4];
+        if (vec) {
+            const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(zb + pi);
+            const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(zb + pi + 2);
+            key[0] = k01.x; key[1] = k01.y; key[2] = k23.x; key[3] = k23.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
         }
-        if (out_depth) out_depth[o] = dep;
-        if (out_ids) out_ids[o] = id;
+        uint32_t rgb[4], id[4];
+        float dep[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k], out_rgb != nullptr);
+        if (sigma > 0.f && out_depth) {
+            const uint32_t k0 = p.dyn[4], k1 = p.dyn[5];
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (key[k] != ~0ull)
+                    dep[k] = noisy_depth(sigma, k0, k1, p.inv_far, __uint_as_float(~(uint32_t)(key[k] >> 32)),
+                                         (uint32_t)(pi + k), agent);
+        }
+        const size_t o = fbase + pi;
+        if (vec) {
+            if (out_rgb) {
+                // four packed 24-bit RGB values -> three little-endian words
+                uint32_t *r32 = reinterpret_cast<uint32_t *>(out_rgb + 3 * o);
+                r32[0] = rgb[0] | (rgb[1] << 24);
+                r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
+                r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
+            }
+            if (out_depth) *reinterpret_cast<float4 *>(out_depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
+            if (out_ids) *reinterpret_cast<uint4 *>(out_ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
+        } else {
+            for (uint32_t k = 0; k < n; k++) {
+                if (out_rgb) {
+                    out_rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
+                    out_rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
+                    out_rgb[3 * (o + k) + 2] = (uint8_t)((rgb[k] >> 16) & 255u);
+                }
+                if (out_depth) out_depth[o + k] = dep[k];
+                if (out_ids) out_ids[o + k] = id[k];
+            }
+        }
     }
 }
 
@@ -870,20 +906,15 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         e = cudaMemsetAsync(p.stats, 0, 9 * sizeof(uint32_t), stream);
         if (e != cudaSuccess) return e;
     }
-    // empty z-buffers for the active views, just before the raster: they stay
-    // resident in L2 for its atomics
-    zclear_kernel<<<(uint32_t)sms * 4, 256, 0, stream>>>(p);
+    // culling (and the z-buffer clear it performs) runs for every call
+    cull_kernel<<<(uint32_t)sms * 8, 256, 0, stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
-        const uint32_t cull_blocks = std::min<uint32_t>((p.total_items + 7) / 8, (uint32_t)sms * 8);
-        cull_kernel<<<cull_blocks, 256, 0, stream>>>(p);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
         mark(1, stream);
         e = set_raster_smem_attr(dev);
         if (e != cudaSuccess) return e;
-        const uint32_t hiz_threads = p.n_views * p.hiz_w * p.hiz_h * kHizTile;
+        const uint32_t hiz_threads = p.n_views * p.hiz_w * p.hiz_h * 4u;
         const uint32_t hiz_blocks = std::min<uint32_t>((hiz_threads + 255) / 256, (uint32_t)sms * 16);
         for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
             if (ph > 0) {
@@ -911,8 +942,8 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         mark(1, stream);
     }
     mark(2, stream);
-    const uint32_t px = p.width * p.height;
-    const uint32_t bx = std::min<uint32_t>((px + kShadeThreads - 1) / kShadeThreads, 4096);
+    const uint32_t quads = ((p.width + 3) / 4) * p.height;
+    const uint32_t bx = std::min<uint32_t>((quads + kShadeThreads - 1) / kShadeThreads, 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
         shade_kernel<<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
