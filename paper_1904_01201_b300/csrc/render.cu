@@ -120,7 +120,7 @@ __device__ __forceinline__ int meshlet_backfacing(const Params &p, const SceneDe
     return sub_area > 2.f * change ? 2 : 1;
 }
 
-__global__ void __launch_bounds__(256) cull_kernel(const Params p)
+__global__ void __launch_bounds__(256) cull_kernel_vg(const Params p)
 {
     // the active views' z-buffers set to empty (~0), 16 bytes per store (the
     // z-buffer starts on a 256-byte boundary); done here, before the raster,
@@ -133,9 +133,18 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             z2[i] = make_ulonglong2(~0ull, ~0ull);
         if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) p.zbuf[n - 1] = ~0ull;
     }
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    // per-warp staging of the phase lists: one atomic claim per 32 entries
+    __shared__ uint4 s_buf[8][3][2 * 32];
+    uint32_t nbuf[3] = {0u, 0u, 0u};
+    auto flush = [&](uint32_t ph, uint32_t cnt) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(p.vis_count + ph, cnt);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if ((uint32_t)lane < cnt) p.vis[vis_index(p, ph, base + lane)] = s_buf[warp][ph][lane];
+    };
     ItemDecoder dec;
     const uint32_t total_items = p.dyn[1];
     for (uint32_t item = warp_id; item < total_items; item += n_warps) {
@@ -147,11 +156,23 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         const Group grp = S.groups[g];
         if (!aabb_visible(pl, grp.bmin, grp.bmax)) continue;
         const uint32_t m = grp.m0 + lane;
+        const bool valid = m < grp.m1;
+        Meshlet ml{};
+        if (valid) ml = S.meshlets[m];
+        // the next meshlet's first vertex / triangle close this one's ranges:
+        // from the neighbouring lane (whole warp, converged), or loaded by the
+        // group's last lane
+        uint32_t nvb = __shfl_down_sync(0xFFFFFFFFu, ml.vbase, 1);
+        uint32_t ntb = __shfl_down_sync(0xFFFFFFFFu, ml.tbase, 1);
+        if (valid && (m + 1 == grp.m1 || lane == 31)) {
+            const Meshlet nx = S.meshlets[m + 1];
+            nvb = nx.vbase;
+            ntb = nx.tbase;
+        }
         bool vis = false;
         uint32_t phase = 0;
         uint4 entry = make_uint4(0u, 0u, 0u, 0u);
-        if (m < grp.m1) {
-            const Meshlet ml = S.meshlets[m];
+        if (valid) {
             vis = aabb_visible(pl, ml.bmin, ml.bmax);
             if (vis) {
                 const int bf = meshlet_backfacing(p, S, p.views[vi].M, p.views[vi].pos, ml.bmin, ml.bmax, m);
@@ -161,8 +182,7 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
                 }
                 if (bf == 2) vis = false;
             }
-            const Meshlet nx = S.meshlets[m + 1];
-            entry = pair_entry(vi, m, ml.vbase, nx.vbase - ml.vbase, ml.tbase, nx.tbase - ml.tbase);
+            entry = pair_entry(vi, m, ml.vbase, nvb - ml.vbase, ml.tbase, ntb - ml.tbase);
             // distance band of the box from the camera -> occlusion phase
             const float *cp = p.views[vi].pos;
             float d2 = 0.f;
@@ -173,19 +193,156 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             }
             phase = (p.n_phases > 1 && d2 > p.phase_r2[0]) + (p.n_phases > 2 && d2 > p.phase_r2[1]);
         }
-        // one warp-aggregated append per phase list
+        // stage this item's pairs per phase; flush 32 at a time
 #pragma unroll
         for (uint32_t ph = 0; ph < 3; ph++) {
             const bool mine = vis && phase == ph;
             const unsigned mask = __ballot_sync(0xFFFFFFFFu, mine);
             if (!mask) continue;
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(p.vis_count + ph, (uint32_t)__popc(mask));
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            const uint32_t k = base + __popc(mask & ((1u << lane) - 1u));
-            if (mine) p.vis[vis_index(p, ph, k)] = entry;
+            if (mine) s_buf[warp][ph][nbuf[ph] + __popc(mask & ((1u << lane) - 1u))] = entry;
+            nbuf[ph] += (uint32_t)__popc(mask);
+            __syncwarp();
+            if (nbuf[ph] >= 32) {
+                flush(ph, 32);
+                __syncwarp();
+                const uint32_t rest = nbuf[ph] - 32;
+                uint4 moved = make_uint4(0u, 0u, 0u, 0u);
+                if ((uint32_t)lane < rest) moved = s_buf[warp][ph][32 + lane];
+                __syncwarp();
+                if ((uint32_t)lane < rest) s_buf[warp][ph][lane] = moved;
+                nbuf[ph] = rest;
+                __syncwarp();
+            }
         }
     }
+#pragma unroll
+    for (uint32_t ph = 0; ph < 3; ph++)
+        if (nbuf[ph]) flush(ph, nbuf[ph]);
+}
+
+// Views of one group tested per warp item (the group's and its meshlets'
+// records are read once for all of them).
+constexpr uint32_t kCullViews = 16;
+constexpr uint32_t kCullSlots = 32;
+
+// Frustum (and back-face) culling of every (view, meshlet) pair, group-major:
+// a warp item is (scene slot, group, block of up to kCullViews of the slot's
+// views); lane l holds meshlet m0 + l of the group, loaded once, and tests it
+// in each view of the block; the group box is tested first per view. Visible
+// pairs are staged per warp and appended 32 at a time. Used when the call has
+// at most kCullSlots scene slots (cull_kernel_vg otherwise).
+__global__ void __launch_bounds__(256) cull_kernel(const Params p)
+{
+    {
+        const size_t n = (size_t)p.dyn[0] * p.width * p.height;
+        ulonglong2 *z2 = reinterpret_cast<ulonglong2 *>(p.zbuf);
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2; i += (size_t)gridDim.x * blockDim.x)
+            z2[i] = make_ulonglong2(~0ull, ~0ull);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) p.zbuf[n - 1] = ~0ull;
+    }
+    __shared__ uint32_t s_ibase[kCullSlots + 1], s_v0[kCullSlots], s_nv[kCullSlots], s_nch[kCullSlots];
+    __shared__ uint32_t s_scene[kCullSlots];
+    __shared__ uint4 s_buf[8][3][2 * 32];
+    const uint32_t n_slots = p.dyn[2];
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (uint32_t k = 0; k < n_slots; k++) {
+            const uint32_t v0 = p.slot_view_base[k];
+            const uint32_t v1 = k + 1 < n_slots ? p.slot_view_base[k + 1] : p.dyn[0];
+            const uint32_t sc = p.slot_scene[k];
+            const uint32_t nch = (v1 - v0 + kCullViews - 1) / kCullViews;
+            s_ibase[k] = acc;
+            s_v0[k] = v0;
+            s_nv[k] = v1 - v0;
+            s_nch[k] = nch;
+            s_scene[k] = sc;
+            acc += p.scenes[sc].n_groups * nch;
+        }
+        s_ibase[n_slots] = acc;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t nbuf[3] = {0u, 0u, 0u};
+    auto flush = [&](uint32_t ph, uint32_t cnt) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(p.vis_count + ph, cnt);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if ((uint32_t)lane < cnt) p.vis[vis_index(p, ph, base + lane)] = s_buf[warp][ph][lane];
+    };
+    const uint32_t total_items = s_ibase[n_slots];
+    for (uint32_t item = warp_id; item < total_items; item += n_warps) {
+        uint32_t k = 0;
+        while (s_ibase[k + 1] <= item) k++;
+        const uint32_t local = item - s_ibase[k];
+        const uint32_t g = local / s_nch[k], ch = local % s_nch[k];
+        const uint32_t va = s_v0[k] + ch * kCullViews;
+        const uint32_t vb = min(va + kCullViews, s_v0[k] + s_nv[k]);
+        const SceneDev &S = p.scenes[s_scene[k]];
+        const Group grp = S.groups[g];
+        const uint32_t m = grp.m0 + lane;
+        const bool valid = m < grp.m1;
+        Meshlet ml{};
+        if (valid) ml = S.meshlets[m];
+        uint32_t nvb = __shfl_down_sync(0xFFFFFFFFu, ml.vbase, 1);
+        uint32_t ntb = __shfl_down_sync(0xFFFFFFFFu, ml.tbase, 1);
+        if (valid && (m + 1 == grp.m1 || lane == 31)) {
+            const Meshlet nx = S.meshlets[m + 1];
+            nvb = nx.vbase;
+            ntb = nx.tbase;
+        }
+        for (uint32_t vi = va; vi < vb; vi++) {
+            const float *pl = p.views[vi].planes;
+            if (!aabb_visible(pl, grp.bmin, grp.bmax)) continue;
+            bool vis = false;
+            uint32_t phase = 0;
+            uint4 entry = make_uint4(0u, 0u, 0u, 0u);
+            if (valid) {
+                vis = aabb_visible(pl, ml.bmin, ml.bmax);
+                if (vis) {
+                    const int bf = meshlet_backfacing(p, S, p.views[vi].M, p.views[vi].pos, ml.bmin, ml.bmax, m);
+                    if (p.stats) {
+                        atomicAdd(p.stats + 6, 1u);
+                        if (bf) atomicAdd(p.stats + (bf == 2 ? 8 : 7), 1u);
+                    }
+                    if (bf == 2) vis = false;
+                }
+                entry = pair_entry(vi, m, ml.vbase, nvb - ml.vbase, ml.tbase, ntb - ml.tbase);
+                const float *cp = p.views[vi].pos;
+                float d2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float dk = fmaxf(fmaxf(ml.bmin[c] - cp[c], cp[c] - ml.bmax[c]), 0.f);
+                    d2 = __fmaf_rn(dk, dk, d2);
+                }
+                phase = (p.n_phases > 1 && d2 > p.phase_r2[0]) + (p.n_phases > 2 && d2 > p.phase_r2[1]);
+            }
+#pragma unroll
+            for (uint32_t ph = 0; ph < 3; ph++) {
+                const bool mine = vis && phase == ph;
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, mine);
+                if (!mask) continue;
+                if (mine) s_buf[warp][ph][nbuf[ph] + __popc(mask & ((1u << lane) - 1u))] = entry;
+                nbuf[ph] += (uint32_t)__popc(mask);
+                __syncwarp();
+                if (nbuf[ph] >= 32) {
+                    flush(ph, 32);
+                    __syncwarp();
+                    const uint32_t rest = nbuf[ph] - 32;
+                    uint4 moved = make_uint4(0u, 0u, 0u, 0u);
+                    if ((uint32_t)lane < rest) moved = s_buf[warp][ph][32 + lane];
+                    __syncwarp();
+                    if ((uint32_t)lane < rest) s_buf[warp][ph][lane] = moved;
+                    nbuf[ph] = rest;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (uint32_t ph = 0; ph < 3; ph++)
+        if (nbuf[ph]) flush(ph, nbuf[ph]);
 }
 
 // --------------------------------------------------------------------- raster
@@ -907,7 +1064,10 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         if (e != cudaSuccess) return e;
     }
     // culling (and the z-buffer clear it performs) runs for every call
-    cull_kernel<<<(uint32_t)sms * 8, 256, 0, stream>>>(p);
+    if (p.n_slots <= kCullSlots)
+        cull_kernel<<<(uint32_t)sms * 8, 256, 0, stream>>>(p);
+    else
+        cull_kernel_vg<<<(uint32_t)sms * 8, 256, 0, stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
