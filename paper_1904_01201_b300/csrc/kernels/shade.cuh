@@ -36,13 +36,15 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     const uint32_t c00 = __ldg(S.atlas + (size_t)y0 * W + x0), c10 = __ldg(S.atlas + (size_t)y0 * W + x1);
     const uint32_t c01 = __ldg(S.atlas + (size_t)y1 * W + x0), c11 = __ldg(S.atlas + (size_t)y1 * W + x1);
     const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
+    const uchar4 t00 = *reinterpret_cast<const uchar4 *>(&c00), t10 = *reinterpret_cast<const uchar4 *>(&c10);
+    const uchar4 t01 = *reinterpret_cast<const uchar4 *>(&c01), t11 = *reinterpret_cast<const uchar4 *>(&c11);
+    const float v00[3] = {(float)t00.x, (float)t00.y, (float)t00.z}, v10[3] = {(float)t10.x, (float)t10.y, (float)t10.z};
+    const float v01[3] = {(float)t01.x, (float)t01.y, (float)t01.z}, v11[3] = {(float)t11.x, (float)t11.y, (float)t11.z};
     uint32_t out = 0;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const float v00 = (float)((c00 >> (8 * c)) & 255u), v10 = (float)((c10 >> (8 * c)) & 255u);
-        const float v01 = (float)((c01 >> (8 * c)) & 255u), v11 = (float)((c11 >> (8 * c)) & 255u);
-        const float top = __fmaf_rn(ax, v10, __fmul_rn(gx, v00));
-        const float bot = __fmaf_rn(ax, v11, __fmul_rn(gx, v01));
+        const float top = __fmaf_rn(ax, v10[c], __fmul_rn(gx, v00[c]));
+        const float bot = __fmaf_rn(ax, v11[c], __fmul_rn(gx, v01[c]));
         out |= round_channel(__fmaf_rn(ay, bot, __fmul_rn(gy, top))) << (8 * c);
     }
     return out;
@@ -135,7 +137,7 @@ __device__ __forceinline__ void interp(const Tri2D &t, int Px, int Py, const flo
     const float w0 = __fmul_rn(i64_to_float_approx(e0), t.q0);
     const float w1 = __fmul_rn(i64_to_float_approx(e1), t.q1);
     const float w2 = __fmul_rn(i64_to_float_approx(e2), t.q2);
-    const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
+    const float r = __fdividef(1.0f, __fadd_rn(__fadd_rn(w0, w1), w2));     // shading tolerates 2 ulp
     const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
 #pragma unroll
     for (int c = 0; c < NA; c++) attr[c] = __fmaf_rn(l0, a0[c], __fmaf_rn(l1, a1[c], __fmul_rn(l2, a2[c])));
@@ -154,7 +156,7 @@ __device__ __forceinline__ float lod_lambda(const SceneDev &S, const Tri2D &t, i
     const float w0 = __fmul_rn(i64_to_float_approx(e0), t.q0);
     const float w1 = __fmul_rn(i64_to_float_approx(e1), t.q1);
     const float w2 = __fmul_rn(i64_to_float_approx(e2), t.q2);
-    const float r = __frcp_rn(__fadd_rn(__fadd_rn(w0, w1), w2));
+    const float r = __fdividef(1.0f, __fadd_rn(__fadd_rn(w0, w1), w2));
     const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
     const float x0 = __fmul_rn(-256.0f * __int2float_rn(t.Y2 - t.Y1), t.q0);
     const float x1 = __fmul_rn(-256.0f * __int2float_rn(t.Y0 - t.Y2), t.q1);
