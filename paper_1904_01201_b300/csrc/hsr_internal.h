@@ -196,6 +196,7 @@ struct Params {
     uint4 *surv;
     uint32_t *surv_count;      // [2] survivors of phase 1, phase 2 (preset to 0)
     uint32_t fault_tx;         // test hook: extra bytes each meshlet staging waits for (0 in normal operation)
+    uint32_t cull_views;       // views a culling warp item covers (1..16, from the amount of work)
     uint32_t *stats;           // diagnostic counters or null: [0..2] pairs per phase, [3..5] skipped per phase
     // Tile bins of large triangles: a triangle with more than small_px
     // candidate pixels is stored once in `big_rec` and binned to every 8x8

@@ -220,8 +220,9 @@ __global__ void __launch_bounds__(256) cull_kernel_vg(const Params p)
         if (nbuf[ph]) flush(ph, nbuf[ph]);
 }
 
-// Views of one group tested per warp item (the group's and its meshlets'
-// records are read once for all of them).
+// Most views of one group tested per warp item (the group's and its
+// meshlets' records are read once for all of them); fewer when the call is
+// small, so that every warp still gets items.
 constexpr uint32_t kCullViews = 16;
 constexpr uint32_t kCullSlots = 32;
 
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             const uint32_t v0 = p.slot_view_base[k];
             const uint32_t v1 = k + 1 < n_slots ? p.slot_view_base[k + 1] : p.dyn[0];
             const uint32_t sc = p.slot_scene[k];
-            const uint32_t nch = (v1 - v0 + kCullViews - 1) / kCullViews;
+            const uint32_t nch = (v1 - v0 + p.cull_views - 1) / p.cull_views;
             s_ibase[k] = acc;
             s_v0[k] = v0;
             s_nv[k] = v1 - v0;
@@ -277,8 +278,8 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         while (s_ibase[k + 1] <= item) k++;
         const uint32_t local = item - s_ibase[k];
         const uint32_t g = local / s_nch[k], ch = local % s_nch[k];
-        const uint32_t va = s_v0[k] + ch * kCullViews;
-        const uint32_t vb = min(va + kCullViews, s_v0[k] + s_nv[k]);
+        const uint32_t va = s_v0[k] + ch * p.cull_views;
+        const uint32_t vb = min(va + p.cull_views, s_v0[k] + s_nv[k]);
         const SceneDev &S = p.scenes[s_scene[k]];
         const Group grp = S.groups[g];
         const uint32_t m = grp.m0 + lane;
@@ -1064,10 +1065,19 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         if (e != cudaSuccess) return e;
     }
     // culling (and the z-buffer clear it performs) runs for every call
+    // grid from the work: the z-buffer clear (16 bytes per thread, 8 stores
+    // each) and the (view, group) items, capped at 8 CTAs per SM
+    const uint64_t clear_blocks = ((uint64_t)p.n_views * p.width * p.height / 2 + 2047) / 2048;
+    const uint64_t item_blocks = ((uint64_t)p.total_items + 31) / 32;
+    const uint32_t cull_blocks = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(std::max(clear_blocks, item_blocks), (uint64_t)sms * 8));
+    Params pc = p;
+    pc.cull_views = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(kCullViews, (uint64_t)p.total_items / ((uint64_t)sms * 48)));
     if (p.n_slots <= kCullSlots)
-        cull_kernel<<<(uint32_t)sms * 8, 256, 0, stream>>>(p);
+        cull_kernel<<<cull_blocks, 256, 0, stream>>>(pc);
     else
-        cull_kernel_vg<<<(uint32_t)sms * 8, 256, 0, stream>>>(p);
+        cull_kernel_vg<<<cull_blocks, 256, 0, stream>>>(pc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (p.total_items > 0) {
