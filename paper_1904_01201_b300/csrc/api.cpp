@@ -518,7 +518,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     if (cfg_in)
         cfg = *cfg_in;
     else
-        lookup_tuned(make_key(scenes, n_scenes, n, width, height, ids != nullptr), cfg);
+        if (!lookup_tuned(make_key(scenes, n_scenes, n, width, height, ids != nullptr), cfg))
+            cfg = default_launch_cfg(items);
     Plan pl;
     make_plan(pl, n_scenes, n, width, height, list_entries, items, cfg);
 
@@ -1005,7 +1006,8 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
     if (cfg)
         lc = from_config(*cfg);
     else
-        lookup_tuned(make_key(scenes, n_scenes, n_cap, width, height, ids != nullptr), lc);
+        if (!lookup_tuned(make_key(scenes, n_scenes, n_cap, width, height, ids != nullptr), lc))
+            lc = default_launch_cfg(items);
     hsr_batch *b = new (std::nothrow) hsr_batch();
     if (!b) return HSR_ERR_OOM;
     cudaGetDevice(&b->device);

@@ -224,13 +224,24 @@ struct alignas(16) BigTriStorage {
 constexpr uint32_t kBigInstCap = 1u << 20;
 
 struct LaunchCfg {
-    uint32_t small_px = 16;
-    uint32_t bin_px = 256;
+    uint32_t small_px = 32;
+    uint32_t bin_px = 64;
     uint32_t chunk = 4;
     uint32_t raster_ctas_per_sm = 3;
-    uint32_t n_phases = 3;
-    float phase_r[2] = {3.0f, 7.0f};
+    uint32_t n_phases = 2;
+    float phase_r[2] = {4.0f, 10.0f};
 };
+
+// The configuration used when none was tuned for a call's signature: the
+// defaults, with a single occlusion phase for small calls (under 16k
+// (view, group) items, where the extra kernels of a phase cost more than the
+// culling saves).
+inline LaunchCfg default_launch_cfg(uint64_t items)
+{
+    LaunchCfg c;
+    if (items < 16384) c.n_phases = 1;
+    return c;
+}
 
 // Sets kernel attributes for the current device (call before stream capture).
 cudaError_t prepare_kernels();
