@@ -384,9 +384,12 @@ HSR_API int hsr_config_default(hsr_config *cfg);
 /*
  * Autotuner (the batching row of the scope: bin and tile sizes chosen per
  * workload). Renders the given batch repeatedly (into the given outputs)
- * under candidate configurations, timing each with CUDA events on the
- * caller's stream (median of `reps` timed calls after one warm-up), by
- * coordinate descent from the default; stores the fastest configuration for
+ * under candidate configurations, each captured as a batch graph (as
+ * hsr_batch_create does) and timed with CUDA events on the caller's stream
+ * around its launch, after a 256 MiB device write that evicts L2 (median of
+ * `reps` timed launches after one warm-up; the 256 MiB is allocated for the
+ * call), by coordinate descent from the default for this call's size (one
+ * occlusion phase below 16,384 culling items, two above); stores the fastest configuration for
  * this workload signature (scene set, n, width, height, ids present) so that
  * later hsr_render / hsr_render_batch calls with the same signature use it,
  * and returns it in *best (and its time in *best_ms). Synchronises the stream.

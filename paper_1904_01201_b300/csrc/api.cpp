@@ -1221,28 +1221,50 @@ int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         return HSR_ERR_CUDA;
     }
     int status = HSR_OK;
+    // Each candidate is timed as a batch replays it: captured into a graph,
+    // launched after a write of more than the L2 size (so that its geometry
+    // and texels come from HBM, and the host has enqueued the graph before
+    // the device reaches it), device time between events around the launch.
+    const size_t flush_bytes = 256ull << 20;
+    void *flush = nullptr;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return HSR_ERR_OOM;
+    }
     auto measure = [&](const LaunchCfg &c, float &ms) -> int {
-        int st = render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
-                              cuda_stream, &c);
+        const hsr_config hc = to_config(c);
+        hsr_batch *b = nullptr;
+        int st = batch_create(scenes, n_scenes, n, n, intr, width, height, rgb, depth, ids, &hc, &b);
         if (st != HSR_OK) return st;
         std::vector<float> t;
-        for (uint32_t r = 0; r < reps; r++) {
-            if (cudaEventRecord(e0, stream) != cudaSuccess) return HSR_ERR_CUDA;
-            st = render_views(scenes, n_scenes, scene_of_agent, poses, n, intr, width, height, rgb, depth, ids,
-                              cuda_stream, &c);
-            if (st != HSR_OK) return st;
-            if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
-                return HSR_ERR_CUDA;
+        st = hsr_batch_render(b, scene_of_agent, poses, n, nullptr, cuda_stream);
+        for (uint32_t r = 0; r < reps && st == HSR_OK; r++) {
+            if (cudaMemsetAsync(flush, r & 1, flush_bytes, stream) != cudaSuccess ||
+                cudaEventRecord(e0, stream) != cudaSuccess) {
+                st = HSR_ERR_CUDA;
+                break;
+            }
+            st = hsr_batch_render(b, scene_of_agent, poses, n, nullptr, cuda_stream);
+            if (st != HSR_OK) break;
+            if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                st = HSR_ERR_CUDA;
+                break;
+            }
             float x = 0;
             cudaEventElapsedTime(&x, e0, e1);
             t.push_back(x);
         }
+        free_batch(b);
+        if (st != HSR_OK) return st;
         std::sort(t.begin(), t.end());
         ms = t[t.size() / 2];
         return HSR_OK;
     };
-    // coordinate descent over the launch parameters, two sweeps
-    LaunchCfg cur;
+    // coordinate descent over the launch parameters from the default, two sweeps
+    uint64_t max_g = 0;
+    for (uint32_t i = 0; i < n_scenes; i++) max_g = std::max<uint64_t>(max_g, scenes[i]->dev.n_groups);
+    LaunchCfg cur = default_launch_cfg((uint64_t)n * max_g);
     float cur_ms = 0;
     status = measure(cur, cur_ms);
     const uint32_t small_v[] = {8, 16, 24, 32};
@@ -1276,6 +1298,7 @@ int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(flush);
     if (status != HSR_OK) return status;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
