@@ -206,7 +206,7 @@ struct Params {
     struct BigTri *big_rec;
     uint32_t *big_rec_count;   // [1]
     uint32_t big_rec_cap;
-    uint2 *big_inst;           // (record, first tile of a run, row-major over its tile rectangle)
+    uint2 *big_inst;           // (record, first row of a run from the top of its candidate rectangle | run length << 16)
     uint32_t *big_inst_count;  // [3]
     uint32_t big_inst_cap;
     uint32_t hiz_w, hiz_h;

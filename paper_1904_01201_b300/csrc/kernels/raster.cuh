@@ -14,8 +14,10 @@
 //  * small triangles (<= small_px <= 32 candidate pixels, bounding box under 2^15
 //    sub-pixels per axis so every edge value fits in int32): one thread walks
 //    its own triangle's pixels;
-//  * other triangles are queued per warp in shared memory and rasterised by
-//    the whole warp, lanes spread over an 8x4 pixel footprint, int64 edges.
+//  * other triangles are rasterised by a whole warp, row by row over the
+//    candidate samples of conservative per-row spans, int64 edges: queued per
+//    warp in shared memory (up to bin_px candidates) or binned in global
+//    memory as work items of up to 32 rows for a later pass.
 #pragma once
 #include "setup.cuh"
 
@@ -207,32 +209,141 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0
     }
 }
 
-// The whole warp, one 8x8 tile of a binned triangle: lane (lx, ly) covers
-// pixels (lx, ly) and (lx, ly + 4) of the tile, int64 edges.
-__device__ __forceinline__ void raster_tile_warp(const BigTri &t, int tx, int ty, int lane, float q_far,
+// int64 -> float with relative error below 2^-22 (magnitude split into two
+// 32-bit halves, both converted without cancellation): for conservative
+// bounds only.
+__device__ __forceinline__ float i64_to_float_rel(long long v)
+{
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const float f = __fmaf_rn(__uint2float_rn((uint32_t)(a >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)a));
+    return v < 0 ? -f : f;
+}
+
+// Rows of a large triangle per work item of the tile-bin path: about 1024
+// candidate pixels, at most one row per lane.
+__device__ __forceinline__ int big_rows_per_item(int x0, int x1)
+{
+    return max(1, min(32, 1024 / (x1 - x0 + 1)));
+}
+
+// The whole warp, rows [r0, r1] of a large triangle (within its candidate
+// rectangle). Lane k bounds the inside columns of row r0 + k; the candidates
+// of the 32 rows are then numbered consecutively (warp prefix sum of the row
+// lengths) and spread over the lanes 32 at a time, each lane finding its row
+// by a binary search of the prefix. Every candidate takes the exact edge test
+// and the same fp32 plane and key as the other paths: the row bounds only
+// skip columns that cannot be inside, so they never change a result.
+//
+// Row bounds: with E(j) the biased edge value at column x0 + j, a sample is
+// inside an edge iff E(j) = E(0) - 256 dy j >= 0, so the inside columns lie at
+// or below E(0) / (256 dy) (dy > 0) or at or above it (dy < 0); dy == 0
+// decides the whole row.
+//  * narrow triangles (bounding box under 2^15 sub-pixels per axis): every
+//    edge value at a candidate fits in int32 (as for small triangles); the
+//    quotient is taken in fp32 with relative error below 2^-22, under 2^-7
+//    of a column where it can fall inside the rectangle (under 2^15 columns
+//    from its start), and the bound is rounded with a 1/64-column allowance;
+//  * others: int64 edge values, the quotient from a conversion with relative
+//    error below 2^-20 (under 16 sub-pixels wherever it falls inside the
+//    image), widened by a whole column on each side.
+__device__ __forceinline__ void raster_rows_warp(const BigTri &t, int r0, int r1, int lane, float q_far,
                                                  unsigned long long *zbuf, int W)
 {
-    const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
-    const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
-    const int b2 = edge_bias(t.X0, t.Y0, t.X1, t.Y1);
-    const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
-    const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
-    const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
-    const int px = tx * 8 + (lane & 7);
-    if (px < (int)t.x0 || px > (int)t.x1) return;
-    const int Px = 256 * px + 128;
+    const int Xb[3] = {t.X1, t.X2, t.X0}, Yb[3] = {t.Y1, t.Y2, t.Y0};
+    const int dx[3] = {t.X2 - t.X1, t.X0 - t.X2, t.X1 - t.X0};
+    const int dy[3] = {t.Y2 - t.Y1, t.Y0 - t.Y2, t.Y1 - t.Y0};
+    const int bias[3] = {edge_bias(t.X1, t.Y1, t.X2, t.Y2), edge_bias(t.X2, t.Y2, t.X0, t.Y0),
+                         edge_bias(t.X0, t.Y0, t.X1, t.Y1)};
+    const int mnx = min(t.X0, min(t.X1, t.X2)), mxx = max(t.X0, max(t.X1, t.X2));
+    const int mny = min(t.Y0, min(t.Y1, t.Y2)), mxy = max(t.Y0, max(t.Y1, t.Y2));
+    const bool narrow = mxx - mnx < 32768 && mxy - mny < 32768;
+    const int Px0 = 256 * (int)t.x0 + 128;
+    const float jmax = (float)((int)t.x1 - (int)t.x0);
+    float rdy[3];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int py = ty * 8 + (lane >> 3) + 4 * h;
-        if (py < (int)t.y0 || py > (int)t.y1) continue;
-        const int Py = 256 * py + 128;
-        const long long e0 = (long long)dx0 * (Py - t.Y1) - (long long)dy0 * (Px - t.X1);
-        const long long e1 = (long long)dx1 * (Py - t.Y2) - (long long)dy1 * (Px - t.X2);
-        const long long e2 = (long long)dx2 * (Py - t.Y0) - (long long)dy2 * (Px - t.X0);
-        if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
-        const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0, t.qlo, t.qhi);
-        if (!(q >= q_far)) continue;
-        zmin(zbuf + (size_t)py * W + px, depth_key(q, t.id));
+    for (int k = 0; k < 3; k++)
+        rdy[k] = dy[k] != 0 ? __frcp_rn(__int2float_rn(narrow ? 256 * dy[k] : dy[k])) : 0.f;
+    for (int rb = r0; rb <= r1; rb += 32) {
+        const int py = rb + lane;
+        int xa = 0, len = 0;
+        if (py <= r1) {
+            const int Py = 256 * py + 128;
+            float lo = 0.f, hi = jmax;          // columns, from t.x0
+            bool empty = false;
+            if (narrow) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const int E = dx[k] * (Py - Yb[k]) - dy[k] * (Px0 - Xb[k]) - bias[k];
+                    if (dy[k] == 0) {
+                        empty |= E < 0;
+                    } else {
+                        const float lim = __fmul_rn(__int2float_rn(E), rdy[k]);
+                        if (dy[k] > 0)
+                            hi = fminf(hi, floorf(lim + 0.015625f));
+                        else
+                            lo = fmaxf(lo, ceilf(lim - 0.015625f));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const long long c = (long long)dx[k] * (Py - Yb[k]) + (long long)dy[k] * Xb[k] - bias[k];
+                    if (dy[k] == 0) {
+                        empty |= c < 0;
+                    } else {
+                        // sample column bound c / dy, as a column index from t.x0
+                        const float lim = (__fmul_rn(i64_to_float_rel(c), rdy[k]) - (float)Px0) * (1.0f / 256.0f);
+                        if (dy[k] > 0)
+                            hi = fminf(hi, floorf(lim) + 1.0f);
+                        else
+                            lo = fmaxf(lo, ceilf(lim) - 1.0f);
+                    }
+                }
+            }
+            if (!empty && lo <= hi) {
+                xa = (int)t.x0 + (int)lo;
+                len = (int)hi - (int)lo + 1;
+            }
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const int excl = incl - len;
+        for (int base = 0; base < total; base += 32) {
+            const int g = base + lane;
+            int j = 0;                                   // last row whose run starts at or before g
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int c = j + s;
+                const int e = __shfl_sync(0xFFFFFFFFu, excl, c & 31);
+                if (c < 32 && e <= g) j = c;
+            }
+            const int ej = __shfl_sync(0xFFFFFFFFu, excl, j);
+            const int xj = __shfl_sync(0xFFFFFFFFu, xa, j);
+            if (g >= total) continue;
+            const int px = xj + (g - ej), pyj = rb + j;
+            const int Px = 256 * px + 128, Py = 256 * pyj + 128;
+            bool inside;
+            if (narrow) {
+                const int e0 = dx[0] * (Py - t.Y1) - dy[0] * (Px - t.X1);
+                const int e1 = dx[1] * (Py - t.Y2) - dy[1] * (Px - t.X2);
+                const int e2 = dx[2] * (Py - t.Y0) - dy[2] * (Px - t.X0);
+                inside = ((e0 - bias[0]) | (e1 - bias[1]) | (e2 - bias[2])) >= 0;
+            } else {
+                const long long e0 = (long long)dx[0] * (Py - t.Y1) - (long long)dy[0] * (Px - t.X1);
+                const long long e1 = (long long)dx[1] * (Py - t.Y2) - (long long)dy[1] * (Px - t.X2);
+                const long long e2 = (long long)dx[2] * (Py - t.Y0) - (long long)dy[2] * (Px - t.X0);
+                inside = ((e0 - bias[0]) | (e1 - bias[1]) | (e2 - bias[2])) >= 0;
+            }
+            if (!inside) continue;
+            const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0, t.qlo, t.qhi);
+            if (!(q >= q_far)) continue;
+            zmin(zbuf + (size_t)pyj * W + px, depth_key(q, t.id));
+        }
     }
 }
 
@@ -240,26 +351,7 @@ __device__ __forceinline__ void raster_tile_warp(const BigTri &t, int tx, int ty
 __device__ __forceinline__ void raster_big_warp(const BigTri &t, int lane, float q_far, unsigned long long *zbuf,
                                                 int W)
 {
-    const int b0 = edge_bias(t.X1, t.Y1, t.X2, t.Y2);
-    const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
-    const int b2 = edge_bias(t.X0, t.Y0, t.X1, t.Y1);
-    const int dx0 = t.X2 - t.X1, dy0 = t.Y2 - t.Y1;
-    const int dx1 = t.X0 - t.X2, dy1 = t.Y0 - t.Y2;
-    const int dx2 = t.X1 - t.X0, dy2 = t.Y1 - t.Y0;
-    const int lx = lane & 7, ly = lane >> 3;
-    for (int py = (int)t.y0 + ly; py <= (int)t.y1; py += 4) {
-        const int Py = 256 * py + 128;
-        for (int px = (int)t.x0 + lx; px <= (int)t.x1; px += 8) {
-            const int Px = 256 * px + 128;
-            const long long e0 = (long long)dx0 * (Py - t.Y1) - (long long)dy0 * (Px - t.X1);
-            const long long e1 = (long long)dx1 * (Py - t.Y2) - (long long)dy1 * (Px - t.X2);
-            const long long e2 = (long long)dx2 * (Py - t.Y0) - (long long)dy2 * (Px - t.X0);
-            if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
-            const float q = plane_q(t.pa, t.pb, t.q0, Px - t.X0, Py - t.Y0, t.qlo, t.qhi);
-            if (!(q >= q_far)) continue;
-            zmin(zbuf + (size_t)py * W + px, depth_key(q, t.id));
-        }
-    }
+    raster_rows_warp(t, (int)t.y0, (int)t.y1, lane, q_far, zbuf, W);
 }
 
 }  // namespace hsr

@@ -37,7 +37,6 @@ constexpr int kRasterThreads = kRasterWarps * 32;
 constexpr int kBigCap = 2 * kMeshletTris;        // a lane emits at most two sub-triangles
 constexpr int kShadeThreads = 256;
 static_assert(sizeof(BigTri) == sizeof(BigTriStorage), "binned triangle storage size");
-constexpr uint32_t kTilesPerInst = 8;
 constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
 
 // Error flags raised by kernels of this device (kErrWaitTimeout, ...).
@@ -390,17 +389,17 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     r.view = view;
     r.pad_ = 0;
     if (p.big_rec && npx > (int)p.bin_px) {
-        // bin to 8x8 tiles for the tile raster pass
-        // instances cover runs of kTilesPerInst tiles of the triangle's tile rectangle
-        const uint32_t ntiles = (uint32_t)(((x1 >> 3) - (x0 >> 3) + 1) * ((y1 >> 3) - (y0 >> 3) + 1));
-        const uint32_t ninst = (ntiles + kTilesPerInst - 1) / kTilesPerInst;
+        // bin for the large-triangle pass: instances cover runs of
+        // big_rows_per_item rows of the triangle's candidate rectangle
+        const uint32_t rpi = (uint32_t)big_rows_per_item(x0, x1);
+        const uint32_t ninst = ((uint32_t)(y1 - y0) + rpi) / rpi;
         const uint32_t ri = atomicAdd(p.big_rec_count, 1u);
         if (ri < p.big_rec_cap) {
             const uint32_t k0 = atomicAdd(p.big_inst_count + phase, ninst);
             uint2 *inst = p.big_inst + (size_t)phase * p.big_inst_cap;
             if (k0 + ninst <= p.big_inst_cap && k0 + ninst >= k0) {
                 p.big_rec[ri] = r;
-                for (uint32_t k = 0; k < ninst; k++) inst[k0 + k] = make_uint2(ri, k * kTilesPerInst);
+                for (uint32_t k = 0; k < ninst; k++) inst[k0 + k] = make_uint2(ri, (k * rpi) | (rpi << 16));
                 return;
             }
             // reservation straddles the end: mark the in-range slots as empty
@@ -411,9 +410,10 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
     bigq[slot] = r;
 }
 
-// Tile raster of the binned large triangles of one phase: one warp per
-// instance (a triangle and a run of up to kTilesPerInst of its 8x8 tiles,
-// counted row-major over its tile rectangle), grid-stride.
+// Raster of the binned large triangles of one phase: one warp per instance
+// (a triangle and a run of up to big_rows_per_item rows of its candidate
+// rectangle: first row offset in the low 16 bits, run length in the high
+// bits; images are at most 4096 rows), grid-stride.
 __global__ void __launch_bounds__(256) big_raster_kernel(const Params p, uint32_t phase)
 {
     const int lane = threadIdx.x & 31;
@@ -425,13 +425,10 @@ __global__ void __launch_bounds__(256) big_raster_kernel(const Params p, uint32_
         const uint2 in = inst[i];
         if (in.x == kNoRecord) continue;
         const BigTri t = p.big_rec[in.x];
-        const int tx0 = t.x0 >> 3, ty0 = t.y0 >> 3;
-        const int ntx = (t.x1 >> 3) - tx0 + 1;
-        const uint32_t ntiles = (uint32_t)(ntx * ((t.y1 >> 3) - ty0 + 1));
         unsigned long long *zb = p.zbuf + (size_t)t.view * p.width * p.height;
-        const uint32_t kend = min(in.y + kTilesPerInst, ntiles);
-        for (uint32_t k = in.y; k < kend; k++)
-            raster_tile_warp(t, tx0 + (int)(k % ntx), ty0 + (int)(k / ntx), lane, p.q_far, zb, (int)p.width);
+        const int r0 = (int)t.y0 + (int)(in.y & 0xFFFFu);
+        const int r1 = min((int)t.y1, r0 + (int)(in.y >> 16) - 1);
+        raster_rows_warp(t, r0, r1, lane, p.q_far, zb, (int)p.width);
     }
 }
 
