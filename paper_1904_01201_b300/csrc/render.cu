@@ -224,11 +224,13 @@ __global__ void __launch_bounds__(256) cull_kernel_vg(const Params p)
 // small, so that every warp still gets items.
 constexpr uint32_t kCullViews = 16;
 constexpr uint32_t kCullSlots = 32;
+static_assert(kCullViews <= 32, "one lane per view of a culling item");
 
 // Frustum (and back-face) culling of every (view, meshlet) pair, group-major:
 // a warp item is (scene slot, group, block of up to kCullViews of the slot's
-// views); lane l holds meshlet m0 + l of the group, loaded once, and tests it
-// in each view of the block; the group box is tested first per view. Visible
+// views); the group box is tested in all views of the block at once (a view
+// per lane), then lane l holds meshlet m0 + l of the group, loaded once, and
+// tests it in each view that sees the group. Visible
 // pairs are staged per warp and appended 32 at a time. Used when the call has
 // at most kCullSlots scene slots (cull_kernel_vg otherwise).
 __global__ void __launch_bounds__(256) cull_kernel(const Params p)
@@ -292,9 +294,17 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             nvb = nx.vbase;
             ntb = nx.tbase;
         }
-        for (uint32_t vi = va; vi < vb; vi++) {
+        // the group box against every view of the block at once, one view
+        // per lane; then only the views that see the group
+        uint32_t vmask;
+        {
+            const uint32_t v = va + (uint32_t)lane;
+            vmask = __ballot_sync(0xFFFFFFFFu, v < vb && aabb_visible(p.views[v].planes, grp.bmin, grp.bmax));
+        }
+        while (vmask) {
+            const uint32_t vi = va + (uint32_t)(__ffs(vmask) - 1);
+            vmask &= vmask - 1u;
             const float *pl = p.views[vi].planes;
-            if (!aabb_visible(pl, grp.bmin, grp.bmax)) continue;
             bool vis = false;
             uint32_t phase = 0;
             uint4 entry = make_uint4(0u, 0u, 0u, 0u);
