@@ -21,6 +21,13 @@ __device__ __forceinline__ uint32_t round_channel(float c)
     return (uint32_t)fminf(fmaxf(r, 0.0f), 255.0f);
 }
 
+// Channel c (0..2) of a packed texel as a float, exactly: the byte placed in
+// the low mantissa bits of 2^23 (one byte permute), minus 2^23.
+__device__ __forceinline__ float texel_channel(uint32_t t, int c)
+{
+    return __fsub_rn(__uint_as_float(__byte_perm(t, 0x4B000000u, 0x7440u | (uint32_t)c)), 8388608.0f);
+}
+
 __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, float v)
 {
     const float aw = (float)S.atlas_w, ah = (float)S.atlas_h;
@@ -36,15 +43,11 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     const uint32_t c00 = __ldg(S.atlas + (size_t)y0 * W + x0), c10 = __ldg(S.atlas + (size_t)y0 * W + x1);
     const uint32_t c01 = __ldg(S.atlas + (size_t)y1 * W + x0), c11 = __ldg(S.atlas + (size_t)y1 * W + x1);
     const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
-    const uchar4 t00 = *reinterpret_cast<const uchar4 *>(&c00), t10 = *reinterpret_cast<const uchar4 *>(&c10);
-    const uchar4 t01 = *reinterpret_cast<const uchar4 *>(&c01), t11 = *reinterpret_cast<const uchar4 *>(&c11);
-    const float v00[3] = {(float)t00.x, (float)t00.y, (float)t00.z}, v10[3] = {(float)t10.x, (float)t10.y, (float)t10.z};
-    const float v01[3] = {(float)t01.x, (float)t01.y, (float)t01.z}, v11[3] = {(float)t11.x, (float)t11.y, (float)t11.z};
     uint32_t out = 0;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const float top = __fmaf_rn(ax, v10[c], __fmul_rn(gx, v00[c]));
-        const float bot = __fmaf_rn(ax, v11[c], __fmul_rn(gx, v01[c]));
+        const float top = __fmaf_rn(ax, texel_channel(c10, c), __fmul_rn(gx, texel_channel(c00, c)));
+        const float bot = __fmaf_rn(ax, texel_channel(c11, c), __fmul_rn(gx, texel_channel(c01, c)));
         out |= round_channel(__fmaf_rn(ay, bot, __fmul_rn(gy, top))) << (8 * c);
     }
     return out;
@@ -71,8 +74,8 @@ __device__ __forceinline__ void sample_level(const SceneDev &S, uint32_t l, floa
     const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
-        const float v00 = (float)((c00 >> (8 * ch)) & 255u), v10 = (float)((c10 >> (8 * ch)) & 255u);
-        const float v01 = (float)((c01 >> (8 * ch)) & 255u), v11 = (float)((c11 >> (8 * ch)) & 255u);
+        const float v00 = texel_channel(c00, ch), v10 = texel_channel(c10, ch);
+        const float v01 = texel_channel(c01, ch), v11 = texel_channel(c11, ch);
         const float top = __fmaf_rn(ax, v10, __fmul_rn(gx, v00));
         const float bot = __fmaf_rn(ax, v11, __fmul_rn(gx, v01));
         c[ch] = __fmaf_rn(ay, bot, __fmul_rn(gy, top));
@@ -127,16 +130,25 @@ __device__ __forceinline__ void load_tri(const SceneDev &S, const float *M, cons
 
 // Perspective-correct attribute interpolation at P over an oriented triangle
 // whose attributes are a0 (vertex 0), a1 (vertex 1), a2 (vertex 2).
+// `narrow`: the triangle's bounding box is under 2^15 sub-pixels per axis and
+// P lies in it, so every edge value fits in int32 and converts in one step.
 template <int NA>
-__device__ __forceinline__ void interp(const Tri2D &t, int Px, int Py, const float *a0, const float *a1,
-                                       const float *a2, float (&attr)[3])
+__device__ __forceinline__ void interp(const Tri2D &t, bool narrow, int Px, int Py, const float *a0,
+                                       const float *a1, const float *a2, float (&attr)[3])
 {
-    const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
-    const long long e1 = (long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2);
-    const long long e2 = (long long)(t.X1 - t.X0) * (Py - t.Y0) - (long long)(t.Y1 - t.Y0) * (Px - t.X0);
-    const float w0 = __fmul_rn(i64_to_float_approx(e0), t.q0);
-    const float w1 = __fmul_rn(i64_to_float_approx(e1), t.q1);
-    const float w2 = __fmul_rn(i64_to_float_approx(e2), t.q2);
+    float f0, f1, f2;
+    if (narrow) {
+        f0 = __int2float_rn((t.X2 - t.X1) * (Py - t.Y1) - (t.Y2 - t.Y1) * (Px - t.X1));
+        f1 = __int2float_rn((t.X0 - t.X2) * (Py - t.Y2) - (t.Y0 - t.Y2) * (Px - t.X2));
+        f2 = __int2float_rn((t.X1 - t.X0) * (Py - t.Y0) - (t.Y1 - t.Y0) * (Px - t.X0));
+    } else {
+        f0 = i64_to_float_approx((long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1));
+        f1 = i64_to_float_approx((long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2));
+        f2 = i64_to_float_approx((long long)(t.X1 - t.X0) * (Py - t.Y0) - (long long)(t.Y1 - t.Y0) * (Px - t.X0));
+    }
+    const float w0 = __fmul_rn(f0, t.q0);
+    const float w1 = __fmul_rn(f1, t.q1);
+    const float w2 = __fmul_rn(f2, t.q2);
     const float r = __fdividef(1.0f, __fadd_rn(__fadd_rn(w0, w1), w2));     // shading tolerates 2 ulp
     const float l0 = __fmul_rn(w0, r), l1 = __fmul_rn(w1, r), l2 = __fmul_rn(w2, r);
 #pragma unroll
@@ -183,7 +195,8 @@ template <int NA>
 struct ShadeTri {
     uint32_t tri = 0xFFFFFFFFu;
     bool clipped = false;
-    Tri2D t;                            // oriented (unclipped case)
+    bool narrow = false;                // bounding box under 2^15 sub-pixels per axis
+    Tri2D t;                            // oriented (unclipped case; t.A is not set)
     float a[3][NA > 0 ? NA : 1];        // attributes in oriented order
     uint4 T;
 };
@@ -202,8 +215,13 @@ __device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev
     float q[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) project_snap(v[k].xe, v[k].ye, v[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
-    // a winning fragment exists, so the triangle is front facing: orient_cull succeeds
-    orient_cull(X[0], Y[0], q[0], X[1], Y[1], q[1], X[2], Y[2], q[2], st.t);
+    // a winning fragment exists, so the triangle is front facing (its area
+    // is negative): orient_cull's order, vertices 1 and 2 swapped
+    st.t.X0 = X[0]; st.t.Y0 = Y[0]; st.t.q0 = q[0];
+    st.t.X1 = X[2]; st.t.Y1 = Y[2]; st.t.q1 = q[2];
+    st.t.X2 = X[1]; st.t.Y2 = Y[1]; st.t.q2 = q[1];
+    st.narrow = max(X[0], max(X[1], X[2])) - min(X[0], min(X[1], X[2])) < 32768 &&
+                max(Y[0], max(Y[1], Y[2])) - min(Y[0], min(Y[1], Y[2])) < 32768;
 #pragma unroll
     for (int c = 0; c < NA; c++) {
         st.a[0][c] = v[0].a[c];
@@ -240,7 +258,7 @@ __device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M,
         const float qq = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0, tri_qlo(t), tri_qhi(t));
         if (__float_as_uint(qq) != __float_as_uint(qk)) continue;
         // oriented order is (poly 0, poly f+2, poly f+1)
-        interp<NA>(t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a, attr);
+        interp<NA>(t, false, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a, attr);
         if constexpr (NA == 2)
             if (S.sample_mode == HSR_SAMPLE_TRILINEAR)
                 lambda = lod_lambda(S, t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a);
@@ -315,7 +333,7 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
     float a[3] = {0.f, 0.f, 0.f};
     float lambda = 0.0f;
     if (!st.clipped) {
-        interp<NA>(st.t, Px, Py, st.a[0], st.a[1], st.a[2], a);
+        interp<NA>(st.t, st.narrow, Px, Py, st.a[0], st.a[1], st.a[2], a);
         if constexpr (NA == 2)
             if (S.sample_mode == HSR_SAMPLE_TRILINEAR) lambda = lod_lambda(S, st.t, Px, Py, st.a[0], st.a[1], st.a[2]);
         rgb = shade_colour<NA>(S, a, lambda);
