@@ -13,7 +13,7 @@
 //   K4 — per-thread raster of small triangles, warp-cooperative raster of the
 //        rest, into the view's 64-bit z-buffer (raster.cuh)
 // hiz_kernel: between phases, the farthest stored key of every 8x8 tile.
-// shade_kernel (K5): one CTA row per view; each thread resolves four
+// shade_kernel (K5): one CTA row per view; each thread resolves kShadePx
 //   consecutive pixels of a row (shade.cuh) and writes RGB / depth / id with
 //   vector stores when the row layout allows it.
 // Work items are ordered scene-major then view-major, so a scene's geometry
@@ -35,7 +35,13 @@ namespace hsr {
 constexpr int kRasterWarps = 8;
 constexpr int kRasterThreads = kRasterWarps * 32;
 constexpr int kBigCap = 2 * kMeshletTris;        // a lane emits at most two sub-triangles
-constexpr int kShadeThreads = 256;
+// Shading is bound by the latency of its dependent loads (key -> triangle ->
+// vertices -> texels): small CTAs, two pixels per thread and a 64-register
+// bound (8 CTAs, 32 warps per SM) keep the most of them in flight; measured
+// faster than four pixels per thread or one, at 16 to 40 warps per SM.
+constexpr int kShadeThreads = 128;
+constexpr int kShadePx = 2;                      // consecutive pixels of a row per shading thread
+static_assert(kShadePx == 1 || kShadePx == 2 || kShadePx == 4, "shading vector width");
 static_assert(sizeof(BigTri) == sizeof(BigTriStorage), "binned triangle storage size");
 constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
 
@@ -853,56 +859,81 @@ template <int NA>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
                                            uint32_t frame, uint32_t agent, uint32_t outputs)
 {
+    constexpr int K = kShadePx;
     const uint32_t W = p.width, H = p.height;
     uint8_t *const out_rgb = (outputs & HSR_OUT_RGB) ? p.rgb : nullptr;
     float *const out_depth = (outputs & HSR_OUT_DEPTH) ? p.depth : nullptr;
     uint32_t *const out_ids = (outputs & HSR_OUT_IDS) ? p.ids : nullptr;
-    const uint32_t qpr = (W + 3) / 4, quads = qpr * H;
+    const uint32_t qpr = (W + K - 1) / K, quads = qpr * H;
     unsigned long long *zb = p.zbuf + (size_t)vi * W * H;
     const size_t fbase = (size_t)frame * W * H;
-    const bool vec = (W % 4 == 0) && (((uintptr_t)p.rgb & 3) == 0) && (((uintptr_t)p.depth & 15) == 0) &&
-                     (((uintptr_t)p.ids & 15) == 0);
+    // vector stores: K pixels of a row are K consecutive outputs when W is a
+    // multiple of K (and the frame base then is too)
+    const bool vec = (W % K == 0) && (((uintptr_t)p.rgb & (K == 4 ? 3 : 1)) == 0) &&
+                     (((uintptr_t)p.depth & (4 * K - 1)) == 0) && (((uintptr_t)p.ids & (4 * K - 1)) == 0);
     const float sigma = __uint_as_float(p.dyn[3]);
-    ShadeTri<NA> st;
     for (uint32_t qi = blockIdx.x * blockDim.x + threadIdx.x; qi < quads; qi += gridDim.x * blockDim.x) {
-        const uint32_t y = qi / qpr, x0 = (qi % qpr) * 4;
-        const uint32_t n = min(4u, W - x0);
+        ShadeTri<NA> st;           // setup cache over this thread's run of pixels
+        const uint32_t y = qi / qpr, x0 = (qi % qpr) * K;
+        const uint32_t n = min((uint32_t)K, W - x0);
         const size_t pi = (size_t)y * W + x0;
-        unsigned long long key[4];
-        if (vec) {
-            const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(zb + pi);
-            const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(zb + pi + 2);
-            key[0] = k01.x; key[1] = k01.y; key[2] = k23.x; key[3] = k23.y;
-        } else {
+        unsigned long long key[K];
+        bool loaded = false;
+        if constexpr (K > 1) {
+            if (vec) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
+                for (int k = 0; k + 1 < K; k += 2) {
+                    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(zb + pi + k);
+                    key[k] = kk.x;
+                    key[k + 1] = kk.y;
+                }
+                loaded = true;
+            }
         }
-        uint32_t rgb[4], id[4];
-        float dep[4];
+        if (!loaded) {
 #pragma unroll
-        for (int k = 0; k < 4; k++)
+            for (int k = 0; k < K; k++) key[k] = k < (int)n ? zb[pi + k] : ~0ull;
+        }
+        uint32_t rgb[K], id[K];
+        float dep[K];
+#pragma unroll
+        for (int k = 0; k < K; k++)
             shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k], out_rgb != nullptr);
         if (sigma > 0.f && out_depth) {
             const uint32_t k0 = p.dyn[4], k1 = p.dyn[5];
 #pragma unroll
-            for (int k = 0; k < 4; k++)
+            for (int k = 0; k < K; k++)
                 if (key[k] != ~0ull)
                     dep[k] = noisy_depth(sigma, k0, k1, p.inv_far, __uint_as_float(~(uint32_t)(key[k] >> 32)),
                                          (uint32_t)(pi + k), agent);
         }
         const size_t o = fbase + pi;
-        if (vec) {
-            if (out_rgb) {
-                // four packed 24-bit RGB values -> three little-endian words
-                uint32_t *r32 = reinterpret_cast<uint32_t *>(out_rgb + 3 * o);
-                r32[0] = rgb[0] | (rgb[1] << 24);
-                r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
-                r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
+        if (vec && K > 1) {
+            if constexpr (K == 4) {
+                if (out_rgb) {
+                    // four packed 24-bit RGB values -> three little-endian words
+                    uint32_t *r32 = reinterpret_cast<uint32_t *>(out_rgb + 3 * o);
+                    r32[0] = rgb[0] | (rgb[1] << 24);
+                    r32[1] = (rgb[1] >> 8) | (rgb[2] << 16);
+                    r32[2] = (rgb[2] >> 16) | (rgb[3] << 8);
+                }
+                if (out_depth) *reinterpret_cast<float4 *>(out_depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
+                if (out_ids) *reinterpret_cast<uint4 *>(out_ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
+            } else if constexpr (K == 2) {
+                if (out_rgb) {
+                    // two packed 24-bit RGB values -> three little-endian halfwords
+                    uint16_t *r16 = reinterpret_cast<uint16_t *>(out_rgb + 3 * o);
+                    r16[0] = (uint16_t)rgb[0];
+                    r16[1] = (uint16_t)((rgb[0] >> 16) | (rgb[1] << 8));
+                    r16[2] = (uint16_t)(rgb[1] >> 8);
+                }
+                if (out_depth) *reinterpret_cast<float2 *>(out_depth + o) = make_float2(dep[0], dep[1]);
+                if (out_ids) *reinterpret_cast<uint2 *>(out_ids + o) = make_uint2(id[0], id[1]);
             }
-            if (out_depth) *reinterpret_cast<float4 *>(out_depth + o) = make_float4(dep[0], dep[1], dep[2], dep[3]);
-            if (out_ids) *reinterpret_cast<uint4 *>(out_ids + o) = make_uint4(id[0], id[1], id[2], id[3]);
         } else {
-            for (uint32_t k = 0; k < n; k++) {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if ((uint32_t)k >= n) break;
                 if (out_rgb) {
                     out_rgb[3 * (o + k) + 0] = (uint8_t)(rgb[k] & 255u);
                     out_rgb[3 * (o + k) + 1] = (uint8_t)((rgb[k] >> 8) & 255u);
@@ -915,7 +946,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
     }
 }
 
-__global__ void __launch_bounds__(kShadeThreads) shade_kernel(const Params p, uint32_t view0)
+__global__ void __launch_bounds__(kShadeThreads, 8) shade_kernel(const Params p, uint32_t view0)
 {
     __shared__ float sM[12];
     __shared__ SceneDev sS;
@@ -1119,7 +1150,7 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         mark(1, stream);
     }
     mark(2, stream);
-    const uint32_t quads = ((p.width + 3) / 4) * p.height;
+    const uint32_t quads = ((p.width + kShadePx - 1) / kShadePx) * p.height;
     const uint32_t bx = std::min<uint32_t>((quads + kShadeThreads - 1) / kShadeThreads, 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
