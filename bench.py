@@ -362,25 +362,60 @@ def run_gpu(args, wk):
         plain = {"value": n * psteps / (pms / 1e3), "ms_per_step": pms / psteps,
                  "launches_per_step": n}
 
-    # end to end through the C-ABI with host buffers: host poses in, H2D of
-    # the view descriptors inside the call, D2H of RGB + depth to pinned host memory
-    host_rgb = torch.empty(out["rgb"].shape, dtype=torch.uint8, pin_memory=True)
-    host_depth = torch.empty(out["depth"].shape, dtype=torch.float32, pin_memory=True)
-    for _ in range(args.warmup):
-        step()
-        host_rgb.copy_(out["rgb"], non_blocking=True)
-        host_depth.copy_(out["depth"], non_blocking=True)
-    torch.cuda.synchronize()
+    # end to end through the C-ABI with host buffers: every step renders from
+    # host poses (the view descriptors go up inside the call) and copies its
+    # outputs to page-locked host memory (hsr_batch_render_host); two batches
+    # on two streams alternate so that one step's copies overlap the next
+    # step's render, and a step's host buffers are waited for before reuse
+    def host_like(o):
+        return {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items() if v is not None}
+
     e2e_steps = max(3, args.steps // 4)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step()
-        host_rgb.copy_(out["rgb"], non_blocking=True)
-        host_depth.copy_(out["depth"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-    e2e_dt = time.perf_counter() - t0
-    e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(poses.nbytes),
-           "d2h_bytes_per_step": int(out["rgb"].numel() + 4 * out["depth"].numel())}
+    if args.mode == "batched":
+        out2 = hsr.alloc_outputs(n, W, H, ids=wk["ids"], device=dev)
+        graph2 = hsr.hsr_batch_create([h.handle for h in handles], n, wk["intr"], W, H, out2["rgb"],
+                                      out2["depth"], out2.get("ids"))
+        pipes = [(graph, torch.cuda.Stream(dev), host_like(out)), (graph2, torch.cuda.Stream(dev), host_like(out2))]
+        h2d_step = [0]
+
+        def e2e_step(i):
+            b, s, hb = pipes[i % 2]
+            s.synchronize()                      # this pipe's previous frames are in host memory
+            st, h2d_step[0] = hsr.hsr_batch_render_host(b, soa if multi else None, poses, W, H, hb["rgb"],
+                                                        hb["depth"], hb.get("ids"), s)
+            if st != 0:
+                raise hsr.HsrError(st, "hsr_batch_render_host")
+
+        for i in range(args.warmup):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            e2e_step(i)
+        for _, s, _ in pipes:
+            s.synchronize()
+        e2e_dt = time.perf_counter() - t0
+        hsr.hsr_batch_destroy(graph2)
+        h2d_bytes = h2d_step[0]
+        d2h_bytes = sum(v.numel() * v.element_size() for v in pipes[0][2].values())
+    else:
+        hb = host_like(out)
+        for _ in range(args.warmup):
+            step()
+            for k, v in hb.items():
+                v.copy_(out[k], non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            step()
+            for k, v in hb.items():
+                v.copy_(out[k], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e2e_dt = time.perf_counter() - t0
+        h2d_bytes = int(poses.nbytes)
+        d2h_bytes = sum(v.numel() * v.element_size() for v in hb.values())
+    e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
+           "d2h_bytes_per_step": int(d2h_bytes)}
 
     if rank != 0:
         return None

@@ -317,6 +317,23 @@ HSR_API int hsr_batch_render_noisy(hsr_batch *batch, const uint32_t *scene_of_ag
  * frame < the batch's frame count). */
 HSR_API int hsr_batch_render_views(hsr_batch *batch, const hsr_view *views, uint32_t n,
                                    const hsr_depth_noise *noise, void *cuda_stream);
+/*
+ * Render to host memory (the GPU->CPU transfer of Table 2): hsr_batch_render
+ * of n views into frames 0..n-1, then device->host copies of those frames'
+ * outputs on the same stream: host_rgb [n][H][W][3], host_depth [n][H][W],
+ * host_ids [n][H][W] (host memory, page-locked for the copies to run
+ * asynchronously; each may be NULL to skip that output, and a non-NULL one
+ * needs the batch's device buffer of that output, else HSR_ERR_INVALID_ARG).
+ * Asynchronous like cudaMemcpyAsync: the host buffers hold the frames once
+ * the stream has passed the copies. Copies of one call overlap the render of
+ * another only on another stream: alternate two batches (each with its own
+ * device outputs) on two streams to keep both the copy engine and the SMs
+ * busy. *h2d_bytes (may be NULL) receives the bytes the call uploads (the
+ * view descriptor block).
+ */
+HSR_API int hsr_batch_render_host(hsr_batch *batch, const uint32_t *scene_of_agent, const hsr_pose *poses,
+                                  uint32_t n, uint8_t *host_rgb, float *host_depth, uint32_t *host_ids,
+                                  void *cuda_stream, uint64_t *h2d_bytes);
 HSR_API int hsr_batch_destroy(hsr_batch *batch);
 
 /*

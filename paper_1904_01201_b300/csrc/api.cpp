@@ -1090,6 +1090,28 @@ int hsr_batch_render_noisy(hsr_batch *b, const uint32_t *scene_of_agent, const h
     return HSR_OK;
 }
 
+int hsr_batch_render_host(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
+                          uint8_t *host_rgb, float *host_depth, uint32_t *host_ids, void *cuda_stream,
+                          uint64_t *h2d_bytes)
+{
+    if (!b || (host_rgb && !b->rgb) || (host_depth && !b->depth) || (host_ids && !b->ids))
+        return HSR_ERR_INVALID_ARG;
+    const int st = hsr_batch_render_noisy(b, scene_of_agent, poses, n, nullptr, nullptr, cuda_stream);
+    if (st != HSR_OK) return st;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const size_t px = (size_t)n * b->plan.width * b->plan.height;
+    if (host_rgb && cudaMemcpyAsync(host_rgb, b->rgb, 3 * px, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return HSR_ERR_CUDA;
+    if (host_depth &&
+        cudaMemcpyAsync(host_depth, b->depth, sizeof(float) * px, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return HSR_ERR_CUDA;
+    if (host_ids &&
+        cudaMemcpyAsync(host_ids, b->ids, sizeof(uint32_t) * px, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return HSR_ERR_CUDA;
+    if (h2d_bytes) *h2d_bytes = b->plan.desc_bytes;
+    return HSR_OK;
+}
+
 int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, const uint8_t *actions, uint32_t n,
                    const uint32_t *frames, const hsr_depth_noise *noise, void *cuda_stream)
 {

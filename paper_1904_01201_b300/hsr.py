@@ -153,6 +153,7 @@ def _load():
         "hsr_render_noisy": ([P, U32, P, P, U32, ctypes.POINTER(hsr_intrinsics), U32, U32, P, P, P,
                               ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
         "hsr_batch_render_noisy": ([P, P, P, U32, P, ctypes.POINTER(hsr_depth_noise), P], ctypes.c_int),
+        "hsr_batch_render_host": ([P, P, P, U32, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "hsr_server_create": ([P, U32, ctypes.POINTER(hsr_server_config), ctypes.POINTER(P)], ctypes.c_int),
         "hsr_server_submit": ([P, P, U32], ctypes.c_int),
         "hsr_server_attach_agents": ([P, P], ctypes.c_int),
@@ -433,6 +434,35 @@ def hsr_batch_render_noisy(batch, scene_of_agent, poses, frames=None, noise_sigm
     return st
 
 
+def _host_ptr(a, nbytes: int, what: str):
+    """Address of a host buffer (numpy array or CPU torch tensor, contiguous)
+    of at least nbytes, or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.nbytes < nbytes:
+            raise ValueError(f"{what}: needs a contiguous host array of {nbytes} bytes")
+        return ctypes.c_void_p(a.ctypes.data)
+    if a.is_cuda or not a.is_contiguous() or a.numel() * a.element_size() < nbytes:
+        raise ValueError(f"{what}: needs a contiguous host tensor of {nbytes} bytes")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def hsr_batch_render_host(batch, scene_of_agent, poses, width, height, host_rgb=None, host_depth=None,
+                          host_ids=None, stream=None):
+    """Render into frames 0..n-1 and copy them to the given host buffers on
+    `stream` (asynchronous). Returns (status, bytes uploaded)."""
+    poses = np.ascontiguousarray(poses, dtype=np.float32).reshape(-1, 7)
+    n = poses.shape[0]
+    soa = None if scene_of_agent is None else np.ascontiguousarray(scene_of_agent, dtype=np.uint32).reshape(-1)
+    px = n * width * height
+    h2d = ctypes.c_uint64(0)
+    st = _lib.hsr_batch_render_host(ctypes.c_void_p(batch), _np_ptr(soa), _np_ptr(poses), n,
+                                    _host_ptr(host_rgb, 3 * px, "host_rgb"), _host_ptr(host_depth, 4 * px, "host_depth"),
+                                    _host_ptr(host_ids, 4 * px, "host_ids"), _stream_ptr(stream), ctypes.byref(h2d))
+    return st, int(h2d.value)
+
+
 def hsr_batch_destroy(batch) -> None:
     _lib.hsr_batch_destroy(ctypes.c_void_p(batch))
 
@@ -521,6 +551,18 @@ class Batch:
         if st != HSR_OK:
             raise HsrError(st, "hsr_batch_render")
         return self.out
+
+    def render_host(self, poses, host, scene_of_agent=None, stream=None) -> int:
+        """Render into frames 0..n-1 and copy their outputs to host buffers
+        (dict with any of "rgb", "depth", "ids": page-locked CPU tensors) on
+        `stream`; the host buffers are complete once the stream has passed the
+        copies. Returns the bytes uploaded (view descriptors)."""
+        W, H = self.out["rgb"].shape[2], self.out["rgb"].shape[1]
+        st, h2d = hsr_batch_render_host(self.handle, scene_of_agent, poses, W, H, host.get("rgb"),
+                                        host.get("depth"), host.get("ids"), stream)
+        if st != HSR_OK:
+            raise HsrError(st, "hsr_batch_render_host")
+        return h2d
 
     def step(self, agents: "Agents", agent_idx, actions, frames=None, stream=None, noise_sigma=None, noise_seed=0,
              agent_ids=None):

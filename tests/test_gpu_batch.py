@@ -58,3 +58,38 @@ def test_batch_rejects_too_many_views():
         hsr.HSR_ERR_INVALID_ARG
     b.close()
     h.close()
+
+
+def test_render_host_matches_device_outputs():
+    """hsr_batch_render_host: the host copies equal the device frames of the
+    same replay, two batches alternating on two streams (the overlapped form);
+    outputs the batch lacks are rejected."""
+    sc = wl.make_house(23, 60_000, 256)
+    h = hsr.SceneHandle(sc)
+    W, H, n = 80, 64, 9
+    intr = wl.pinhole_90(W, H)
+    bs = [hsr.Batch([h], n, intr, W, H), hsr.Batch([h], n, intr, W, H)]
+    ss = [torch.cuda.Stream(), torch.cuda.Stream()]
+    hosts = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in b.out.items()} for b in bs]
+    for rep in range(4):
+        k = rep % 2
+        ss[k].synchronize()
+        poses = wl.random_poses(sc, n, 300 + rep)
+        up = bs[k].render_host(poses, hosts[k], stream=ss[k])
+        assert up > 0
+        ss[k].synchronize()
+        ref = _np(hsr.render(h, poses, intr, W, H))
+        got = {"rgb": hosts[k]["rgb"].numpy(), "depth": hosts[k]["depth"].numpy(),
+               "ids": hosts[k]["ids"].numpy().view(np.uint32)}
+        for key in ref:
+            assert np.array_equal(got[key], ref[key]), (rep, key)
+    nod = hsr.Batch([h], 2, intr, W, H, ids=False)
+    st, _ = hsr.hsr_batch_render_host(nod.handle, None, wl.random_poses(sc, 2, 0), W, H,
+                                      host_ids=torch.empty((2, H, W), dtype=torch.int32, pin_memory=True))
+    assert st == hsr.HSR_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        hsr.hsr_batch_render_host(nod.handle, None, wl.random_poses(sc, 2, 0), W, H,
+                                  host_rgb=torch.empty((1, H, W, 3), dtype=torch.uint8))
+    for b in bs + [nod]:
+        b.close()
+    h.close()
