@@ -185,14 +185,15 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(wk, n_frames: int, seconds_cap: float = 30.0):
-    """The oracle, as it stands, on a bounded sample of the workload's views."""
+def cpu_baseline(wk, n_frames: int, min_seconds: float = 10.0, seconds_cap: float = 30.0):
+    """The oracle, as it stands, on a bounded sample of the workload's views:
+    at least n_frames views and min_seconds of CPU work, at most seconds_cap."""
     import oracle
     cores = os.cpu_count() or 1
     poses, soa = wk["poses"], wk["soa"]
     done, t0 = 0, time.perf_counter()
     i = 0
-    while done < n_frames and time.perf_counter() - t0 < seconds_cap:
+    while time.perf_counter() - t0 < seconds_cap and not (done >= n_frames and time.perf_counter() - t0 >= min_seconds):
         s = int(soa[i % len(soa)])
         sel = [j for j in range(i, min(i + cores, len(soa))) if soa[j] == s] or [i % len(soa)]
         oracle.render(wk["scenes"][s], poses[sel], wk["intr"], wk["W"], wk["H"], nthreads=cores, ids=wk["ids"])
