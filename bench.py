@@ -178,6 +178,23 @@ def recorded_traffic(workload_name: str):
         return None
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's timed-region length (every rank calls it; a single
+    rank gets its own)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(frames_per_rank: int, world: int, ms_max: float) -> float:
+    """Frames/s of the whole job: every rank's frames over the slowest rank's time."""
+    return frames_per_rank * world / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -326,13 +343,8 @@ def run_gpu(args, wk):
 
     ms, launches, clocks = timed(step, args.steps, uuid)
     local_ms = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    frames = n * args.steps * world
-    value = frames / (ms / 1e3)
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_value(n * args.steps, world, ms)
 
     # per-stage device times (CUDA events recorded by the library around each
     # kernel on this stream), over separate steps after the timed region
