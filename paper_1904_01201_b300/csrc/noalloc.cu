@@ -159,7 +159,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = host_far_threshold(intr->zfar);
     p.inv_far = (float)(1.0 / (double)intr->zfar);
-    const LaunchCfg cfg = default_launch_cfg(items);
+    const LaunchCfg cfg = default_launch_cfg(items, width, height);
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;
     p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + lbytes);
