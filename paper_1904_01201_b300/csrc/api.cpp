@@ -19,6 +19,7 @@
 
 #include "camera.h"
 #include "hsr_internal.h"
+#include "launch_defaults.h"
 
 using namespace hsr;
 
@@ -519,7 +520,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
         cfg = *cfg_in;
     else
         if (!lookup_tuned(make_key(scenes, n_scenes, n, width, height, ids != nullptr), cfg))
-            cfg = default_launch_cfg(items, width, height);
+            cfg = default_launch_cfg(items, (uint64_t)n * width * height);
     Plan pl;
     make_plan(pl, n_scenes, n, width, height, list_entries, items, cfg);
 
@@ -1007,7 +1008,7 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
         lc = from_config(*cfg);
     else
         if (!lookup_tuned(make_key(scenes, n_scenes, n_cap, width, height, ids != nullptr), lc))
-            lc = default_launch_cfg(items, width, height);
+            lc = default_launch_cfg(items, (uint64_t)n_cap * width * height);
     hsr_batch *b = new (std::nothrow) hsr_batch();
     if (!b) return HSR_ERR_OOM;
     cudaGetDevice(&b->device);
@@ -1286,7 +1287,7 @@ int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     // coordinate descent over the launch parameters from the default, two sweeps
     uint64_t max_g = 0;
     for (uint32_t i = 0; i < n_scenes; i++) max_g = std::max<uint64_t>(max_g, scenes[i]->dev.n_groups);
-    LaunchCfg cur = default_launch_cfg((uint64_t)n * max_g, width, height);
+    LaunchCfg cur = default_launch_cfg((uint64_t)n * max_g, (uint64_t)n * width * height);
     float cur_ms = 0;
     status = measure(cur, cur_ms);
     const uint32_t small_v[] = {8, 16, 24, 32};

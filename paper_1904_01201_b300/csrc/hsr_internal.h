@@ -233,22 +233,6 @@ struct LaunchCfg {
     float phase_r[2] = {4.0f, 10.0f};
 };
 
-// The configuration used when none was tuned for a call's signature: the
-// defaults, with a single occlusion phase for small calls (under 16k
-// (view, group) items, where the extra kernels of a phase cost more than the
-// culling saves), and the large-triangle bins reserved for triangles above
-// 32 candidate pixels up to 256^2 images, above 1/1024 of the image beyond
-// (the values the autotuner picks on the house and large workloads: at 512^2
-// the warp rasterises triangles of up to 256 candidates itself faster than
-// the separate pass).
-inline LaunchCfg default_launch_cfg(uint64_t items, uint32_t width, uint32_t height)
-{
-    LaunchCfg c;
-    if (items < 16384) c.n_phases = 1;
-    const uint64_t px = (uint64_t)width * height;
-    c.bin_px = px <= 65536u ? 32u : (uint32_t)std::min<uint64_t>(px / 1024u, 1u << 20);
-    return c;
-}
 
 // Sets kernel attributes for the current device (call before stream capture).
 cudaError_t prepare_kernels();

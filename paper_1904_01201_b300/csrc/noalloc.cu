@@ -33,6 +33,7 @@
 
 #include "../../include/hsr.h"
 #include "hsr_internal.h"
+#include "launch_defaults.h"
 
 namespace hsr {
 
@@ -159,7 +160,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = host_far_threshold(intr->zfar);
     p.inv_far = (float)(1.0 / (double)intr->zfar);
-    const LaunchCfg cfg = default_launch_cfg(items, width, height);
+    const LaunchCfg cfg = default_launch_cfg(items, (uint64_t)n * width * height);
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;
     p.hiz = reinterpret_cast<uint32_t *>(d + off_z + zbytes + lbytes);
