@@ -117,7 +117,7 @@ __device__ __forceinline__ void small_setup(const Tri2D &t, uint32_t id, int x0,
 {
     f.mask = small_coverage(t, x0, x1, y0, y1);
     if (!f.mask) return;
-    depth_plane(t, f.pa, f.pb);
+    depth_plane_narrow(t, f.pa, f.pb);
     f.q0 = t.q0;
     f.qlo = tri_qlo(t);
     f.qhi = tri_qhi(t);
@@ -189,7 +189,7 @@ __device__ __forceinline__ void raster_small(const Tri2D &t, uint32_t id, int x0
     uint32_t mask = small_coverage(t, x0, x1, y0, y1);
     if (!mask) return;
     float pa, pb;
-    depth_plane(t, pa, pb);
+    depth_plane_narrow(t, pa, pb);
     const float qlo = tri_qlo(t), qhi = tri_qhi(t);
     const int w = x1 - x0 + 1;
     // covered samples row by row (bit k of the mask is row k / w, column k % w)

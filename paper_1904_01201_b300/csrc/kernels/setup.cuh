@@ -116,6 +116,17 @@ __device__ __forceinline__ void depth_plane(const Tri2D &t, float &pa, float &pb
     pb = __fdiv_rn(__fmaf_rn(dq2, __int2float_rn(t.X1 - t.X0), -__fmul_rn(dq1, __int2float_rn(t.X2 - t.X0))), fA);
 }
 
+// depth_plane for a triangle whose bounding box is under 2^15 sub-pixels per
+// axis: each product of A is below 2^30 in magnitude, so 0 < A < 2^31 and the
+// int32 conversion gives the same rounded float as i64_to_float_rn.
+__device__ __forceinline__ void depth_plane_narrow(const Tri2D &t, float &pa, float &pb)
+{
+    const float fA = __int2float_rn((int)t.A);
+    const float dq1 = __fsub_rn(t.q1, t.q0), dq2 = __fsub_rn(t.q2, t.q0);
+    pa = __fdiv_rn(__fmaf_rn(dq1, __int2float_rn(t.Y2 - t.Y0), -__fmul_rn(dq2, __int2float_rn(t.Y1 - t.Y0))), fA);
+    pb = __fdiv_rn(__fmaf_rn(dq2, __int2float_rn(t.X1 - t.X0), -__fmul_rn(dq1, __int2float_rn(t.X2 - t.X0))), fA);
+}
+
 // q at a sample, from its offset (exact integers) to vertex 0, clamped to the
 // range [qlo, qhi] of the triangle's vertex values (interior points lie
 // between the vertices' depths; the clamp keeps that true under rounding).
