@@ -362,12 +362,11 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
 }
 
 // --------------------------------------------------------------------- raster
-// Per-warp staging buffer of one meshlet: its view's matrix, its vertex
-// block and its triangle block, the latter widened to start on a 16-byte
-// boundary (the first triangle sits at tri[first_tri & 1]). Filled by the
-// bulk-copy engine while the warp works on the previous meshlet.
+// Per-warp staging buffer of one meshlet: its vertex block and its triangle
+// block, the latter widened to start on a 16-byte boundary (the first
+// triangle sits at tri[first_tri & 1]). Filled by the bulk-copy engine while
+// the warp works on the previous meshlet.
 struct alignas(16) MeshletStage {
-    float M[12];
     float4 vert[kMeshletVerts];
     uint2 tri[kMeshletTris + 2];
 };
@@ -455,7 +454,11 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
                                                 uint32_t *bign, int lane, uint32_t view, uint32_t phase)
 {
     const float zn = p.znear, zf = p.zfar;
-    const float *M = st.M;
+    // the view matrix from the view record (the same 48 bytes for every
+    // lane: one broadcast load each, served by L1 after the first pair)
+    float M[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) M[i] = __ldg(p.views[view].M + i);
 
     // K1: transform + snap this meshlet's vertices
     for (uint32_t v = lane; v < nv; v += 32) {
@@ -666,8 +669,8 @@ __global__ void __launch_bounds__(256) occl_kernel(const Params p, uint32_t phas
 // Scene geometry pointers of the first kSlotCache slots, cached per CTA.
 constexpr uint32_t kSlotCache = 32;
 
-// Global addresses of a pair's view matrix and geometry, and the bulk copies
-// that stage them (issued by one lane).
+// The bulk copies that stage a pair's vertex and triangle blocks (issued by
+// one lane).
 __device__ __forceinline__ void stage_meshlet(MeshletStage &st, uint64_t *bar, const Params &p, const uint4 &e,
                                               const float4 *mvert, const uint2 *mtri)
 {
@@ -675,8 +678,7 @@ __device__ __forceinline__ void stage_meshlet(MeshletStage &st, uint64_t *bar, c
     const uint32_t t0 = e.w & ~1u;                              // 16-byte aligned start
     const uint32_t tn = (e.w + nt - t0 + 1u) & ~1u;             // even count covering the range
     fence_proxy_async();
-    mbar_arrive_expect_tx(bar, 48u + nv * 16u + tn * 8u + p.fault_tx);
-    bulk_g2s(st.M, p.views[pair_view(e)].M, 48u, bar);
+    mbar_arrive_expect_tx(bar, nv * 16u + tn * 8u + p.fault_tx);
     bulk_g2s(st.vert, mvert + e.z, nv * 16u, bar);
     bulk_g2s(st.tri, mtri + t0, tn * 8u, bar);
 }
