@@ -907,6 +907,38 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         }
         std::vector<float4> vert(n_verts);
         for (size_t i = 0; i < n_verts; i++) vert[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
+        // per-triangle shading records (one 64-byte line: the shading pass
+        // reaches a pixel's vertices and attributes with one dependent load)
+        std::vector<float4> srec(4 * (size_t)n_tris);
+        {
+            const bool textured = uv && atlas, coloured = !textured && vert_rgb;
+            auto bits = [](uint32_t u) {
+                float f;
+                std::memcpy(&f, &u, 4);
+                return f;
+            };
+            auto rgb = [&](uint32_t i) {
+                return bits((uint32_t)vert_rgb[3 * (size_t)i] | ((uint32_t)vert_rgb[3 * (size_t)i + 1] << 8) |
+                            ((uint32_t)vert_rgb[3 * (size_t)i + 2] << 16));
+            };
+            for (size_t t = 0; t < n_tris; t++) {
+                const uint32_t a = tri[t].x, b = tri[t].y, c = tri[t].z;
+                const float *pa = xyz + 3 * (size_t)a, *pb = xyz + 3 * (size_t)b, *pc = xyz + 3 * (size_t)c;
+                float4 *r = &srec[4 * t];
+                r[0] = make_float4(pa[0], pa[1], pa[2], pb[0]);
+                r[1] = make_float4(pb[1], pb[2], pc[0], pc[1]);
+                if (textured) {
+                    r[2] = make_float4(pc[2], uv[2 * (size_t)a], uv[2 * (size_t)a + 1], uv[2 * (size_t)b]);
+                    r[3] = make_float4(uv[2 * (size_t)b + 1], uv[2 * (size_t)c], uv[2 * (size_t)c + 1], bits(tri[t].w));
+                } else if (coloured) {
+                    r[2] = make_float4(pc[2], rgb(a), rgb(b), rgb(c));
+                    r[3] = make_float4(0.f, 0.f, 0.f, bits(tri[t].w));
+                } else {
+                    r[2] = make_float4(pc[2], 0.f, 0.f, 0.f);
+                    r[3] = make_float4(0.f, 0.f, 0.f, bits(tri[t].w));
+                }
+            }
+        }
 
         cudaError_t e = cudaSuccess;
         SceneDev &d = s->dev;
@@ -927,6 +959,9 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         d.coord_max = cmax;
         if ((e = upload(s, tri.data(), tri.size(), &dt)) != cudaSuccess) throw e;
         if ((e = upload(s, vert.data(), vert.size(), &dv)) != cudaSuccess) throw e;
+        const float4 *dsr;
+        if ((e = upload(s, srec.data(), srec.size(), &dsr)) != cudaSuccess) throw e;
+        d.srec = dsr;
         d.meshlets = dm;
         d.groups = dg;
         d.mvert = dmv;

@@ -41,6 +41,10 @@ struct SceneDev {
     const uint2 *mtri;         // x: local indices (8 bits each, canonical order), y: triangle index
     const uint4 *tri;          // canonical (i0, i1, i2) + output id, per triangle index
     const float4 *vert;        // x, y, z, 0 per caller vertex
+    // per triangle, one 64-byte shading record (4 float4), vertices in canonical
+    // order: p0.xyz p1.x | p1.yz p2.xy | p2.z a0 a1 a2 | a3 a4 a5 bits(id), where
+    // a = uv0.uv uv1.uv uv2.uv (textured), or bits(rgb0, rgb1, rgb2), 0, 0, 0
+    const float4 *srec;
     // per meshlet, two records: (unit normal n, plane offset w) of its triangles'
     // common plane, and (minimum triangle area, longest edge, max |n.x - w| over
     // its vertices, max |n_t - n| over its triangles); longest edge < 0 when the

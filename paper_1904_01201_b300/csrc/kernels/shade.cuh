@@ -198,7 +198,7 @@ struct ShadeTri {
     bool narrow = false;                // bounding box under 2^15 sub-pixels per axis
     Tri2D t;                            // oriented (unclipped case; t.A is not set)
     float a[3][NA > 0 ? NA : 1];        // attributes in oriented order
-    uint4 T;
+    uint32_t id;                        // output id
 };
 
 template <int NA>
@@ -206,9 +206,30 @@ __device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev
                                                 const Params &p, uint32_t tri)
 {
     st.tri = tri;
-    st.T = __ldg(S.tri + tri);
+    // the triangle's shading record: one 64-byte line
+    const float4 *rec = S.srec + 4 * (size_t)tri;
+    const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2), r3 = __ldg(rec + 3);
+    st.id = __float_as_uint(r3.w);
+    const float px[3] = {r0.x, r0.w, r1.z}, py[3] = {r0.y, r1.x, r1.w}, pz[3] = {r0.z, r1.y, r2.x};
     CVert<NA> v[3];
-    load_tri<NA>(S, M, st.T, v);
+#pragma unroll
+    for (int k = 0; k < 3; k++) eye_transform(M, px[k], py[k], pz[k], v[k].xe, v[k].ye, v[k].d);
+    if (NA == 2) {
+        const float u[3] = {r2.y, r2.w, r3.y}, w[3] = {r2.z, r3.x, r3.z};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            v[k].a[0] = u[k];
+            v[k].a[NA > 1 ? 1 : 0] = w[k];
+        }
+    } else if (NA == 3) {
+        const uint32_t c[3] = {__float_as_uint(r2.y), __float_as_uint(r2.z), __float_as_uint(r2.w)};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            v[k].a[0] = (float)(c[k] & 255u);
+            v[k].a[NA > 1 ? 1 : 0] = (float)((c[k] >> 8) & 255u);
+            v[k].a[NA > 2 ? 2 : 0] = (float)((c[k] >> 16) & 255u);
+        }
+    }
     st.clipped = !(v[0].d >= p.znear && v[1].d >= p.znear && v[2].d >= p.znear);
     if (st.clipped) return;
     int X[3], Y[3];
@@ -328,7 +349,7 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
         return;
     }
     if (tri != st.tri) build_shade_tri<NA>(st, S, M, p, tri);
-    id = st.T.w;
+    id = st.id;
     const int Px = 256 * px + 128, Py = 256 * py + 128;
     float a[3] = {0.f, 0.f, 0.f};
     float lambda = 0.0f;
@@ -338,7 +359,8 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
             if (S.sample_mode == HSR_SAMPLE_TRILINEAR) lambda = lod_lambda(S, st.t, Px, Py, st.a[0], st.a[1], st.a[2]);
         rgb = shade_colour<NA>(S, a, lambda);
     } else {
-        rgb = shade_clipped<NA>(S, M, p, st.T, Px, Py, qk, a, lambda) ? shade_colour<NA>(S, a, lambda) : 0u;
+        rgb = shade_clipped<NA>(S, M, p, __ldg(S.tri + tri), Px, Py, qk, a, lambda) ? shade_colour<NA>(S, a, lambda)
+                                                                                  : 0u;
     }
 }
 
