@@ -182,7 +182,7 @@ struct Params {
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels
-    uint32_t bin_px;           // tile bins for triangles with more candidate pixels than this; per-warp queue between
+    uint32_t bin_px;           // bins for triangles with more candidate pixels than this; per-warp queue between
     uint32_t chunk;            // consecutive visible pairs a raster warp takes per step (<= 32)
     // occlusion phases: a visible meshlet at distance r from the camera goes
     // to phase (r > phase_r[0]) + (r > phase_r[1]), limited to n_phases - 1;

@@ -23,13 +23,13 @@
 
 namespace hsr {
 
-// A large triangle for the warp-cooperative and tile-bin paths (64 bytes).
+// A large triangle for the warp queue and the binned pass (64 bytes).
 struct alignas(16) BigTri {
     int X0, Y0, X1, Y1, X2, Y2;
     float pa, pb, q0, qlo, qhi;
     uint32_t id;
     unsigned short x0, y0, x1, y1;      // candidate pixel range, clipped to the image
-    uint32_t view;                       // z-buffer the triangle belongs to (tile-bin path)
+    uint32_t view;                       // z-buffer the triangle belongs to (binned pass)
     uint32_t pad_;
 };
 
@@ -219,7 +219,7 @@ __device__ __forceinline__ float i64_to_float_rel(long long v)
     return v < 0 ? -f : f;
 }
 
-// Rows of a large triangle per work item of the tile-bin path: about 1024
+// Rows of a large triangle per work item of the binned pass: about 1024
 // candidate pixels, at most one row per lane.
 __device__ __forceinline__ int big_rows_per_item(int x0, int x1)
 {

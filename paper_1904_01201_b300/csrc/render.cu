@@ -1,23 +1,29 @@
 // Render kernels.
 //
-// cull_kernel (K3): one warp per (view, meshlet group) work item; the group
-//   and then its meshlets are tested against the view frustum and the visible
-//   (view, meshlet) pairs are appended to a compact list (bin.cuh).
-// raster_kernel: one launch per occlusion phase; warps take equal shares of
-//   the visible pairs (grid-stride, `chunk` consecutive pairs at a time), keep
-//   the pairs of their phase, skip meshlets the hierarchical z-buffer proves
-//   hidden (phases after the first), and for each remaining pair:
+// cull_kernel (K3): group-major frustum and whole-meshlet back-face culling;
+//   a warp item is (scene, meshlet group, block of views): the group box is
+//   tested in all views of the block at once, then each meshlet in the views
+//   that see the group; visible (view, meshlet) pairs go to per-phase lists
+//   (distance bands) as self-contained entries (bin.cuh). The kernel also
+//   clears the active views' z-buffers. cull_kernel_vg is the (view, group)
+//   form for calls with many scene slots.
+// hiz_kernel, hiz_pyramid_kernel, occl_kernel: before every phase after the
+//   first, the farthest stored key of every 8x8 tile and its pyramid, and the
+//   conservative occlusion test that keeps the pairs not proven hidden.
+// raster_kernel: one launch per occlusion phase, a persistent grid whose
+//   warps claim chunks of pairs from a shared cursor and stage each meshlet's
+//   geometry by bulk copies one meshlet ahead; per pair:
 //   K1 — transform + snap the meshlet's vertices into a per-warp
 //        shared-memory cache (transform.cuh)
 //   K2 — per-lane triangle reject / near clip / cull / depth plane (setup.cuh)
-//   K4 — per-thread raster of small triangles, warp-cooperative raster of the
-//        rest, into the view's 64-bit z-buffer (raster.cuh)
-// hiz_kernel: between phases, the farthest stored key of every 8x8 tile.
+//   K4 — small triangles' covered samples spread over the warp, larger ones
+//        rasterised by the warp row by row or binned for big_raster_kernel,
+//        into the view's 64-bit z-buffer (raster.cuh)
 // shade_kernel (K5): one CTA row per view; each thread resolves kShadePx
 //   consecutive pixels of a row (shade.cuh) and writes RGB / depth / id with
 //   vector stores when the row layout allows it.
-// Work items are ordered scene-major then view-major, so a scene's geometry
-// stays hot in L2 while its views are in flight.
+// Work items are ordered scene-major, so a scene's geometry stays hot in L2
+// while its views are in flight.
 #include <algorithm>
 
 #include <cuda_runtime.h>
