@@ -891,7 +891,8 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
             if (vec) {
 #pragma unroll
                 for (int k = 0; k + 1 < K; k += 2) {
-                    const ulonglong2 kk = *reinterpret_cast<const ulonglong2 *>(zb + pi + k);
+                    // the keys are dead after shading: read them evict-first
+                    const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2 *>(zb + pi + k));
                     key[k] = kk.x;
                     key[k + 1] = kk.y;
                 }
