@@ -1,0 +1,110 @@
+"""The benchmark workloads at their full sizes through the persistent batch
+(the form bench.py times), with sampled views checked against the oracle
+element by element, and the size limits: a 4096 x 4096 view and a call with
+more views than one grid dimension holds. Ids and depth bit-exact, RGB
+within 1/255."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1904_01201_b300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_1904_01201_b300 import hsr  # noqa: E402
+from paper_1904_01201_b300 import workloads as wl  # noqa: E402
+from paper_1904_01201_b300.workloads import Intrinsics  # noqa: E402
+
+import bench  # noqa: E402
+
+BG = 0xFFFFFFFF
+
+
+def _host(out, sel):
+    torch.cuda.synchronize()
+    r = {"rgb": out["rgb"][sel].cpu().numpy(), "depth": out["depth"][sel].cpu().numpy()}
+    if out.get("ids") is not None:
+        r["ids"] = hsr.ids_u32(out["ids"][sel])
+    return r
+
+
+def _check(g, o, what):
+    if "ids" in g:
+        bad = g["ids"] != o["ids"]
+        assert not bad.any(), f"{what}: {int(bad.sum())} id mismatches"
+    assert np.array_equal(g["depth"].view(np.uint32), o["depth"].view(np.uint32)), f"{what}: depth"
+    d = np.abs(g["rgb"].astype(np.int16) - o["rgb"].astype(np.int16))
+    assert d.max() <= 1, f"{what}: rgb {d.max()}"
+
+
+# (small_px, bin_px, chunk, ctas, phases, radii): the untuned default, and the
+# configuration the autotuner picks for these workloads
+CFGS = [None, (32, 256, 4, 3, 3, (2.0, 5.0))]
+
+
+@pytest.mark.parametrize("cfg", CFGS)
+def test_large_workload_full_size_sampled(oracle_mod, cfg):
+    """2M-triangle house, 8192^2 atlas, 256 views at 512^2 with semantic ids,
+    one batch replay; views 0, 128 and 255 against the oracle."""
+    wk = bench.make_workload("large")
+    sc = wk["scenes"][0]
+    h = hsr.SceneHandle(sc)
+    n, W, H = len(wk["soa"]), wk["W"], wk["H"]
+    b = hsr.Batch([h], n, wk["intr"], W, H, ids=True, cfg=None if cfg is None else hsr.hsr_config(*cfg))
+    b.render(wk["poses"])
+    for i in (0, 128, 255):
+        o = oracle_mod.render(sc, wk["poses"][i:i + 1], wk["intr"], W, H, ids=True)
+        _check(_host(b.out, slice(i, i + 1)), o, f"large view {i}")
+    assert (hsr.ids_u32(b.out["ids"][:8]) != BG).mean() > 0.9
+    b.close()
+    h.close()
+
+
+def test_batching_workload_full_size_sampled(oracle_mod):
+    """8 resident scenes (0.2M-2M triangles), 1,024 agents split unevenly, 128^2,
+    one batch replay; the first agent of every scene against the oracle."""
+    wk = bench.make_workload("batching")
+    hs = [hsr.SceneHandle(s) for s in wk["scenes"]]
+    n, W, H = len(wk["soa"]), wk["W"], wk["H"]
+    b = hsr.Batch(hs, n, wk["intr"], W, H, ids=False)
+    b.render(wk["poses"], wk["soa"])
+    for s in range(len(hs)):
+        i = int(np.nonzero(wk["soa"] == s)[0][0])
+        o = oracle_mod.render(wk["scenes"][s], wk["poses"][i:i + 1], wk["intr"], W, H)
+        _check(_host(b.out, slice(i, i + 1)), o, f"batching scene {s} agent {i}")
+    b.close()
+    for h in hs:
+        h.close()
+
+
+def test_maximum_resolution_4096(oracle_mod):
+    """A 4096 x 4096 view of the small room (triangles up to millions of
+    candidate pixels: the binned large-triangle pass at its largest)."""
+    sc = wl.make_room(0)
+    poses = wl.random_poses(sc, 2, 7)
+    intr = wl.pinhole_90(4096, 4096)
+    out = hsr.render(hsr.SceneHandle(sc), poses, intr, 4096, 4096)
+    for i in range(2):
+        o = oracle_mod.render(sc, poses[i:i + 1], intr, 4096, 4096)
+        _check(_host(out, slice(i, i + 1)), o, f"4096^2 view {i}")
+
+
+def test_more_views_than_a_grid_dimension(oracle_mod):
+    """70,000 views in one call (the shading grid's second dimension holds
+    65,535): sampled views on both sides of the split against the oracle."""
+    sc = wl.make_room(1, 3000)
+    n = 70_000
+    poses = wl.random_poses(sc, n, 9)
+    intr = Intrinsics(4.0, 4.0, 4.0, 4.0, 0.01, 10.0)
+    h = hsr.SceneHandle(sc)
+    out = hsr.render(h, poses, intr, 8, 8)
+    for i in (0, 65_534, 65_535, 65_536, n - 1):
+        o = oracle_mod.render(sc, poses[i:i + 1], intr, 8, 8)
+        _check(_host(out, slice(i, i + 1)), o, f"view {i}")
+    ids = hsr.ids_u32(out["ids"])
+    assert (ids[65_535:] != BG).mean() > 0.9
+    h.close()
