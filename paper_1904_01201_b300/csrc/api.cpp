@@ -28,6 +28,8 @@ struct hsr_scene {
     SceneDev dev{};
     SceneDev *dev_desc = nullptr;      // device copy of `dev`
     std::vector<void *> allocs;
+    cudaArray_t atlas_array = nullptr; // the atlas as a texture (2D-local layout) for bilinear gathers
+    cudaTextureObject_t atlas_tex = 0;
     hsr_scene_info info{};
 };
 
@@ -61,6 +63,8 @@ void free_scene(hsr_scene *s)
     cudaSetDevice(s->device);
     cudaDeviceSynchronize();
     for (void *p : s->allocs) cudaFree(p);
+    if (s->atlas_tex) cudaDestroyTextureObject(s->atlas_tex);
+    if (s->atlas_array) cudaFreeArray(s->atlas_array);
     cudaSetDevice(prev);
     delete s;
 }
@@ -985,6 +989,33 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
             d.atlas_w = atlas_w;
             d.atlas_h = atlas_h;
             d.color_mode = kColorTexture;
+            // the same texels in a texture (the driver's 2D-local layout): the
+            // bilinear footprint comes back from one gather per channel; a
+            // scene whose atlas does not fit a texture samples the linear copy
+            d.atlas_tex = 0;
+            const cudaChannelFormatDesc cd = cudaCreateChannelDesc<uchar4>();
+            if (cudaMallocArray(&s->atlas_array, &cd, atlas_w, atlas_h) == cudaSuccess) {
+                cudaResourceDesc rd{};
+                rd.resType = cudaResourceTypeArray;
+                rd.res.array.array = s->atlas_array;
+                cudaTextureDesc td{};
+                td.addressMode[0] = cudaAddressModeClamp;
+                td.addressMode[1] = cudaAddressModeClamp;
+                td.filterMode = cudaFilterModePoint;
+                td.readMode = cudaReadModeElementType;
+                td.normalizedCoords = 0;
+                if (cudaMemcpy2DToArray(s->atlas_array, 0, 0, atlas, (size_t)atlas_w * 4, (size_t)atlas_w * 4, atlas_h,
+                                        cudaMemcpyHostToDevice) == cudaSuccess &&
+                    cudaCreateTextureObject(&s->atlas_tex, &rd, &td, nullptr) == cudaSuccess) {
+                    d.atlas_tex = s->atlas_tex;
+                    s->info.device_bytes += (uint64_t)atlas_w * atlas_h * 4;
+                } else {
+                    s->atlas_tex = 0;
+                }
+            } else {
+                s->atlas_array = nullptr;
+            }
+            (void)cudaGetLastError();   // a failed texture leaves no sticky error: the linear path serves
         } else if (vert_rgb) {
             std::vector<uint32_t> c(n_verts);
             for (size_t i = 0; i < n_verts; i++)

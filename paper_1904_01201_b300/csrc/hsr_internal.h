@@ -54,6 +54,7 @@ struct SceneDev {
     const float2 *uv;          // per vertex, or null
     const uint32_t *vrgb;      // r | g << 8 | b << 16 per vertex, or null
     const uint32_t *atlas;     // RGBA8 texels, row-major, or null
+    unsigned long long atlas_tex;  // the atlas as a texture object (uchar4, clamp, unnormalised), or 0
     uint32_t atlas_w, atlas_h;
     uint32_t n_groups, n_meshlets, n_tris, n_verts;
     int color_mode;

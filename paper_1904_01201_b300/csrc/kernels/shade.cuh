@@ -37,13 +37,30 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     const float fs = floorf(s), ft = floorf(t);
     const float ax = __fsub_rn(s, fs), ay = __fsub_rn(t, ft);
     const int ix = (int)fs, iy = (int)ft;
+    const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
+    uint32_t out = 0;
+    if (S.atlas_tex) {
+        // one gather per channel returns that channel of the footprint
+        // (ix, iy) .. (ix + 1, iy + 1), clamped to the edge: at unnormalised
+        // (ix + 1, iy + 1) the footprint's corner is floor(ix + 1/2) = ix,
+        // half a texel from any rounding boundary; the components come as
+        // x (ix, iy + 1), y (ix + 1, iy + 1), z (ix + 1, iy), w (ix, iy)
+        const float u = (float)(ix + 1), w = (float)(iy + 1);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const uchar4 g = tex2Dgather<uchar4>((cudaTextureObject_t)S.atlas_tex, u, w, c);
+            const float v00 = (float)g.w, v10 = (float)g.z, v01 = (float)g.x, v11 = (float)g.y;
+            const float top = __fmaf_rn(ax, v10, __fmul_rn(gx, v00));
+            const float bot = __fmaf_rn(ax, v11, __fmul_rn(gx, v01));
+            out |= round_channel(__fmaf_rn(ay, bot, __fmul_rn(gy, top))) << (8 * c);
+        }
+        return out;
+    }
     const int W = (int)S.atlas_w, H = (int)S.atlas_h;
     const int x0 = min(max(ix, 0), W - 1), x1 = min(max(ix + 1, 0), W - 1);
     const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
     const uint32_t c00 = __ldg(S.atlas + (size_t)y0 * W + x0), c10 = __ldg(S.atlas + (size_t)y0 * W + x1);
     const uint32_t c01 = __ldg(S.atlas + (size_t)y1 * W + x0), c11 = __ldg(S.atlas + (size_t)y1 * W + x1);
-    const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
-    uint32_t out = 0;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const float top = __fmaf_rn(ax, texel_channel(c10, c), __fmul_rn(gx, texel_channel(c00, c)));
