@@ -405,8 +405,11 @@ HSR_API int hsr_config_default(hsr_config *cfg);
  * hsr_batch_create does) and timed with CUDA events on the caller's stream
  * around its launch, after a 256 MiB device write that evicts L2 (median of
  * `reps` timed launches after one warm-up; the 256 MiB is allocated for the
- * call), by coordinate descent from the default for this call's size (one
- * occlusion phase below 16,384 culling items, two above); stores the fastest configuration for
+ * call), by two sweeps of coordinate descent (small-triangle bound, bin
+ * threshold, chunk, occlusion phases together with their band radii, CTAs per
+ * SM) from the default for this call's size (one occlusion phase below 16,384
+ * culling items, two above; bins above 32 candidates up to 2^24 pixels over
+ * all views, above 256 beyond); stores the fastest configuration for
  * this workload signature (scene set, n, width, height, ids present) so that
  * later hsr_render / hsr_render_batch calls with the same signature use it,
  * and returns it in *best (and its time in *best_ms). Synchronises the stream.

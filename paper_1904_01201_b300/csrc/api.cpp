@@ -1359,20 +1359,27 @@ int hsr_autotune(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     const uint32_t small_v[] = {8, 16, 24, 32};
     const uint32_t bin_v[] = {16, 32, 64, 128, 256, 512, 4096};
     const uint32_t chunk_v[] = {1, 2, 4, 8, 16, 32};
-    const uint32_t phase_v[] = {1, 2, 3};
+    // occlusion phases and their radii are searched together: one phase, or
+    // two or three with each pair of band radii (the best radii depend on
+    // the number of phases)
     const float radius_v[][2] = {{2.f, 5.f}, {3.f, 7.f}, {4.f, 10.f}, {6.f, 14.f}};
     const uint32_t cta_v[] = {2, 3};
     for (int sweep = 0; sweep < 2 && status == HSR_OK; sweep++) {
-        for (int param = 0; param < 6 && status == HSR_OK; param++) {
-            const int nv = param == 0 ? 4 : param == 1 ? 7 : param == 2 ? 5 : param == 3 ? 3 : param == 4 ? 4 : 2;
+        for (int param = 0; param < 5 && status == HSR_OK; param++) {
+            const int nv = param == 0 ? 4 : param == 1 ? 7 : param == 2 ? 6 : param == 3 ? 9 : 2;
             for (int k = 0; k < nv && status == HSR_OK; k++) {
                 LaunchCfg c = cur;
                 switch (param) {
                     case 0: c.small_px = small_v[k]; break;
                     case 1: c.bin_px = bin_v[k]; break;
                     case 2: c.chunk = chunk_v[k]; break;
-                    case 3: c.n_phases = phase_v[k]; break;
-                    case 4: c.phase_r[0] = radius_v[k][0]; c.phase_r[1] = radius_v[k][1]; break;
+                    case 3:
+                        c.n_phases = k == 0 ? 1u : (k <= 4 ? 2u : 3u);
+                        if (k > 0) {
+                            c.phase_r[0] = radius_v[(k - 1) % 4][0];
+                            c.phase_r[1] = radius_v[(k - 1) % 4][1];
+                        }
+                        break;
                     default: c.raster_ctas_per_sm = cta_v[k]; break;
                 }
                 c.bin_px = std::max(c.bin_px, c.small_px);
