@@ -130,6 +130,28 @@ __device__ __forceinline__ void small_setup(const Tri2D &t, uint32_t id, int x0,
     f.id = id;
 }
 
+// Covered samples of a lane's own small triangle, merged by that lane: the
+// same candidate numbering, plane evaluation, far test and key as the warp
+// pass below (used for triangles with at most kDirectFrags covered samples,
+// the common case, which the warp pass would otherwise spread one by one).
+constexpr int kDirectFrags = 4;
+__device__ __forceinline__ void raster_fragments_lane(const SmallFrag &f, float q_far, unsigned long long *zbuf,
+                                                      int W)
+{
+    uint32_t m = f.mask;
+#pragma unroll
+    for (int i = 0; i < kDirectFrags; i++) {
+        if (!m) break;
+        const int b = __ffs(m) - 1;
+        m &= m - 1u;
+        const int row = (int)(((float)b + 0.5f) * f.rw);
+        const int px = f.x0 + (b - row * f.w), py = f.y0 + row;
+        const float q = plane_q(f.pa, f.pb, f.q0, 256 * px + 128 - f.X0, 256 * py + 128 - f.Y0, f.qlo, f.qhi);
+        if (!(q >= q_far)) continue;
+        zmin(zbuf + (size_t)py * W + px, depth_key(q, f.id));
+    }
+}
+
 // Fragments of the small triangles of all lanes, spread over the warp (every
 // lane calls it): covered samples are numbered consecutively across lanes
 // (warp prefix sum of the mask popcounts), lane i takes fragment base + i,

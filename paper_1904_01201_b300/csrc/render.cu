@@ -520,6 +520,12 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
         }
     }
     __syncwarp();
+    // small triangles with few covered samples merge them in their own lane;
+    // the warp spreads the fragments of the others
+    if (sf.mask && __popc(sf.mask) <= kDirectFrags) {
+        raster_fragments_lane(sf, p.q_far, zbuf, (int)p.width);
+        sf.mask = 0u;
+    }
     raster_fragments_warp(sf, lane, p.q_far, zbuf, (int)p.width);
     const uint32_t nb = *bign;
     for (uint32_t r = 0; r < nb; r++) raster_big_warp(bigq[r], lane, p.q_far, zbuf, (int)p.width);
