@@ -262,11 +262,13 @@ __device__ __forceinline__ int big_rows_per_item(int x0, int x1)
 // decides the whole row.
 //  * narrow triangles (bounding box under 2^15 sub-pixels per axis): every
 //    edge value at a candidate fits in int32 (as for small triangles); the
-//    quotient is taken in fp32 with relative error below 2^-22, under 2^-7
-//    of a column where it can fall inside the rectangle (under 2^15 columns
-//    from its start), and the bound is rounded with a 1/64-column allowance;
+//    quotient is taken in fp32 with relative error below 2^-21 (a correctly
+//    rounded conversion and product, and a reciprocal within 2 ulp), under
+//    2^-6 of a column where it can fall inside the rectangle (under 2^15
+//    columns from its start), and the bound is rounded with a 1/32-column
+//    allowance;
 //  * others: int64 edge values, the quotient from a conversion with relative
-//    error below 2^-20 (under 16 sub-pixels wherever it falls inside the
+//    error below 2^-19 (under 32 sub-pixels wherever it falls inside the
 //    image), widened by a whole column on each side.
 __device__ __forceinline__ void raster_rows_warp(const BigTri &t, int r0, int r1, int lane, float q_far,
                                                  unsigned long long *zbuf, int W)
@@ -284,7 +286,7 @@ __device__ __forceinline__ void raster_rows_warp(const BigTri &t, int r0, int r1
     float rdy[3];
 #pragma unroll
     for (int k = 0; k < 3; k++)
-        rdy[k] = dy[k] != 0 ? __frcp_rn(__int2float_rn(narrow ? 256 * dy[k] : dy[k])) : 0.f;
+        rdy[k] = dy[k] != 0 ? __fdividef(1.0f, __int2float_rn(narrow ? 256 * dy[k] : dy[k])) : 0.f;
     for (int rb = r0; rb <= r1; rb += 32) {
         const int py = rb + lane;
         int xa = 0, len = 0;
@@ -301,9 +303,9 @@ __device__ __forceinline__ void raster_rows_warp(const BigTri &t, int r0, int r1
                     } else {
                         const float lim = __fmul_rn(__int2float_rn(E), rdy[k]);
                         if (dy[k] > 0)
-                            hi = fminf(hi, floorf(lim + 0.015625f));
+                            hi = fminf(hi, floorf(lim + 0.03125f));
                         else
-                            lo = fmaxf(lo, ceilf(lim - 0.015625f));
+                            lo = fmaxf(lo, ceilf(lim - 0.03125f));
                     }
                 }
             } else {
