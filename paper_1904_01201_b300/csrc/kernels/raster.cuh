@@ -126,7 +126,7 @@ __device__ __forceinline__ void small_setup(const Tri2D &t, uint32_t id, int x0,
     f.x0 = x0;
     f.y0 = y0;
     f.w = x1 - x0 + 1;
-    f.rw = __frcp_rn((float)f.w);
+    f.rw = __fdividef(1.0f, (float)f.w);       // within 2 ulp: enough for the row (see below)
     f.id = id;
 }
 
@@ -159,8 +159,9 @@ __device__ __forceinline__ void raster_fragments_lane(const SmallFrag &f, float 
 // bit (its k-th covered bit), and merges the fragment exactly as a per-lane
 // loop would: same plane evaluation, same far test, same key. Row and column
 // of candidate bit b < 32 of a rectangle w <= 32 wide: row = floor((b + 1/2)
-// / w) computed as (b + 0.5) * (1/w) in fp32, exact because (b + 1/2) / w is
-// at least 1/(2w) >= 1/64 away from an integer.
+// / w) computed as (b + 0.5) * rw in fp32 with rw within 2 ulp of 1/w: the
+// product is within 2^-17 of (b + 1/2) / w, which is at least 1/(2w) >= 1/64
+// away from an integer, so the floor is exact.
 __device__ __forceinline__ void raster_fragments_warp(const SmallFrag &f, int lane, float q_far,
                                                       unsigned long long *zbuf, int W)
 {
