@@ -1119,9 +1119,11 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
     }
     // culling (and the z-buffer clear it performs) runs for every call
     // grid from the work: the z-buffer clear (16 bytes per thread, 8 stores
-    // each) and the (view, group) items, capped at 8 CTAs per SM
+    // each) and the (view, group) items (one per warp: an item is a chain of
+    // dependent record loads, so small calls want many warps in flight),
+    // capped at 8 CTAs per SM
     const uint64_t clear_blocks = ((uint64_t)p.n_views * p.width * p.height / 2 + 2047) / 2048;
-    const uint64_t item_blocks = ((uint64_t)p.total_items + 31) / 32;
+    const uint64_t item_blocks = ((uint64_t)p.total_items + 7) / 8;
     const uint32_t cull_blocks = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>(std::max(clear_blocks, item_blocks), (uint64_t)sms * 8));
     Params pc = p;
