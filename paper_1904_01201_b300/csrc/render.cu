@@ -1167,8 +1167,15 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         mark(1, stream);
     }
     mark(2, stream);
+    // runs of kShadePx pixels per view; each thread takes up to eight of them
+    // (grid-stride), enough to amortise a CTA's prologue (the view's scene
+    // record), while the call keeps about four waves of resident CTAs
     const uint32_t quads = ((p.width + kShadePx - 1) / kShadePx) * p.height;
-    const uint32_t bx = std::min<uint32_t>((quads + kShadeThreads - 1) / kShadeThreads, 1024);
+    const uint64_t resident = (uint64_t)sms * 8u * kShadeThreads;
+    const uint32_t per_thread =
+        (uint32_t)std::min<uint64_t>(8, std::max<uint64_t>(1, (uint64_t)quads * p.n_views / (4 * resident)));
+    const uint32_t bx =
+        std::min<uint32_t>((quads + kShadeThreads * per_thread - 1) / (kShadeThreads * per_thread), 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
         shade_kernel<<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
