@@ -46,6 +46,22 @@ KERNEL_SOURCES = ["paper_1904_01201_b300/csrc/render.cu", "paper_1904_01201_b300
                   "paper_1904_01201_b300/csrc/kernels/shade.cuh", "paper_1904_01201_b300/csrc/kernels/bulk.cuh"]
 
 
+def d2h_link_gbs(dev, nbytes: int = 256 << 20) -> float:
+    """Device -> page-locked host copy bandwidth (GB/s), best of three."""
+    import torch
+    src = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dst = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    best = 0.0
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        best = max(best, nbytes / (time.perf_counter() - t) / 1e9)
+    del src, dst
+    return best
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -429,6 +445,13 @@ def run_gpu(args, wk):
         d2h_bytes = sum(v.numel() * v.element_size() for v in hb.values())
     e2e = {"value": n * e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d_bytes),
            "d2h_bytes_per_step": int(d2h_bytes)}
+    # the device->host link these frames cross, measured the same way (one
+    # 256 MiB copy to page-locked memory, best of three, untimed): the e2e
+    # frame traffic against it
+    link = d2h_link_gbs(dev)
+    e2e["d2h_gbs"] = e2e["value"] * d2h_bytes / n / 1e9
+    e2e["link_gbs"] = link
+    e2e["link_frac"] = e2e["d2h_gbs"] / link if link else None
 
     if rank != 0:
         return None
