@@ -399,7 +399,7 @@ def run_gpu(args, wk):
     def host_like(o):
         return {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items() if v is not None}
 
-    e2e_steps = max(3, args.steps // 4)
+    e2e_steps = max(20, args.steps // 4)      # enough steps for the two pipes to reach steady state
     if args.mode == "batched":
         out2 = hsr.alloc_outputs(n, W, H, ids=wk["ids"], device=dev)
         graph2 = hsr.hsr_batch_create([h.handle for h in handles], n, wk["intr"], W, H, out2["rgb"],
