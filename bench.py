@@ -304,10 +304,12 @@ def run_gpu(args, wk):
             raise hsr.HsrError(st, "hsr_batch_render")
         return 1
 
+    intr_c = hsr.as_intrinsics(wk["intr"])      # converted once, as a caller looping over agents would
+
     def step_plain():
         for i in range(n):
             h = handles[int(soa[i])]
-            st = hsr.hsr_render(h.handle, poses[i:i + 1], wk["intr"], W, H, out["rgb"][i:i + 1], out["depth"][i:i + 1],
+            st = hsr.hsr_render(h.handle, poses[i:i + 1], intr_c, W, H, out["rgb"][i:i + 1], out["depth"][i:i + 1],
                                 None if "ids" not in out else out["ids"][i:i + 1], stream)
             if st != 0:
                 raise hsr.HsrError(st, "render")

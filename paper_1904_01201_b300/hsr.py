@@ -251,6 +251,8 @@ def _stream_ptr(stream):
 
 
 def as_intrinsics(intr) -> hsr_intrinsics:
+    if isinstance(intr, hsr_intrinsics):
+        return intr
     a = np.asarray(getattr(intr, "as_array", lambda: intr)(), dtype=np.float32).reshape(6)
     return hsr_intrinsics(*[float(v) for v in a])
 
