@@ -276,6 +276,113 @@ def test_perspective_correct_texture_on_floor(oracle_mod):
     assert np.all(np.abs(got - expect[:, None]) <= 1)
 
 
+def _round_half_up(c):
+    return np.clip(np.floor(np.asarray(c, dtype=np.float64) + 0.5), 0, 255)
+
+
+def test_vertex_colours_linear_on_fronto_parallel_quad(oracle_mod):
+    # Distinct vertex colours that are a linear function of the screen
+    # position of a fronto-parallel quad (constant depth): every interpolated
+    # pixel must equal that function at its centre. Pairing a weight with the
+    # wrong vertex moves the ramps by up to their whole range.
+    W, H = 16, 12
+    sc = _fullscreen_quad(W, H, uv=False)
+    f = W / 2.0
+    sx = sc.xyz[:, 0].astype(np.float64) / -sc.xyz[:, 2] * f + W / 2.0
+    sy = H / 2.0 - sc.xyz[:, 1].astype(np.float64) / -sc.xyz[:, 2] * f
+    # corners sit at sx in {0, W}, sy in {0, H}: integer channel values there
+    col = np.stack([255 * sx / W, 255 * sy / H, 40 + 120 * sx / W + 60 * sy / H], 1)
+    assert np.allclose(col, np.round(col), atol=1e-9)
+    sc.vrgb = np.round(col).astype(np.uint8)
+    out = oracle_mod.render(sc, identity_pose()[None], screen_intr(W, H), W, H)
+    px = np.arange(W) + 0.5
+    py = np.arange(H) + 0.5
+    X, Y = np.meshgrid(px, py)
+    expect = np.stack([255 * X / W, 255 * Y / H, 40 + 120 * X / W + 60 * Y / H], -1)
+    got = out["rgb"][0].astype(np.float64)
+    assert np.all(np.abs(got - _round_half_up(expect)) <= 1)
+    assert np.mean(got != _round_half_up(expect)) < 0.02
+
+
+def test_vertex_colours_perspective_correct_on_floor(oracle_mod):
+    # Camera 1.5 m above a floor trapezoid from d = 2 to d = 8 (pitch 0, the
+    # 90-degree pinhole of Sec. 4). Vertex colours are linear in world x and
+    # depth d, so at every pixel the colour is that linear function at the
+    # floor point its centre ray hits: d = h fy / (y + 1/2 - cy),
+    # x = (x_px + 1/2 - cx) d / fx. Affine (screen-linear) weights get the
+    # red ramp wrong by tens of units in the middle rows.
+    W = H = 128
+    intr = pinhole_90(W, H, 0.01, 10.0)
+    v = np.array([[-2, 0, -2], [2, 0, -2], [8, 0, -8], [-8, 0, -8]], dtype=np.float64)
+    idx = np.array([[0, 1, 2], [0, 2, 3]])
+    n = np.cross(v[1] - v[0], v[2] - v[0])
+    if n[1] < 0:
+        idx = idx[:, [0, 2, 1]]
+    d_v, x_v = -v[:, 2], v[:, 0]
+
+    def colour(x, d):
+        return np.stack([40 * (d - 2), 15 * (x + 8), 10 + 20 * (d - 2) + 5 * (x + 8)], -1)
+
+    cv = colour(x_v, d_v)
+    assert np.allclose(cv, np.round(cv)) and cv.min() >= 0 and cv.max() <= 255
+    sc = Scene(xyz=v.astype(np.float32), idx=idx.astype(np.uint32), vrgb=np.round(cv).astype(np.uint8))
+    out = oracle_mod.render(sc, identity_pose(0, 1.5, 0)[None], intr, W, H)
+    hit = out["ids"][0] != BG
+    rows = np.arange(76, 112)
+    assert np.all(hit[rows].sum(1) > 0)
+    d = 1.5 * 64.0 / (rows + 0.5 - 64.0)
+    X = (np.arange(W)[None, :] + 0.5 - 64.0) * d[:, None] / 64.0
+    expect = _round_half_up(colour(X, np.repeat(d[:, None], W, 1)))
+    got = out["rgb"][0][rows].astype(np.float64)
+    m = hit[rows]
+    # one snapped vertex moves the floor by under 2^-9 px: within one unit
+    assert np.all(np.abs(got[m] - expect[m]) <= 1)
+
+
+def test_near_clipped_floor_interpolates_uv_at_the_clip_points(oracle_mod):
+    # A textured floor from behind the camera (d = -2) to d = 8 crosses the
+    # near plane, so the visible part of its triangles comes from the
+    # clipped polygons, whose new vertices carry uv interpolated along the
+    # clipped edges. With u linear in world x, v linear in world depth and a
+    # texture holding (R, G) = (row, column), each pixel's colour is fixed by
+    # the floor point its centre ray hits; a clip point with the wrong uv
+    # (swapped endpoints, t measured from the other end) bends the ramps.
+    W = H = 64
+    near = 0.25
+    intr = pinhole_90(W, H, near, 10.0)
+    h = 0.3
+    v = np.array([[-10, 0, 2], [10, 0, 2], [10, 0, -8], [-10, 0, -8]], dtype=np.float64)
+    idx = np.array([[0, 1, 2], [0, 2, 3]])
+    n = np.cross(v[1] - v[0], v[2] - v[0])
+    if n[1] < 0:
+        idx = idx[:, [0, 2, 1]]
+    uv = np.stack([(v[:, 0] + 10) / 20, (-v[:, 2] + 2) / 10], 1).astype(np.float32)
+    atlas = np.zeros((256, 256, 4), dtype=np.uint8)
+    atlas[..., 0] = np.arange(256)[:, None]
+    atlas[..., 1] = np.arange(256)[None, :]
+    sc = Scene(xyz=v.astype(np.float32), idx=idx.astype(np.uint32), uv=uv, atlas=atlas)
+    pose = identity_pose(0, h, 0)
+    out = oracle_mod.render(sc, pose[None], intr, W, H)
+    hit = out["ids"][0] != BG
+    rows = np.arange(H // 2 + 1, H)          # below the horizon
+    assert hit[rows].all()
+    d = h * 32.0 / (rows + 0.5 - 32.0)
+    assert d.min() > near and d.max() < 8
+    X = (np.arange(W)[None, :] + 0.5 - 32.0) * d[:, None] / 32.0
+    u = (X + 10) / 20
+    vv = (np.repeat(d[:, None], W, 1) + 2) / 10
+    # texel row t = 256 v - 1/2 holds the value t (a ramp): bilinear returns t
+    expect_r = _round_half_up(256 * vv - 0.5)
+    expect_g = _round_half_up(256 * u - 0.5)
+    got = out["rgb"][0][rows].astype(np.float64)
+    assert np.all(np.abs(got[..., 0] - expect_r) <= 1)
+    assert np.all(np.abs(got[..., 1] - expect_g) <= 1)
+    # both floor triangles reach behind the camera: every hit pixel is shaded
+    # from a clipped polygon
+    d_tri = -v[idx][:, :, 2]
+    assert np.all((d_tri < near).any(1))
+
+
 # ---------------------------------------------------------------- invariants
 def test_order_and_rotation_independence(oracle_mod):
     sc = make_room(2, 4000)
