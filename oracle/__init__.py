@@ -63,7 +63,20 @@ def lib():
         _lib.oracle_actuate.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, P, P]
         _lib.oracle_actuate.restype = ctypes.c_int
+        _lib.oracle_guard_clip.argtypes = [P, ctypes.c_int, ctypes.c_float, ctypes.c_float, P]
+        _lib.oracle_guard_clip.restype = ctypes.c_int
     return _lib
+
+
+def guard_clip(poly, gx: float, gy: float) -> np.ndarray:
+    """The rasteriser's guard-band clip of one polygon ([n <= 4, 3] rows of
+    (x_e, y_e, d)) against |x_e| <= gx d, |y_e| <= gy d; returns [m, 3]."""
+    v = np.ascontiguousarray(poly, dtype=np.float32).reshape(-1, 3)
+    out = np.zeros((8, 3), dtype=np.float32)
+    m = lib().oracle_guard_clip(_ptr(v), v.shape[0], float(gx), float(gy), _ptr(out))
+    if m < 0:
+        raise ValueError("a polygon of at most 4 vertices")
+    return out[:m].copy()
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

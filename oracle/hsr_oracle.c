@@ -25,6 +25,21 @@
  *              p = fma(t, p_b - p_a, p_a), d := near; fan from first vertex.
  *   project  : q = 1/d, sx = fma(fx, x_e*q, cx), sy = fma(-fy, y_e*q, cy),
  *              X = rint(256 sx), Y = rint(256 sy)  (8 sub-pixel bits).
+ *   guard    : a (near-clipped) polygon with a snapped coordinate at or
+ *              beyond +-2^30 is clipped further, Sutherland-Hodgman, against
+ *              the eye-space planes x_e >= -gx d, x_e <= gx d, y_e >= -gy d,
+ *              y_e <= gy d in that order, gx = 2^21 / fx, gy = 2^21 / fy
+ *              (float division): they project 2^21 pixels (2^29 sub-pixels)
+ *              either side of the principal point.  Plane distances are
+ *              fma(g, d, +-x_e); a crossing edge is cut from its endpoint
+ *              b nearer the cut (the inside one when s_in <= -s_out, else the
+ *              outside one), other endpoint r: t = s_b / (s_b - s_r),
+ *              p = fma(t, p_r - p_b, p_b), attributes likewise.  The choice
+ *              depends only on the two endpoints, so the two triangles sharing
+ *              an edge cut it at the same point, and the cut is computed from
+ *              the nearer endpoint, without cancellation against the far one.
+ *              The polygon is then projected again and fanned from its first
+ *              vertex.
  *   cull     : A = (X1-X0)(Y2-Y0) - (Y1-Y0)(X2-X0) in int64, keep A < 0
  *              (front faces are counter-clockwise in the world), then swap
  *              vertices 1 and 2 so that A > 0.
@@ -33,7 +48,12 @@
  *              (edge i->j is top iff dy == 0 and dx > 0, left iff dy < 0).
  *   depth    : plane of q over the snapped vertices, relative to vertex 0,
  *              fp32 op order below, clamped to [min q_i, max q_i] of the
- *              (sub-)triangle's vertices; fragment kept iff 1/q <= far.
+ *              (sub-)triangle's vertices; fragment kept iff 1/q <= far.  The
+ *              sub-triangles of a clipped polygon (near plane or guard band)
+ *              are first rotated cyclically so that vertex 0 has the smallest
+ *              q (the first such on ties): their other vertices can sit at
+ *              q = 1/near or far outside the image, where an fp32 plane
+ *              referenced at them loses the on-screen depth to cancellation.
  *   key      : ((~bits(q)) << 32) | triangle index; per-pixel minimum.
  *   shade    : perspective-correct weights E_k * q_k (fp64), bilinear
  *              clamp-to-edge texture lookup at (u*Wt - 0.5, v*Ht - 0.5), or
@@ -69,7 +89,7 @@
 #define OR_OK 0
 #define OR_ERR_ARG 1
 #define OR_ERR_OOM 2
-#define OR_ERR_RANGE 3      /* a snapped coordinate left +-2^30 sub-pixels */
+#define OR_ERR_RANGE 3      /* a snapped coordinate beyond +-2^30 sub-pixels after the guard clip */
 
 static uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
 static float u2f(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
@@ -202,6 +222,7 @@ typedef struct {
     /* views */
     const float *poses; uint32_t n;
     float fx, fy, cx, cy, znear, zfar;
+    float gx, gy;           /* guard planes |x_e| <= gx d, |y_e| <= gy d */
     uint32_t W, H;
     uint8_t *rgb; float *depth; uint32_t *ids; uint32_t *cover;
     /* depth noise */
@@ -349,6 +370,82 @@ static overt clip_point(const overt *p, const overt *r, float znear, int nattr)
     return o;
 }
 
+/* Guard-band clip of a polygon (n <= 4 vertices, all d >= near) against the
+   four planes of the reading in the header; returns the new size (<= 8). */
+static int guard_clip(const overt *in, int n, float gx, float gy, int nattr, overt *out)
+{
+    overt a[8], b[8];
+    int na = n;
+    for (int k = 0; k < n; k++) a[k] = in[k];
+    for (int pl = 0; pl < 4; pl++) {
+        const float g = pl < 2 ? gx : gy;
+        const float sgn = (pl & 1) ? -1.0f : 1.0f;     /* L, R, B, T: fma(g, d, +x), fma(g, d, -x), ... */
+        float dist[8];
+        for (int k = 0; k < na; k++) dist[k] = fmaf(g, a[k].d, sgn * (pl < 2 ? a[k].xe : a[k].ye));
+        int nb = 0;
+        for (int k = 0; k < na; k++) {
+            const int k1 = (k + 1) % na;
+            const int ain = dist[k] >= 0.0f, bin = dist[k1] >= 0.0f;
+            if (ain) b[nb++] = a[k];
+            if (ain != bin) {
+                /* cut from the endpoint nearer the cut: the inside one when
+                   s_in <= -s_out, else the outside one */
+                const overt *pi = ain ? &a[k] : &a[k1], *po = ain ? &a[k1] : &a[k];
+                const float si = ain ? dist[k] : dist[k1], so = ain ? dist[k1] : dist[k];
+                const int from_in = si <= -so;
+                const overt *pb = from_in ? pi : po, *pr = from_in ? po : pi;
+                const float sb = from_in ? si : so, sr = from_in ? so : si;
+                const float t = sb / (sb - sr);
+                overt o;
+                o.xe = fmaf(t, pr->xe - pb->xe, pb->xe);
+                o.ye = fmaf(t, pr->ye - pb->ye, pb->ye);
+                o.d = fmaf(t, pr->d - pb->d, pb->d);
+                o.vid = 0xFFFFFFFFu;
+                for (int c = 0; c < nattr; c++) o.attr[c] = pb->attr[c] + (double)t * (pr->attr[c] - pb->attr[c]);
+                for (int c = nattr; c < 3; c++) o.attr[c] = 0;
+                b[nb++] = o;
+            }
+        }
+        na = nb;
+        for (int k = 0; k < na; k++) a[k] = b[k];
+        if (na == 0) break;
+    }
+    for (int k = 0; k < na; k++) out[k] = a[k];
+    return na;
+}
+
+/* The guard clip on its own (for the pins): in, out [n][3] = (x_e, y_e, d)
+   per vertex; returns the clipped size (out holds up to 8 vertices). */
+int oracle_guard_clip(const float *in, int n, float gx, float gy, float *out)
+{
+    if (n < 0 || n > 4) return -1;
+    overt v[4], r[8];
+    for (int k = 0; k < n; k++) {
+        v[k].xe = in[3 * k]; v[k].ye = in[3 * k + 1]; v[k].d = in[3 * k + 2];
+        v[k].vid = (uint32_t)k;
+        v[k].attr[0] = v[k].attr[1] = v[k].attr[2] = 0;
+    }
+    const int m = guard_clip(v, n, gx, gy, 0, r);
+    for (int k = 0; k < m; k++) { out[3 * k] = r[k].xe; out[3 * k + 1] = r[k].ye; out[3 * k + 2] = r[k].d; }
+    return m;
+}
+
+/* Project and snap the polygon's vertices; 0 if a coordinate is at or beyond
+   +-2^30 sub-pixels (or not a number). */
+static int project_poly(const ojob *J, const overt *poly, int np, int32_t *X, int32_t *Y, float *q)
+{
+    for (int k = 0; k < np; k++) {
+        q[k] = 1.0f / poly[k].d;
+        float sx = fmaf(J->fx, poly[k].xe * q[k], J->cx);
+        float sy = fmaf(-J->fy, poly[k].ye * q[k], J->cy);
+        float rx = rintf(sx * 256.0f), ry = rintf(sy * 256.0f);
+        if (!(fabsf(rx) < 1073741824.0f) || !(fabsf(ry) < 1073741824.0f)) return 0;
+        X[k] = (int32_t)rx;
+        Y[k] = (int32_t)ry;
+    }
+    return 1;
+}
+
 static int render_frame(ojob *J, uint32_t f, uint64_t *best)
 {
     const uint32_t W = J->W, H = J->H;
@@ -394,7 +491,7 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
         const float zn = J->znear, zf = J->zfar;
         if (v[0].d < zn && v[1].d < zn && v[2].d < zn) continue;
         if (v[0].d > zf && v[1].d > zf && v[2].d > zf) continue;
-        overt poly[4];
+        overt poly[8];
         int np = 0;
         if (v[0].d >= zn && v[1].d >= zn && v[2].d >= zn) {
             poly[0] = v[0]; poly[1] = v[1]; poly[2] = v[2]; np = 3;
@@ -406,17 +503,16 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
                 if (ain != bin) poly[np++] = clip_point(a, b, zn, nattr);
             }
         }
-        /* project and snap */
-        int32_t X[4], Y[4];
-        float q[4];
-        for (int k = 0; k < np; k++) {
-            q[k] = 1.0f / poly[k].d;
-            float sx = fmaf(J->fx, poly[k].xe * q[k], J->cx);
-            float sy = fmaf(-J->fy, poly[k].ye * q[k], J->cy);
-            float rx = rintf(sx * 256.0f), ry = rintf(sy * 256.0f);
-            if (!(fabsf(rx) < 1073741824.0f) || !(fabsf(ry) < 1073741824.0f)) return OR_ERR_RANGE;
-            X[k] = (int32_t)rx;
-            Y[k] = (int32_t)ry;
+        /* project and snap; beyond the fixed-point range, clip to the guard band */
+        int32_t X[8], Y[8];
+        float q[8];
+        int clipped = np != 3 || poly[0].vid != v[0].vid || poly[1].vid != v[1].vid || poly[2].vid != v[2].vid;
+        if (!project_poly(J, poly, np, X, Y, q)) {
+            clipped = 1;
+            overt near_poly[4];
+            for (int k = 0; k < np; k++) near_poly[k] = poly[k];
+            np = guard_clip(near_poly, np, J->gx, J->gy, nattr, poly);
+            if (!project_poly(J, poly, np, X, Y, q)) return OR_ERR_RANGE;
         }
         for (int fan = 0; fan + 2 < np; fan++) {
             int i0 = 0, i1 = fan + 1, i2 = fan + 2;
@@ -424,6 +520,14 @@ static int render_frame(ojob *J, uint32_t f, uint64_t *best)
             if (A >= 0) continue;
             int tmp = i1; i1 = i2; i2 = tmp;      /* orient to positive area */
             A = -A;
+            if (clipped) {
+                /* a clipped polygon's vertices can sit at q = 1/near or on the
+                   guard planes: the plane is referenced at the sub-triangle's
+                   vertex of smallest q (first in oriented order on ties), a
+                   cyclic rotation that keeps the orientation */
+                if (q[i1] < q[i0] && q[i1] <= q[i2]) { tmp = i0; i0 = i1; i1 = i2; i2 = tmp; }
+                else if (q[i2] < q[i0] && q[i2] < q[i1]) { tmp = i0; i0 = i2; i2 = i1; i1 = tmp; }
+            }
             const int32_t X0 = X[i0], Y0 = Y[i0], X1 = X[i1], Y1 = Y[i1], X2 = X[i2], Y2 = Y[i2];
             const float q0 = q[i0], q1 = q[i1], q2 = q[i2];
             /* plane of q, relative to vertex 0 */
@@ -587,6 +691,8 @@ int oracle_render_full(const float *xyz, uint32_t nv, const uint32_t *idx, uint3
         J->poses = poses; J->n = n;
         J->fx = intr[0]; J->fy = intr[1]; J->cx = intr[2]; J->cy = intr[3];
         J->znear = intr[4]; J->zfar = intr[5];
+        J->gx = 2097152.0f / J->fx;
+        J->gy = 2097152.0f / J->fy;
         J->W = W; J->H = H; J->rgb = rgb; J->depth = depth; J->ids = ids; J->cover = cover;
         J->noise_sigma = noise_sigma; J->noise_seed = noise_seed; J->agent_ids = agent_ids;
         J->nlev = nlev;

@@ -562,6 +562,161 @@ def _rot_from_float_quat(pose):
     return _rodrigues(q[1:] / s, ang)
 
 
+# ---------------------------------------------------------------- guard band
+def _max_snap(scene, pose, intr):
+    """Largest |256 s| over the scene's vertices in front of the near plane
+    and its near-plane crossing points (double precision, identity rotation)."""
+    fx, fy, cx, cy, near, far = [float(v) for v in intr.as_array()]
+    e = scene.xyz.astype(np.float64) - np.asarray(pose[:3], dtype=np.float64)
+    best = 0.0
+    for tri in scene.idx.astype(np.int64):
+        pts = [e[i] for i in tri]
+        for a in range(3):
+            p, r = pts[a], pts[(a + 1) % 3]
+            dp, dr = -p[2], -r[2]
+            cand = [p] if dp >= near else []
+            if (dp >= near) != (dr >= near):
+                t = (near - dp) / (dr - dp)
+                cand.append(p + t * (r - p))
+            for c in cand:
+                d = max(-c[2], near)
+                best = max(best, abs(256 * (fx * c[0] / d + cx)), abs(256 * (-fy * c[1] / d + cy)))
+    return best
+
+
+def _clip64(poly, gx, gy):
+    """Sutherland-Hodgman in float64 against x >= -gx d, x <= gx d,
+    y >= -gy d, y <= gy d (the exact clip the float32 one approximates)."""
+    pts = [np.asarray(p, dtype=np.float64) for p in poly]
+    for k in range(4):
+        g, comp, sgn = (gx, 0, 1.0) if k == 0 else (gx, 0, -1.0) if k == 1 else (gy, 1, 1.0) if k == 2 else (gy, 1, -1.0)
+        dist = [g * p[2] + sgn * p[comp] for p in pts]
+        out = []
+        for i in range(len(pts)):
+            j = (i + 1) % len(pts)
+            if dist[i] >= 0:
+                out.append(pts[i])
+            if (dist[i] >= 0) != (dist[j] >= 0):
+                t = dist[i] / (dist[i] - dist[j])
+                out.append(pts[i] + t * (pts[j] - pts[i]))
+        pts = out
+        if not pts:
+            break
+    return np.array(pts).reshape(-1, 3)
+
+
+def test_guard_clip_points_lie_on_the_cut_edges(oracle_mod):
+    # Polygons with vertices from 1e-6 m to 10 m deep and up to 10 m to the
+    # side, so that cuts fall close to one endpoint of edges whose other
+    # endpoint is 10^6 times farther: each cut point must agree with the
+    # float64 clip to float precision of its own size (a cut computed from
+    # the far endpoint is off by that endpoint's rounding, up to ~10 %).
+    rng = np.random.default_rng(9)
+    gx, gy = np.float32(2.0 ** 21) / np.float32(24.0), np.float32(2.0 ** 21) / np.float32(30.0)
+    checked = 0
+    for trial in range(3000):
+        n = int(rng.integers(3, 5))
+        d = 10.0 ** rng.uniform(-6, 1, n)
+        poly = np.stack([rng.uniform(-10, 10, n), rng.uniform(-10, 10, n), d], 1).astype(np.float32)
+        got = oracle_mod.guard_clip(poly, gx, gy)
+        ref = _clip64(poly.astype(np.float64), float(gx), float(gy))
+        if len(got) != len(ref):
+            continue                    # a vertex within rounding of a plane
+        checked += 1
+        assert np.all(np.abs(got[:, 2] - ref[:, 2]) <= 1e-5 * ref[:, 2]), trial
+        scale = np.abs(ref[:, :2]) + np.array([gx, gy]) * ref[:, 2:3]
+        assert np.all(np.abs(got[:, :2] - ref[:, :2]) <= 1e-5 * scale), trial
+    assert checked > 2900
+
+
+def test_guard_band_huge_fronto_parallel_quad(oracle_mod):
+    # A quad at depth D reaching 10^6 m to every side: all four vertices snap
+    # far beyond +-2^30 sub-pixels, so both triangles are clipped to the
+    # guard band. The clipped polygons keep the quad's plane (d = D at every
+    # clip point), so every pixel is covered exactly once at depth D exactly,
+    # and the shared diagonal, which crosses the screen, leaves no crack.
+    W, H = 40, 24
+    for D in (1.0, 0.5, 4.0):
+        c = np.array([[-1e6, -1e6, -D], [1e6, -1e6, -D], [-1e6, 1e6, -D], [1e6, 1e6, -D]])
+        for diag in (0, 1):
+            tris = [[c[0], c[1], c[3]], [c[0], c[3], c[2]]] if diag == 0 else [[c[0], c[1], c[2]], [c[1], c[3], c[2]]]
+            sc = scene_from_tris(tris)
+            intr = screen_intr(W, H)
+            assert _max_snap(sc, identity_pose(), intr) > 2.0 ** 30
+            out = oracle_mod.render(sc, identity_pose()[None], intr, W, H, coverage=True)
+            assert np.all(out["cover"][0] == 1)
+            assert np.all(out["depth"][0] == np.float32(D))
+
+
+def test_guard_band_floor_interpolates_uv_at_guard_points(oracle_mod):
+    # The near-clipped floor of the near-clip pin with a near plane of 2e-6 m:
+    # its clip points project ~10^9 pixels below the image, so the polygons
+    # are clipped again at the guard planes (bottom, left and right), and
+    # every visible pixel is shaded through guard-clip vertices. u is linear
+    # in world x, v in depth; the colour must follow the closed form.
+    W = H = 64
+    near = 2e-6
+    intr = Intrinsics(32.0, 32.0, 32.0, 32.0, near, 10.0)
+    h = 0.3
+    v = np.array([[-10, 0, 2], [10, 0, 2], [10, 0, -8], [-10, 0, -8]], dtype=np.float64)
+    idx = np.array([[0, 1, 2], [0, 2, 3]])
+    n = np.cross(v[1] - v[0], v[2] - v[0])
+    if n[1] < 0:
+        idx = idx[:, [0, 2, 1]]
+    uv = np.stack([(v[:, 0] + 10) / 20, (-v[:, 2] + 2) / 10], 1).astype(np.float32)
+    atlas = np.zeros((256, 256, 4), dtype=np.uint8)
+    atlas[..., 0] = np.arange(256)[:, None]
+    atlas[..., 1] = np.arange(256)[None, :]
+    sc = Scene(xyz=v.astype(np.float32), idx=idx.astype(np.uint32), uv=uv, atlas=atlas)
+    pose = identity_pose(0, h, 0)
+    assert _max_snap(sc, pose, intr) > 2.0 ** 33
+    out = oracle_mod.render(sc, pose[None], intr, W, H)
+    rows = np.arange(H // 2 + 1, H)
+    assert (out["ids"][0][rows] != BG).all()
+    d = h * 32.0 / (rows + 0.5 - 32.0)
+    X = (np.arange(W)[None, :] + 0.5 - 32.0) * d[:, None] / 32.0
+    expect_r = _round_half_up(256 * (np.repeat(d[:, None], W, 1) + 2) / 10 - 0.5)
+    expect_g = _round_half_up(256 * (X + 10) / 20 - 0.5)
+    got = out["rgb"][0][rows].astype(np.float64)
+    assert np.all(np.abs(got[..., 0] - expect_r) <= 1)
+    assert np.all(np.abs(got[..., 1] - expect_g) <= 1)
+    # and the floor's depth follows d = h fy / (y + 1/2 - cy), i.e. q is
+    # (y + 1/2 - cy) / (h fy): snapping moves each vertex by at most 2^-9 px,
+    # which moves q by at most 2^-9 / (h fy) per unit of slope (doubled here)
+    q_true = (rows + 0.5 - 32.0) / (h * 32.0)
+    q_got = 1.0 / out["depth"][0][rows].astype(np.float64)
+    assert np.all(np.abs(q_got - q_true[:, None]) <= 2.0 ** -8 / (h * 32.0) + 1e-6 * q_true[:, None])
+
+
+@pytest.mark.parametrize("block", range(2))
+def test_guard_band_random_scenes_vs_ray_casting(oracle_mod, block):
+    # Random scenes around the camera with near planes of 1e-6 .. 1e-5 m and
+    # fx != fy: triangles reaching behind the camera are near-clipped at
+    # points that project far outside the fixed-point range, then clipped to
+    # the guard band. Ids must equal the float64 ray cast on every
+    # unambiguous pixel.
+    rng = np.random.default_rng(500 + block)
+    n_guard = 0
+    amb_total = px_total = 0
+    for trial in range(60):
+        W, H = int(rng.integers(8, 40)), int(rng.integers(8, 40))
+        T = int(rng.integers(4, 40))
+        sc = _random_tiny_scene(rng, T)
+        f = float(rng.uniform(0.4, 1.2)) * W
+        intr = Intrinsics(f, f * float(rng.uniform(0.7, 1.4)), W / 2 + float(rng.uniform(-2, 2)),
+                          H / 2 + float(rng.uniform(-2, 2)), float(10 ** rng.uniform(-6, -5)), 6.0)
+        pose = identity_pose()
+        n_guard += _max_snap(sc, pose, intr) >= 2.0 ** 30
+        o = oracle_mod.render(sc, pose[None], intr, W, H)
+        bf = brute_force(sc, pose.astype(np.float64), intr, W, H)
+        ok = ~bf["ambiguous"]
+        assert np.array_equal(o["ids"][0][ok], bf["ids"][ok]), (trial, W, H, T)
+        amb_total += int(bf["ambiguous"].sum())
+        px_total += W * H
+    assert n_guard >= 30
+    assert amb_total / px_total < 0.02
+
+
 def test_equal_depth_ties_go_to_lower_index(oracle_mod):
     # coincident coplanar triangles give equal keys' depth parts: the lower
     # triangle index must win every tie, whatever the submission order
