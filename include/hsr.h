@@ -52,8 +52,8 @@ typedef enum {
     HSR_ERR_INVALID_ARG = 1,  /* null pointer, zero count, index >= n_verts,
                                  non-finite input, non-unit quaternion
                                  (| |q| - 1 | > 1e-3), width/height outside
-                                 1..4096, bad intrinsics, or a pose/scene whose
-                                 projection could leave +-2^30 sub-pixels      */
+                                 1..4096, or intrinsics outside their limits
+                                 (see hsr_intrinsics)                          */
     HSR_ERR_OOM = 2,          /* device or host allocation failed             */
     HSR_ERR_CUDA = 3,         /* a CUDA runtime call failed                    */
     HSR_ERR_TIMEOUT = 4,      /* a bounded device wait expired                 */
@@ -69,10 +69,19 @@ typedef struct {
     float quat[4];     /* w, x, y, z: world-from-camera rotation            */
 } hsr_pose;
 
+/*
+ * Pinhole intrinsics. Limits (else HSR_ERR_INVALID_ARG): all finite, fx > 0,
+ * fy > 0, |cx| <= 65536, |cy| <= 65536, 2^-20 <= znear < zfar.
+ * Projected vertices are snapped to 1/256 pixel in 32-bit integers; a
+ * triangle whose snapped coordinates would reach +-2^30 sub-pixels (very
+ * near the camera, at large focal lengths or tiny near planes) is first
+ * clipped to a guard band 2^21 pixels either side of the principal point,
+ * which leaves the pixels it covers unchanged, so any pose is rendered.
+ */
 typedef struct {
     float fx, fy;      /* focal lengths in pixels (90 deg HFOV: fx = W/2)   */
     float cx, cy;      /* principal point in pixels (image centre: W/2,H/2) */
-    float znear;       /* near clip distance, metres, > 0                   */
+    float znear;       /* near clip distance, metres                        */
     float zfar;        /* fragments with depth > zfar are discarded         */
 } hsr_intrinsics;
 
@@ -455,16 +464,25 @@ HSR_API int hsr_get_stage_stats(uint32_t *counts);
 /*
  * Allocation-free variant of hsr_render (the paper has no counterpart; this is
  * a library-integration feature). Same arguments, outputs and results as
- * hsr_render, but no memory is allocated on the call path: its scratch (view
- * descriptors, z-buffer, visible-meshlet list) is one fixed 32 MiB array in
- * device memory, present on every GPU that loads the library until the
- * process exits. For callers that cannot let a library allocate: processes
- * whose framework already holds the device memory in its own pool, loops that
- * cannot afford an allocator call, and hosts that route every allocation
- * through their own allocator.
+ * hsr_render (any non-empty subset of rgb, depth, ids), but no memory is
+ * allocated on the call path: its scratch (view descriptors, z-buffer,
+ * visible-meshlet list) is one fixed 32 MiB array in device memory, present
+ * on every GPU that loads the library until the process exits. For callers
+ * that cannot let a library allocate: processes whose framework already
+ * holds the device memory in its own pool, loops that cannot afford an
+ * allocator call, and hosts that route every allocation through their own
+ * allocator.
  *   - A call needing more than 32 MiB of scratch (about 8 B per output pixel
  *     per view + 48 B per meshlet per view + 192 B per view) returns
  *     HSR_ERR_OVERFLOW; split such batches or use hsr_render.
+ *   - The view descriptors are staged in a fixed 1 MiB host buffer (192 B per
+ *     view: at most 5,457 views per call, more return HSR_ERR_OVERFLOW). It is
+ *     ordinary pageable memory, copied with cudaMemcpyAsync under a
+ *     process-wide lock: the copy has read it when the call returns, and the
+ *     call may wait for work queued earlier on the stream.
+ *   - Large triangles are rasterised by the warp that set them up (the
+ *     separate large-triangle pass of hsr_render needs scratch this array
+ *     does not hold): the images are the same, the speed can differ.
  *   - All calls share the array and it keeps the last call's contents (each
  *     call re-initialises what it needs). Calls whose work overlaps on the
  *     GPU race and corrupt each other's images: order them on one stream.
@@ -482,8 +500,11 @@ HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose *poses, ui
  * expires makes the kernel stop, record the failure and return, leaving the
  * context usable (the frame is then incomplete). hsr_device_status waits for
  * the current device and returns HSR_ERR_TIMEOUT if any kernel recorded such
- * a failure since the last clear (clear != 0 resets the record), HSR_OK
- * otherwise, HSR_ERR_CUDA if the device cannot be queried.
+ * a failure since the last clear (clear != 0 resets the record),
+ * HSR_ERR_OVERFLOW if a triangle was dropped because its guard-band-clipped
+ * vertices still left the fixed-point range (not reachable within the
+ * documented input limits), HSR_OK otherwise, HSR_ERR_CUDA if the device
+ * cannot be queried.
  */
 HSR_API int hsr_device_status(int clear);
 /* Test hook for the failure path above: renders launched while extra_bytes

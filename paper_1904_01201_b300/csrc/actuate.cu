@@ -60,9 +60,7 @@ __global__ void __launch_bounds__(kActuateThreads) actuate_kernel(const Params p
             const float nx = (float)((double)pose[0] + ag->step * (hx / len));
             const float nz = (float)((double)pose[2] + ag->step * (hz / len));
             const NavDev &nav = ag->nav[v.scene];
-            const float np[3] = {nx, pose[1], nz};
-            if (navigable(nav, nx, nz) &&
-                snap_bound_ok(nav.amin, nav.amax, np, p.fx, p.fy, p.cx, p.cy, p.znear)) {
+            if (navigable(nav, nx, nz)) {
                 pose[0] = nx;
                 pose[2] = nz;
             }

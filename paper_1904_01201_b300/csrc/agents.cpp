@@ -166,10 +166,6 @@ int hsr_agents_create(const hsr_scene *const *scenes, uint32_t n_scenes, const h
         std::memset(&d, 0, sizeof(d));
         d.x0 = m.x0; d.z0 = m.z0; d.cell = m.cell; d.nx = m.nx; d.nz = m.nz;
         d.grid = a->d_grid + off;
-        for (int k = 0; k < 3; k++) {
-            d.amin[k] = a->info[s].aabb_min[k];
-            d.amax[k] = a->info[s].aabb_max[k];
-        }
         off += (nb + 255) & ~(size_t)255;
     }
     AgentsDev ad{};

@@ -87,13 +87,17 @@ uint64_t spread21(uint64_t x)
 // agent pose). Double precision, fixed operation order, rounded once to float.
 bool camera_matrix(const hsr_pose &pose, float M[12]) { return camera_from_pose(pose.pos, pose.quat, M); }
 
+// Finite, positive focal lengths, a principal point within 2^16 pixels of
+// the image origin (so that the guard band, 2^21 pixels either side of it,
+// stays inside the fixed-point range), 2^-20 m <= near < far.
 bool intrinsics_ok(const hsr_intrinsics *in)
 {
     if (!in) return false;
     const float v[6] = {in->fx, in->fy, in->cx, in->cy, in->znear, in->zfar};
     for (float f : v)
         if (!std::isfinite(f)) return false;
-    return in->fx > 0.f && in->fy > 0.f && in->znear > 0.f && in->zfar > in->znear;
+    return in->fx > 0.f && in->fy > 0.f && std::fabs(in->cx) <= 65536.f && std::fabs(in->cy) <= 65536.f &&
+           in->znear >= 0x1p-20f && in->zfar > in->znear;
 }
 
 // Smallest positive float q with 1/q <= far (both rounded to nearest), so the
@@ -111,12 +115,12 @@ float far_threshold(float zfar)
     return q;
 }
 
-// Conservative bound on |256 sx| and |256 sy| for a view of this scene: any
-// vertex (or near-clipped point) has |x_e|, |y_e| <= distance to the farthest
-// box corner and d >= near.
-bool snap_in_range(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in)
+// Guard-plane slope of a focal length: 2^21 / f (one IEEE float division),
+// the planes |x_e| <= g d project 2^21 pixels either side of the principal point.
+float guard_g(float f)
 {
-    return snap_bound_ok(s->info.aabb_min, s->info.aabb_max, pose.pos, in.fx, in.fy, in.cx, in.cy, in.znear);
+    volatile float num = 2097152.0f;
+    return num / f;
 }
 
 struct Staging {
@@ -207,7 +211,7 @@ hsr_config to_config(const LaunchCfg &l)
 // Layout of the per-render descriptors (host staging and device copy) and of
 // the device scratch, for a capacity of n_cap views of the given scenes.
 //   descriptors: header (counters + dyn words) | scene table | slot arrays | views
-//   scratch:     z-buffer | visible lists | tile z | binned triangles | bin instances
+//   scratch:     z-buffer | visible lists | tile z | binned triangles | bin instances | survivors
 struct Plan {
     uint32_t n_cap = 0, width = 0, height = 0, n_scenes = 0;
     LaunchCfg cfg;
@@ -315,11 +319,15 @@ bool noise_ok(const hsr_depth_noise *nz)
 // zeroed counters and the dynamic header words. frames[i] (or i) is the
 // output frame of agent i; its depth-noise stream is keyed by
 // noise.agent_ids[i], else by agent_base + its output frame.
+// *guard (if given) is set when some view may snap a vertex beyond +-2^30
+// sub-pixels (guard_free fails for its pose, or, for step batches whose poses
+// live on the device, for a camera anywhere in its scene's box).
 int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint32_t *scene_of_agent,
                      const hsr_pose *poses, uint32_t n, const uint32_t *frames, const hsr_intrinsics &intr,
                      unsigned char *hbuf, const NoiseReq &nr = NoiseReq{}, const StepReq *step = nullptr,
-                     const uint32_t *outputs = nullptr)
+                     const uint32_t *outputs = nullptr, bool *guard = nullptr)
 {
+    bool need_guard = false;
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
     if (!noise_ok(nr.noise)) return HSR_ERR_INVALID_ARG;
     const uint32_t *agent_ids = nr.noise ? nr.noise->agent_ids : nullptr;
@@ -353,14 +361,20 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
         lists += scenes[sidx]->dev.n_meshlets;
         View &v = hv[k];
         std::memset(&v, 0, sizeof(View));
+        const hsr_scene_info &box = scenes[sidx]->info;
         if (step) {
             v.state = step->state[i];
             v.action = step->action[i];
+            // agents stay inside their scene's box: a camera at one corner
+            // sees the farthest corner at the largest possible distance
+            need_guard |= !guard_free(box.aabb_min, box.aabb_max, box.aabb_min, intr.fx, intr.fy, intr.cx, intr.cy,
+                                      intr.znear);
         } else {
             if (!camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
-            if (!snap_in_range(scenes[sidx], poses[i], intr)) return HSR_ERR_INVALID_ARG;
             view_planes(v.M, intr, pl.width, pl.height, v.planes);
             for (int c = 0; c < 3; c++) v.pos[c] = poses[i].pos[c];
+            need_guard |= !guard_free(box.aabb_min, box.aabb_max, poses[i].pos, intr.fx, intr.fy, intr.cx, intr.cy,
+                                      intr.znear);
         }
         v.scene = sidx;
         v.outputs = outputs ? outputs[i] : (uint32_t)(HSR_OUT_RGB | HSR_OUT_DEPTH | HSR_OUT_IDS);
@@ -382,6 +396,7 @@ int fill_descriptors(const Plan &pl, const hsr_scene *const *scenes, const uint3
         hdr[kHdrDyn + 4] = (uint32_t)nr.noise->seed;
         hdr[kHdrDyn + 5] = (uint32_t)(nr.noise->seed >> 32);
     }
+    if (guard) *guard = need_guard;
     return HSR_OK;
 }
 
@@ -429,6 +444,8 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
     p.znear = intr.znear; p.zfar = intr.zfar;
     p.q_far = far_threshold(intr.zfar);
     p.inv_far = (float)(1.0 / (double)intr.zfar);
+    p.gx = guard_g(intr.fx);
+    p.gy = guard_g(intr.fy);
     const LaunchCfg &cfg = pl.cfg;
     p.small_px = std::min<uint32_t>(std::max<uint32_t>(cfg.small_px, 1), 32);
     p.bin_px = std::max(cfg.bin_px, p.small_px);
@@ -440,10 +457,10 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
     return p;
 }
 
-// Stream work of one render: upload descriptors, optionally preset the
-// z-buffer, launch the kernels.
+// Stream work of one render: upload descriptors, the actuation pass of a
+// step batch, the kernels (guard: shading with the guard-band path).
 cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const void *h_desc, cudaStream_t stream,
-                           bool actuate = false)
+                           bool actuate, bool guard)
 {
     cudaError_t e = cudaMemcpyAsync(d_desc, h_desc, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return e;
@@ -451,7 +468,7 @@ cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const 
         e = launch_actuate(p, pl.n_cap, stream);
         if (e != cudaSuccess) return e;
     }
-    return launch_render(p, pl.cfg, stream);
+    return launch_render(p, pl.cfg, stream, guard);
 }
 
 // Scenes, poses, intrinsics and size of a render; at least one output buffer
@@ -543,8 +560,9 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     }
     if (!st.done && cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) != cudaSuccess) return HSR_ERR_CUDA;
     auto *hbuf = static_cast<unsigned char *>(st.host);
+    bool guard = false;
     int status = fill_descriptors(pl, scenes, scene_of_agent, poses, n, vr.frames, *intr, hbuf, nr, nullptr,
-                                  vr.outputs);
+                                  vr.outputs, &guard);
     if (status != HSR_OK) return status;
 
     void *dbuf = nullptr, *sbuf = nullptr;
@@ -560,7 +578,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     e = cudaMemcpyAsync(dbuf, hbuf, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
     if (e == cudaSuccess) st.pending = true;
-    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream);
+    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream, guard);
     cudaError_t e1 = cudaFreeAsync(sbuf, stream);
     cudaError_t e2 = cudaFreeAsync(dbuf, stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -580,10 +598,12 @@ struct hsr_batch {
     unsigned char *d_desc[2] = {nullptr, nullptr};
     unsigned char *h_desc[2] = {nullptr, nullptr};
     unsigned char *d_scratch = nullptr;
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    cudaGraph_t step_graph[2] = {nullptr, nullptr};      // upload, actuation, render (captured on first step)
-    cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+    // captured renders per descriptor buffer k, in four variants: pose
+    // renders (0) and step renders (2: upload, actuation, render), each also
+    // with the guard-band shading (+1); variant 0 is captured at creation,
+    // the others on first use
+    cudaGraph_t graph[4][2] = {};
+    cudaGraphExec_t exec[4][2] = {};
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool launched[2] = {false, false};
     int cur = 0;
@@ -603,10 +623,10 @@ void free_batch(hsr_batch *b)
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     for (int k = 0; k < 2; k++) {
-        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
-        if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
-        if (b->step_exec[k]) cudaGraphExecDestroy(b->step_exec[k]);
-        if (b->step_graph[k]) cudaGraphDestroy(b->step_graph[k]);
+        for (int v = 0; v < 4; v++) {
+            if (b->exec[v][k]) cudaGraphExecDestroy(b->exec[v][k]);
+            if (b->graph[v][k]) cudaGraphDestroy(b->graph[v][k]);
+        }
         if (b->done[k]) cudaEventDestroy(b->done[k]);
         if (b->d_desc[k]) cudaFree(b->d_desc[k]);
         if (b->h_desc[k]) cudaFreeHost(b->h_desc[k]);
@@ -627,9 +647,10 @@ void host_view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, u
 {
     view_planes(M, in, W, H, planes);
 }
-bool host_snap_in_range(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in)
+float host_guard_g(float f) { return guard_g(f); }
+bool host_guard_free(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in)
 {
-    return snap_in_range(s, pose, in);
+    return guard_free(s->info.aabb_min, s->info.aabb_max, pose.pos, in.fx, in.fy, in.cx, in.cy, in.znear);
 }
 const SceneDev &host_scene_dev(const hsr_scene *s) { return s->dev; }
 }  // namespace hsr
@@ -1103,17 +1124,45 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
         if ((e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
         const Params p = make_params(pl, b->d_desc[k], b->d_scratch, *intr, rgb, depth, ids);
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
-        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs);
-        e = cudaStreamEndCapture(cs, &b->graph[k]);
+        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, false, false);
+        e = cudaStreamEndCapture(cs, &b->graph[0][k]);
         if (er != cudaSuccess) return fail(er);
         if (e != cudaSuccess) return fail(e);
-        if ((e = cudaGraphInstantiate(&b->exec[k], b->graph[k], 0)) != cudaSuccess) return fail(e);
+        if ((e = cudaGraphInstantiate(&b->exec[0][k], b->graph[0][k], 0)) != cudaSuccess) return fail(e);
     }
     cudaStreamDestroy(cs);
     cs = nullptr;
     b->plan = pl;
     b->n_frames = n_frames;
     *out = b;
+    return HSR_OK;
+}
+
+// Graph variant v (0: pose render, 2: step render, +1: guard-band shading) of
+// descriptor buffer k, captured on first use. Called with the batch's lock.
+int batch_exec(hsr_batch *b, int v, int k, cudaGraphExec_t *out)
+{
+    if (!b->exec[v][k]) {
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSR_ERR_CUDA;
+        const Plan &pl = b->plan;
+        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, b->intr, b->rgb, b->depth, b->ids);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, v >= 2, (v & 1) != 0);
+            e = cudaStreamEndCapture(cs, &b->graph[v][k]);
+            if (er != cudaSuccess) e = er;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[v][k], b->graph[v][k], 0);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            if (b->graph[v][k]) cudaGraphDestroy(b->graph[v][k]);
+            b->graph[v][k] = nullptr;
+            b->exec[v][k] = nullptr;
+            return cuda_status(e);
+        }
+    }
+    *out = b->exec[v][k];
     return HSR_OK;
 }
 }  // namespace hsr
@@ -1133,6 +1182,7 @@ int hsr_batch_render(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pos
     return hsr_batch_render_noisy(b, scene_of_agent, poses, n, frames, nullptr, cuda_stream);
 }
 
+
 int hsr_batch_render_noisy(hsr_batch *b, const uint32_t *scene_of_agent, const hsr_pose *poses, uint32_t n,
                            const uint32_t *frames, const hsr_depth_noise *noise, void *cuda_stream)
 {
@@ -1148,9 +1198,13 @@ int hsr_batch_render_noisy(hsr_batch *b, const uint32_t *scene_of_agent, const h
     if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
     NoiseReq nr;
     nr.noise = noise;
-    int st = fill_descriptors(pl, b->scenes.data(), scene_of_agent, poses, n, frames, b->intr, b->h_desc[k], nr);
+    bool guard = false;
+    int st = fill_descriptors(pl, b->scenes.data(), scene_of_agent, poses, n, frames, b->intr, b->h_desc[k], nr,
+                              nullptr, nullptr, &guard);
     if (st != HSR_OK) return st;
-    if (cudaGraphLaunch(b->exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    if ((st = batch_exec(b, guard ? 1 : 0, k, &ex)) != HSR_OK) return st;
+    if (cudaGraphLaunch(ex, stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
     b->cur ^= 1;
@@ -1188,15 +1242,8 @@ int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, 
     const Plan &pl = b->plan;
     if (n > pl.n_cap) return HSR_ERR_OVERFLOW;
     if (av.device != b->device || av.n_scenes != b->scenes.size()) return HSR_ERR_INVALID_ARG;
-    for (uint32_t s = 0; s < av.n_scenes; s++) {
+    for (uint32_t s = 0; s < av.n_scenes; s++)
         if (av.scenes[s] != b->scenes[s]) return HSR_ERR_INVALID_ARG;
-        // agents stay inside their scene's box: a camera at one corner sees
-        // the farthest corner at the largest possible distance
-        const hsr_scene_info &in = av.info[s];
-        if (!snap_bound_ok(in.aabb_min, in.aabb_max, in.aabb_min, b->intr.fx, b->intr.fy, b->intr.cx, b->intr.cy,
-                           b->intr.znear))
-            return HSR_ERR_INVALID_ARG;
-    }
     std::vector<uint32_t> soa(n), sorted(agent_idx, agent_idx + n);
     for (uint32_t i = 0; i < n; i++) {
         if (agent_idx[i] >= av.n_agents || actions[i] > HSR_ACTION_TURN_RIGHT) return HSR_ERR_INVALID_ARG;
@@ -1209,34 +1256,19 @@ int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, 
     std::lock_guard<std::mutex> lock(b->mu);
     const int k = b->cur;
     if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
-    if (!b->step_exec[k]) {
-        cudaStream_t cs = nullptr;
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HSR_ERR_CUDA;
-        const Params p = make_params(pl, b->d_desc[k], b->d_scratch, b->intr, b->rgb, b->depth, b->ids);
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, true);
-            e = cudaStreamEndCapture(cs, &b->step_graph[k]);
-            if (er != cudaSuccess) e = er;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->step_exec[k], b->step_graph[k], 0);
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess) {
-            if (b->step_graph[k]) cudaGraphDestroy(b->step_graph[k]);
-            b->step_graph[k] = nullptr;
-            b->step_exec[k] = nullptr;
-            return cuda_status(e);
-        }
-    }
     NoiseReq nr;
     nr.noise = noise;
     StepReq sr;
     sr.state = agent_idx;
     sr.action = actions;
     sr.agents_dev = (uint64_t)(uintptr_t)av.dev;
-    int st = fill_descriptors(pl, b->scenes.data(), soa.data(), nullptr, n, frames, b->intr, b->h_desc[k], nr, &sr);
+    bool guard = false;
+    int st = fill_descriptors(pl, b->scenes.data(), soa.data(), nullptr, n, frames, b->intr, b->h_desc[k], nr, &sr,
+                              nullptr, &guard);
     if (st != HSR_OK) return st;
-    if (cudaGraphLaunch(b->step_exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    if ((st = batch_exec(b, guard ? 3 : 2, k, &ex)) != HSR_OK) return st;
+    if (cudaGraphLaunch(ex, stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
     b->cur ^= 1;
@@ -1260,10 +1292,13 @@ int hsr_batch_render_views(hsr_batch *b, const hsr_view *views, uint32_t n, cons
     if (b->launched[k] && cudaEventSynchronize(b->done[k]) != cudaSuccess) return HSR_ERR_CUDA;
     NoiseReq nr;
     nr.noise = noise;
+    bool guard = false;
     st = fill_descriptors(pl, b->scenes.data(), soa.data(), poses.data(), n, frames.data(), b->intr, b->h_desc[k], nr,
-                          nullptr, outs.data());
+                          nullptr, outs.data(), &guard);
     if (st != HSR_OK) return st;
-    if (cudaGraphLaunch(b->exec[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    if ((st = batch_exec(b, guard ? 1 : 0, k, &ex)) != HSR_OK) return st;
+    if (cudaGraphLaunch(ex, stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
     b->cur ^= 1;
@@ -1484,7 +1519,8 @@ int hsr_device_status(int clear)
 {
     uint32_t flags = 0;
     if (read_device_errors(&flags, clear != 0) != cudaSuccess) return HSR_ERR_CUDA;
-    return (flags & kErrWaitTimeout) ? HSR_ERR_TIMEOUT : HSR_OK;
+    if (flags & kErrWaitTimeout) return HSR_ERR_TIMEOUT;
+    return (flags & kErrRange) ? HSR_ERR_OVERFLOW : HSR_OK;
 }
 
 int hsr_debug_inject_wait_fault(uint32_t extra_bytes)

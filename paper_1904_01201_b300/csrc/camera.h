@@ -1,6 +1,5 @@
-// Camera setup of one view (step a1): the world-to-eye matrix of a pose, the
-// world-space culling planes of its frustum, and the bound that keeps its
-// snapped coordinates in range. Compiled for the host (descriptor fill) and
+// Camera setup of one view (step a1): the world-to-eye matrix of a pose and
+// the world-space culling planes of its frustum. Compiled for the host (descriptor fill) and
 // for the device (the actuation pass, which moves agents and rebuilds their
 // cameras without a host round trip); both builds run the same IEEE double
 // operations in the same order (no contraction on either side), so a pose
@@ -19,7 +18,6 @@
 
 namespace hsr {
 
-constexpr double kSnapLimit = 1073741824.0;     // |snapped coordinate| < 2^30
 constexpr double kPlaneMarginPx = 2.0;          // culling planes pushed out by this many pixels
 constexpr double kPlaneMarginDepth = 1e-4;      // and the near / far planes by this many metres
 
@@ -83,11 +81,14 @@ HSR_HD void frustum_planes(const float M[12], double fx, double fy, double cx, d
     }
 }
 
-// Conservative bound on |256 sx| and |256 sy| for a camera at `pos` viewing a
-// scene inside the box [amin, amax]: any vertex (or near-clipped point) has
-// |x_e|, |y_e| <= the distance to the farthest box corner and d >= near.
-HSR_HD bool snap_bound_ok(const float amin[3], const float amax[3], const float pos[3], double fx, double fy,
-                          double cx, double cy, double znear)
+// Whether a view from `pos` of a scene inside the box [amin, amax] keeps
+// every snapped coordinate inside +-2^30 sub-pixels, so that no triangle can
+// need the guard band: any vertex (or near-clipped point) has |x_e|, |y_e| <=
+// the distance R to the farthest box corner and d >= near, hence
+// |256 s| <= 256 (f R / near + |c| + 2). Conservative; a call whose views
+// all pass it shades without the guard-band path.
+HSR_HD bool guard_free(const float amin[3], const float amax[3], const float pos[3], double fx, double fy, double cx,
+                       double cy, double znear)
 {
     double r2 = 0.0;
     for (int c = 0; c < 8; c++) {
@@ -102,8 +103,7 @@ HSR_HD bool snap_bound_ok(const float amin[3], const float amax[3], const float 
     const double R = sqrt(r2) * (1.0 + 1e-6) + 1e-6;
     const double f = fx > fy ? fx : fy;
     const double c = fabs(cx) > fabs(cy) ? fabs(cx) : fabs(cy);
-    const double bound = 256.0 * (f * R / znear + c + 2.0);
-    return bound < kSnapLimit;
+    return 256.0 * (f * R / znear + c + 2.0) < 1073741824.0;
 }
 
 }  // namespace hsr

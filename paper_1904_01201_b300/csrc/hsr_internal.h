@@ -76,19 +76,17 @@ struct alignas(16) View {
     uint32_t agent;            // key of the depth-noise stream
     uint32_t state;            // agent-state slot moved by the actuation pass (step batches)
     uint32_t action;           // action applied to that slot first (hsr_action)
-    uint32_t outputs;          // HSR_OUT_* bits this view writes (with its buffer present)
+    uint32_t outputs;          // HSR_OUT_* bits this view writes (with its buffer present), | kViewGuard
     uint32_t pad_[3];
 };
 
 static_assert(sizeof(View) == 192, "View is 12 x 16 bytes");
 
-// Navigability grid of one scene on the device, with the scene's bounding box
-// (the fixed-point range check of a moved camera).
+// Navigability grid of one scene on the device.
 struct NavDev {
     float x0, z0, cell;
     uint32_t nx, nz, pad_;
     const uint8_t *grid;       // [nz][nx], nonzero = navigable
-    float amin[3], amax[3];
 };
 
 // Device-resident agents: poses, per-scene grids, actuation amounts. Its
@@ -146,7 +144,13 @@ __host__ __device__
 #endif
 inline uint32_t pair_nt(const uint4 &e) { return (e.x >> 27) + 1u; }
 
+// Set in View::outputs by the rasteriser when it emitted a guard-band-clipped
+// triangle for the view; the host writes every view record afresh for each
+// render.
+constexpr uint32_t kViewGuard = 1u << 31;
+
 constexpr uint32_t kErrWaitTimeout = 1u;    // a bounded wait for a bulk copy gave up
+constexpr uint32_t kErrRange = 2u;          // a guard-clipped vertex still left the fixed-point range
 
 struct Params {
     const SceneDev *scenes;    // device array
@@ -182,6 +186,7 @@ struct Params {
     float inv_far;             // 1/far: a noisy inverse depth at or below it reports depth 0
     float fx, fy, cx, cy, znear, zfar;
     float q_far;               // smallest float q with 1/q <= zfar
+    float gx, gy;              // guard planes |x_e| <= gx d, |y_e| <= gy d (2^21 / fx, 2^21 / fy)
     uint32_t small_px;         // per-thread raster when a triangle has at most this many candidate pixels
     uint32_t bin_px;           // bins for triangles with more candidate pixels than this; per-warp queue between
     uint32_t chunk;            // consecutive visible pairs a raster warp takes per step (<= 32)
@@ -242,8 +247,10 @@ struct LaunchCfg {
 // Sets kernel attributes for the current device (call before stream capture).
 cudaError_t prepare_kernels();
 
-// Launches the cull, raster and shade kernels on `stream`.
-cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream);
+// Launches the cull, raster and shade kernels on `stream`; `guard`: some view
+// may snap a vertex beyond +-2^30 sub-pixels (guard_free failed for it), so
+// shading compiles in the guard-band path.
+cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard);
 // Device error flags (kErrWaitTimeout, ...) raised by kernels on the current
 // device since the last clear; waits for the device.
 cudaError_t read_device_errors(uint32_t *flags, bool clear);

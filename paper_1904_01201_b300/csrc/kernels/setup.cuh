@@ -60,6 +60,16 @@ __device__ __forceinline__ int clip_near(const CVert<NA> (&v)[3], float znear, C
     return n;
 }
 
+// Fan sub-triangles of a clipped polygon (near plane or guard band) take the
+// vertex of smallest q as the origin of their depth plane (the first such on
+// ties, in oriented order): the cyclic rotation that puts it first. Their
+// other vertices can sit at q = 1/near or far outside the image, where a
+// plane referenced at them loses the on-screen depth to cancellation.
+__device__ __forceinline__ int min_q_rotation(float q0, float q1, float q2)
+{
+    return (q1 < q0 && q1 <= q2) ? 1 : ((q2 < q0 && q2 < q1) ? 2 : 0);
+}
+
 // A front-facing triangle in oriented (positive-area) order.
 struct Tri2D {
     int X0, Y0, X1, Y1, X2, Y2;
@@ -79,6 +89,133 @@ __device__ __forceinline__ bool orient_cull(int X0, int Y0, float q0, int X1, in
     t.X2 = X1; t.Y2 = Y1; t.q2 = q1;
     t.A = -A;
     return true;
+}
+
+// Orientation of fan sub-triangle (0, f+1, f+2) of a clipped polygon: false
+// when culled; else its vertex indices in oriented order, rotated to the
+// min-q origin, and the triangle.
+__device__ __forceinline__ bool clipped_fan_tri(const int *X, const int *Y, const float *q, int f, int (&ix)[3],
+                                                Tri2D &t)
+{
+    const int i1 = f + 1, i2 = f + 2;
+    const long long A = (long long)(X[i1] - X[0]) * (long long)(Y[i2] - Y[0]) -
+                        (long long)(Y[i1] - Y[0]) * (long long)(X[i2] - X[0]);
+    if (A >= 0) return false;
+    const int o[3] = {0, i2, i1};
+    const int r = min_q_rotation(q[o[0]], q[o[1]], q[o[2]]);
+    ix[0] = o[r];
+    ix[1] = o[r == 2 ? 0 : r + 1];
+    ix[2] = o[r == 0 ? 2 : r - 1];
+    t.X0 = X[ix[0]]; t.Y0 = Y[ix[0]]; t.q0 = q[ix[0]];
+    t.X1 = X[ix[1]]; t.Y1 = Y[ix[1]]; t.q1 = q[ix[1]];
+    t.X2 = X[ix[2]]; t.Y2 = Y[ix[2]]; t.q2 = q[ix[2]];
+    t.A = -A;
+    return true;
+}
+
+// Guard band (reading; the paper states no rasterisation rule): a
+// (near-clipped) polygon with a snapped coordinate at or beyond +-2^30
+// sub-pixels is clipped, Sutherland-Hodgman, against the eye-space planes
+// x_e >= -gx d, x_e <= gx d, y_e >= -gy d, y_e <= gy d in that order
+// (gx = 2^21 / fx, gy = 2^21 / fy: 2^29 sub-pixels either side of the
+// principal point). Plane distances are fma(g, d, +-x); a crossing edge is
+// cut from its endpoint b nearer the cut (the inside one when
+// s_in <= -s_out, else the outside one): t = s_b / (s_b - s_r),
+// p = fma(t, p_r - p_b, p_b) for x, y, d and the attributes. The choice
+// depends only on the edge's two endpoints, so the two triangles sharing an
+// edge cut it at the same point, and no cut is computed against a far
+// endpoint's rounding. Out of line: few triangles ever take it.
+constexpr int kMaxClipVerts = 8;
+
+// A near-clipped polygon passed by value to the out-of-line guard-band
+// functions (their callers keep no hot state in memory for them).
+template <int NA>
+struct ClipPoly {
+    CVert<NA> v[4];
+    int n;
+};
+
+// The camera constants the guard band needs, by value (a kernel's parameter
+// block passed by reference to an out-of-line function would be copied to
+// local memory in every thread).
+struct GuardCam {
+    float gx, gy, fx, fy, cx, cy;
+};
+
+template <int NA>
+__device__ __forceinline__ int clip_guard(const ClipPoly<NA> &in, float gx, float gy, CVert<NA> (&out)[kMaxClipVerts])
+{
+    CVert<NA> a[kMaxClipVerts], b[kMaxClipVerts];
+    int na = in.n;
+    for (int k = 0; k < in.n; k++) a[k] = in.v[k];
+    for (int pl = 0; pl < 4; pl++) {
+        const float g = pl < 2 ? gx : gy;
+        float dist[kMaxClipVerts];
+        for (int k = 0; k < na; k++) {
+            const float c = pl < 2 ? a[k].xe : a[k].ye;
+            dist[k] = __fmaf_rn(g, a[k].d, (pl & 1) ? -c : c);
+        }
+        int nb = 0;
+        for (int k = 0; k < na; k++) {
+            const int k1 = k + 1 == na ? 0 : k + 1;
+            const bool ain = dist[k] >= 0.f, bin = dist[k1] >= 0.f;
+            if (ain) b[nb++] = a[k];
+            if (ain != bin) {
+                const int ii = ain ? k : k1, io = ain ? k1 : k;
+                const bool from_in = dist[ii] <= -dist[io];
+                const CVert<NA> &pb = a[from_in ? ii : io];
+                const CVert<NA> &pr = a[from_in ? io : ii];
+                const float sb = dist[from_in ? ii : io], sr = dist[from_in ? io : ii];
+                const float t = __fdiv_rn(sb, __fsub_rn(sb, sr));
+                CVert<NA> o;
+                o.xe = __fmaf_rn(t, __fsub_rn(pr.xe, pb.xe), pb.xe);
+                o.ye = __fmaf_rn(t, __fsub_rn(pr.ye, pb.ye), pb.ye);
+                o.d = __fmaf_rn(t, __fsub_rn(pr.d, pb.d), pb.d);
+                o.gid = 0xFFFFFFFFu;
+#pragma unroll
+                for (int c = 0; c < NA; c++) o.a[c] = __fmaf_rn(t, __fsub_rn(pr.a[c], pb.a[c]), pb.a[c]);
+                b[nb++] = o;
+            }
+        }
+        na = nb;
+        for (int k = 0; k < na; k++) a[k] = b[k];
+        if (na == 0) break;
+    }
+    for (int k = 0; k < na; k++) out[k] = a[k];
+    return na;
+}
+
+// Guard clip, projection and the oriented, min-q-rotated fan of a clipped
+// polygon: writes up to 6 sub-triangles to out (their vertex indices into
+// the clipped polygon to ix when non-null) and returns their count, or -1
+// if a clipped vertex still leaves the fixed-point range (not reachable
+// within the documented input limits). Out of line: few triangles take it.
+template <int NA>
+__device__ __noinline__ int guard_fan(const ClipPoly<NA> poly, const GuardCam cam, Tri2D *out,
+                                      CVert<NA> *gout)
+{
+    CVert<NA> g[kMaxClipVerts];
+    const int ng = clip_guard<NA>(poly, cam.gx, cam.gy, g);
+    int X[kMaxClipVerts], Y[kMaxClipVerts];
+    float q[kMaxClipVerts];
+    bool in_range = true;
+    for (int k = 0; k < ng; k++)
+        in_range &= project_snap(g[k].xe, g[k].ye, g[k].d, cam.fx, cam.fy, cam.cx, cam.cy, q[k], X[k], Y[k]);
+    if (!in_range) return -1;
+    int m = 0;
+    for (int f = 0; f + 2 < ng; f++) {
+        int ix[3];
+        Tri2D t;
+        if (!clipped_fan_tri(X, Y, q, f, ix, t)) continue;
+        out[m] = t;
+        if (gout) {
+            gout[3 * m] = g[ix[0]];
+            gout[3 * m + 1] = g[ix[1]];
+            gout[3 * m + 2] = g[ix[2]];
+        }
+        m++;
+    }
+    return m;
 }
 
 // Plane of q over the snapped vertices, relative to vertex 0:

@@ -176,8 +176,8 @@ __device__ __forceinline__ void interp(const Tri2D &t, bool narrow, int Px, int 
 // log2 of the larger texel-space length of the uv derivative along x and
 // along y, from the exact derivatives of the perspective-correct weights
 // w_k = E_k q_k (one pixel is 256 sub-pixel steps of each edge function).
-__device__ __forceinline__ float lod_lambda(const SceneDev &S, const Tri2D &t, int Px, int Py, const float *a0,
-                                            const float *a1, const float *a2)
+__device__ __forceinline__ float lod_lambda(uint32_t atlas_w, uint32_t atlas_h, const Tri2D &t, int Px, int Py,
+                                            const float *a0, const float *a1, const float *a2)
 {
     const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
     const long long e1 = (long long)(t.X0 - t.X2) * (Py - t.Y2) - (long long)(t.Y0 - t.Y2) * (Px - t.X2);
@@ -197,7 +197,7 @@ __device__ __forceinline__ float lod_lambda(const SceneDev &S, const Tri2D &t, i
     const float gx0 = __fmul_rn(__fmaf_rn(-l0, sx, x0), r), gy0 = __fmul_rn(__fmaf_rn(-l0, sy, y0), r);
     const float gx1 = __fmul_rn(__fmaf_rn(-l1, sx, x1), r), gy1 = __fmul_rn(__fmaf_rn(-l1, sy, y1), r);
     const float gx2 = __fmul_rn(__fmaf_rn(-l2, sx, x2), r), gy2 = __fmul_rn(__fmaf_rn(-l2, sy, y2), r);
-    const float aw = (float)S.atlas_w, ah = (float)S.atlas_h;
+    const float aw = (float)atlas_w, ah = (float)atlas_h;
     const float ux = __fmul_rn(__fmaf_rn(gx0, a0[0], __fmaf_rn(gx1, a1[0], __fmul_rn(gx2, a2[0]))), aw);
     const float vx = __fmul_rn(__fmaf_rn(gx0, a0[1], __fmaf_rn(gx1, a1[1], __fmul_rn(gx2, a2[1]))), ah);
     const float uy = __fmul_rn(__fmaf_rn(gy0, a0[0], __fmaf_rn(gy1, a1[0], __fmul_rn(gy2, a2[0]))), aw);
@@ -218,7 +218,10 @@ struct ShadeTri {
     uint32_t id;                        // output id
 };
 
-template <int NA>
+// G: the view may hold winners that need the guard band (a snapped vertex
+// at or beyond +-2^30 sub-pixels sends the triangle to the clipping path);
+// views without any (flagged by the rasteriser) skip the range test.
+template <int NA, bool G>
 __device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev &S, const float *M,
                                                 const Params &p, uint32_t tri)
 {
@@ -251,8 +254,14 @@ __device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev
     if (st.clipped) return;
     int X[3], Y[3];
     float q[3];
+    bool in_range = true;
 #pragma unroll
-    for (int k = 0; k < 3; k++) project_snap(v[k].xe, v[k].ye, v[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
+    for (int k = 0; k < 3; k++)
+        in_range &= project_snap(v[k].xe, v[k].ye, v[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
+    if (G && !in_range) {      // guard band: the clipping path
+        st.clipped = true;
+        return;
+    }
     // a winning fragment exists, so the triangle is front facing (its area
     // is negative): orient_cull's order, vertices 1 and 2 swapped
     st.t.X0 = X[0]; st.t.Y0 = Y[0]; st.t.q0 = q[0];
@@ -268,20 +277,21 @@ __device__ __forceinline__ void build_shade_tri(ShadeTri<NA> &st, const SceneDev
     }
 }
 
-// Near-clipped triangle: rebuild the clipped polygon and find the fan
-// sub-triangle whose fragment at P has inverse depth qk.
+// The fan sub-triangle (0, f+1, f+2) of a near-clipped polygon (at most 4
+// vertices: f = 0, 1) that covers P, by the rasteriser's orientation and
+// coverage rule: its perspective-correct attributes and level of detail. At
+// most one covers P: two front-facing sub-triangles (0, 1, 2) and (0, 2, 3)
+// lie on opposite sides of their shared edge 0-2, which the top-left rule
+// gives to one of them, so coverage alone names the sub-triangle that
+// produced the pixel's fragment.
 template <int NA>
-__device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M, const Params &p, const uint4 &T,
-                                              int Px, int Py, float qk, float (&attr)[3], float &lambda)
+__device__ __forceinline__ bool shade_fan(const SceneDev &S, const CVert<NA> (&poly)[4], const int (&X)[4],
+                                          const int (&Y)[4], const float (&q)[4], int np, int Px, int Py,
+                                          float (&attr)[3], float &lambda)
 {
-    CVert<NA> v[3];
-    load_tri<NA>(S, M, T, v);
-    CVert<NA> poly[4];
-    const int np = clip_near<NA>(v, p.znear, poly);
-    int X[4], Y[4];
-    float q[4];
-    for (int k = 0; k < np; k++) project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
-    for (int f = 0; f + 2 < np; f++) {
+#pragma unroll
+    for (int f = 0; f < 2; f++) {
+        if (f + 2 >= np) break;
         Tri2D t;
         if (!orient_cull(X[0], Y[0], q[0], X[f + 1], Y[f + 1], q[f + 1], X[f + 2], Y[f + 2], q[f + 2], t)) continue;
         const long long e0 = (long long)(t.X2 - t.X1) * (Py - t.Y1) - (long long)(t.Y2 - t.Y1) * (Px - t.X1);
@@ -291,18 +301,76 @@ __device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M,
         const int b1 = edge_bias(t.X2, t.Y2, t.X0, t.Y0);
         const int b2 = edge_bias(t.X0, t.Y0, t.X1, t.Y1);
         if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
-        float pa, pb;
-        depth_plane(t, pa, pb);
-        const float qq = plane_q(pa, pb, t.q0, Px - t.X0, Py - t.Y0, tri_qlo(t), tri_qhi(t));
-        if (__float_as_uint(qq) != __float_as_uint(qk)) continue;
         // oriented order is (poly 0, poly f+2, poly f+1)
         interp<NA>(t, false, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a, attr);
         if constexpr (NA == 2)
             if (S.sample_mode == HSR_SAMPLE_TRILINEAR)
-                lambda = lod_lambda(S, t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a);
+                lambda = lod_lambda(S.atlas_w, S.atlas_h, t, Px, Py, poly[0].a, poly[f + 2].a, poly[f + 1].a);
         return true;
     }
     return false;
+}
+
+// The guard-band search: the fan sub-triangle of the guard-clipped polygon
+// (up to six) whose fragment at P has inverse depth qk (the rasteriser's
+// coverage and min-q plane), its attributes and level of detail.
+template <int NA>
+__device__ __forceinline__ bool shade_guard_fan(const SceneDev &S, const ClipPoly<NA> &poly, const GuardCam &cam,
+                                                int Px, int Py, float qk, float (&attr)[3], float &lambda)
+{
+    Tri2D t[kMaxClipVerts - 2];
+    CVert<NA> v[3 * (kMaxClipVerts - 2)];
+    const int m = guard_fan<NA>(poly, cam, t, v);
+    for (int k = 0; k < m; k++) {
+        const Tri2D &s = t[k];
+        const long long e0 = (long long)(s.X2 - s.X1) * (Py - s.Y1) - (long long)(s.Y2 - s.Y1) * (Px - s.X1);
+        const long long e1 = (long long)(s.X0 - s.X2) * (Py - s.Y2) - (long long)(s.Y0 - s.Y2) * (Px - s.X2);
+        const long long e2 = (long long)(s.X1 - s.X0) * (Py - s.Y0) - (long long)(s.Y1 - s.Y0) * (Px - s.X0);
+        const int b0 = edge_bias(s.X1, s.Y1, s.X2, s.Y2);
+        const int b1 = edge_bias(s.X2, s.Y2, s.X0, s.Y0);
+        const int b2 = edge_bias(s.X0, s.Y0, s.X1, s.Y1);
+        if (((e0 - b0) | (e1 - b1) | (e2 - b2)) < 0) continue;
+        float pa, pb;
+        depth_plane(s, pa, pb);
+        const float qq = plane_q(pa, pb, s.q0, Px - s.X0, Py - s.Y0, tri_qlo(s), tri_qhi(s));
+        if (__float_as_uint(qq) != __float_as_uint(qk)) continue;
+        interp<NA>(s, false, Px, Py, v[3 * k].a, v[3 * k + 1].a, v[3 * k + 2].a, attr);
+        if constexpr (NA == 2)
+            if (S.sample_mode == HSR_SAMPLE_TRILINEAR)
+                lambda = lod_lambda(S.atlas_w, S.atlas_h, s, Px, Py, v[3 * k].a, v[3 * k + 1].a, v[3 * k + 2].a);
+        return true;
+    }
+    return false;
+}
+
+// Clipped triangle: rebuild the near-clipped polygon and find the fan
+// sub-triangle that produced P's fragment (inverse depth qk); with G, a
+// polygon beyond the fixed-point range is clipped to the guard band first.
+template <int NA, bool G>
+__device__ __forceinline__ bool shade_clipped(const SceneDev &S, const float *M, const Params &p, const uint4 &T,
+                                              int Px, int Py, float qk, float (&attr)[3], float &lambda)
+{
+    CVert<NA> v[3];
+    load_tri<NA>(S, M, T, v);
+    CVert<NA> poly[4];
+    const int np = clip_near<NA>(v, p.znear, poly);
+    int X[4], Y[4];
+    float q[4];
+    bool in_range = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (k < np)
+            in_range &= project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
+    if constexpr (G) {
+        if (!in_range) {
+            ClipPoly<NA> cp;
+#pragma unroll
+            for (int k = 0; k < 4; k++) cp.v[k] = poly[k];
+            cp.n = np;
+            return shade_guard_fan<NA>(S, cp, GuardCam{p.gx, p.gy, p.fx, p.fy, p.cx, p.cy}, Px, Py, qk, attr, lambda);
+        }
+    }
+    return shade_fan<NA>(S, poly, X, Y, q, np, Px, Py, attr, lambda);
 }
 
 template <int NA>
@@ -345,8 +413,9 @@ __device__ __forceinline__ float noisy_depth(float sigma, uint32_t k0, uint32_t 
     return qn > inv_far ? __frcp_rn(qn) : 0.0f;
 }
 
-// Shade one pixel given its key; `st` caches the last triangle's setup.
-template <int NA>
+// Shade one pixel given its key; `st` caches the last triangle's setup (G:
+// the view may hold winners that need the guard band).
+template <int NA, bool G>
 __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S, const float *M, const Params &p,
                                             int px, int py, unsigned long long key, uint32_t &rgb, float &depth,
                                             uint32_t &id, bool colour)
@@ -365,7 +434,7 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
         id = S.tri[tri].w;
         return;
     }
-    if (tri != st.tri) build_shade_tri<NA>(st, S, M, p, tri);
+    if (tri != st.tri) build_shade_tri<NA, G>(st, S, M, p, tri);
     id = st.id;
     const int Px = 256 * px + 128, Py = 256 * py + 128;
     float a[3] = {0.f, 0.f, 0.f};
@@ -373,11 +442,12 @@ __device__ __forceinline__ void shade_pixel(ShadeTri<NA> &st, const SceneDev &S,
     if (!st.clipped) {
         interp<NA>(st.t, st.narrow, Px, Py, st.a[0], st.a[1], st.a[2], a);
         if constexpr (NA == 2)
-            if (S.sample_mode == HSR_SAMPLE_TRILINEAR) lambda = lod_lambda(S, st.t, Px, Py, st.a[0], st.a[1], st.a[2]);
+            if (S.sample_mode == HSR_SAMPLE_TRILINEAR)
+                lambda = lod_lambda(S.atlas_w, S.atlas_h, st.t, Px, Py, st.a[0], st.a[1], st.a[2]);
         rgb = shade_colour<NA>(S, a, lambda);
     } else {
-        rgb = shade_clipped<NA>(S, M, p, __ldg(S.tri + tri), Px, Py, qk, a, lambda) ? shade_colour<NA>(S, a, lambda)
-                                                                                  : 0u;
+        rgb = shade_clipped<NA, G>(S, M, p, __ldg(S.tri + tri), Px, Py, qk, a, lambda) ? shade_colour<NA>(S, a, lambda)
+                                                                                      : 0u;
     }
 }
 

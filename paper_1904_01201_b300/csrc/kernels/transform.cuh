@@ -13,7 +13,9 @@ namespace hsr {
 
 // Per meshlet vertex, cached in shared memory for the warp that owns the
 // meshlet, split so that the common path reads one 16-byte record:
-//   hot  — snapped X, Y and q (valid when d >= near), and d;
+//   hot  — snapped X, Y and q, and d; q = 0 marks a vertex that is in front
+//          of the near plane or whose snap leaves the fixed-point range (its
+//          triangles take the clipping path);
 //   cold — eye-space x, y and the caller vertex index (near-clip path only).
 struct alignas(16) EyeHot {
     int X, Y;
@@ -34,16 +36,21 @@ __device__ __forceinline__ void eye_transform(const float *M, float x, float y, 
     d = -ze;
 }
 
-// Projection and snap of a point with d >= near (> 0). The caller guarantees
-// |256 sx|, |256 sy| < 2^30 (checked per call on the host).
-__device__ __forceinline__ void project_snap(float xe, float ye, float d, float fx, float fy, float cx,
-                                             float cy, float &q, int &X, int &Y)
+// Projection and snap of a point with d >= near (> 0). Returns false when a
+// snapped coordinate would lie at or beyond +-2^30 sub-pixels (or is not a
+// number): such a triangle is clipped to the guard band first (setup.cuh).
+// Near 2^30 floats are multiples of 64, so testing the product before
+// rounding decides exactly as testing rint of it.
+__device__ __forceinline__ bool project_snap(float xe, float ye, float d, float fx, float fy, float cx, float cy,
+                                             float &q, int &X, int &Y)
 {
     q = __frcp_rn(d);
     const float sx = __fmaf_rn(fx, __fmul_rn(xe, q), cx);
     const float sy = __fmaf_rn(-fy, __fmul_rn(ye, q), cy);
-    X = __float2int_rn(__fmul_rn(sx, 256.0f));
-    Y = __float2int_rn(__fmul_rn(sy, 256.0f));
+    const float fsx = __fmul_rn(sx, 256.0f), fsy = __fmul_rn(sy, 256.0f);
+    X = __float2int_rn(fsx);
+    Y = __float2int_rn(fsy);
+    return fabsf(fsx) < 1073741824.0f && fabsf(fsy) < 1073741824.0f;
 }
 
 }  // namespace hsr

@@ -17,7 +17,11 @@
 //    (about 8 bytes per output pixel per view plus 48 bytes per meshlet per
 //    view, plus 192 bytes per view) is rejected with HSR_ERR_OVERFLOW;
 //  * the host-side descriptors are staged in a fixed 1 MiB host buffer
-//    (at most ~6500 views per call);
+//    (192 bytes per view after a 768-byte header: at most 5,457 views per
+//    call; more return HSR_ERR_OVERFLOW). That buffer is ordinary pageable memory,
+//    copied to the device with cudaMemcpyAsync under a process-wide lock, so
+//    the copy has finished reading it when the call returns and the call may
+//    wait for the stream's earlier work;
 //  * every GPU that loads the library keeps the 32 MiB array until the
 //    process exits;
 //  * all calls share the array: two calls whose work overlaps on the GPU
@@ -40,8 +44,9 @@ namespace hsr {
 bool host_camera_matrix(const hsr_pose &pose, float M[12]);
 bool host_intrinsics_ok(const hsr_intrinsics *in);
 float host_far_threshold(float zfar);
+float host_guard_g(float f);
+bool host_guard_free(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in);
 void host_view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32_t H, float planes[24]);
-bool host_snap_in_range(const hsr_scene *s, const hsr_pose &pose, const hsr_intrinsics &in);
 const SceneDev &host_scene_dev(const hsr_scene *s);
 
 constexpr size_t kNoAllocScratchBytes = 32ull << 20;
@@ -68,7 +73,7 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
                                           const hsr_intrinsics *intr, uint32_t width, uint32_t height, uint8_t *rgb,
                                           float *depth, uint32_t *ids, void *cuda_stream)
 {
-    if (!scene || !poses || n == 0 || !rgb || !depth) return HSR_ERR_INVALID_ARG;
+    if (!scene || !poses || n == 0 || !(rgb || depth || ids)) return HSR_ERR_INVALID_ARG;
     if (width == 0 || height == 0 || width > 4096 || height > 4096) return HSR_ERR_INVALID_ARG;
     if (!host_intrinsics_ok(intr)) return HSR_ERR_INVALID_ARG;
     const SceneDev &sd = host_scene_dev(scene);
@@ -119,21 +124,23 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     hdr[17] = (uint32_t)items;      // work items
     hdr[18] = 1;                    // slots in use
     View *hv = reinterpret_cast<View *>(h + off_views);
+    const uint32_t outputs = (rgb ? HSR_OUT_RGB : 0u) | (depth ? HSR_OUT_DEPTH : 0u) | (ids ? HSR_OUT_IDS : 0u);
+    bool guard = false;
     for (uint32_t i = 0; i < n; i++) {
         View &v = hv[i];
         std::memset(&v, 0, sizeof(View));
         if (!host_camera_matrix(poses[i], v.M)) return HSR_ERR_INVALID_ARG;
-        if (!host_snap_in_range(scene, poses[i], *intr)) return HSR_ERR_INVALID_ARG;
+        guard |= !host_guard_free(scene, poses[i], *intr);
         host_view_planes(v.M, *intr, width, height, v.planes);
         for (int k = 0; k < 3; k++) v.pos[k] = poses[i].pos[k];
         v.scene = 0;
         v.frame = i;
         v.agent = i;
-        v.outputs = HSR_OUT_RGB | HSR_OUT_DEPTH | HSR_OUT_IDS;
+        v.outputs = outputs;
     }
-    // Pageable source: the copy has consumed `h` when this call returns.
+    // Pageable source: the copy has consumed `h` when this call returns. The
+    // z-buffer needs no preset: the culling kernel clears every active view's.
     if (cudaMemcpyAsync(d, h, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HSR_ERR_CUDA;
-    if (cudaMemsetAsync(d + off_z, 0xFF, (size_t)zbytes, stream) != cudaSuccess) return HSR_ERR_CUDA;
 
     Params p{};
     p.vis_count = reinterpret_cast<uint32_t *>(d);
@@ -160,6 +167,14 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.znear = intr->znear; p.zfar = intr->zfar;
     p.q_far = host_far_threshold(intr->zfar);
     p.inv_far = (float)(1.0 / (double)intr->zfar);
+    p.gx = host_guard_g(intr->fx);
+    p.gy = host_guard_g(intr->fy);
+    // the bounded-wait test hook and the diagnostic counters, as in
+    // hsr_render (neither allocates here); the large-triangle bins stay off
+    // (big_rec null: no scratch for them), so every large triangle takes
+    // the per-warp queue
+    p.fault_tx = debug_fault_tx();
+    p.stats = stage_stats_buffer();
     const LaunchCfg cfg = default_launch_cfg(items, (uint64_t)n * width * height);
     p.small_px = cfg.small_px < 32 ? cfg.small_px : 32;
     p.chunk = cfg.chunk > 0 ? (cfg.chunk < 32 ? cfg.chunk : 32) : 1;
@@ -172,5 +187,5 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.n_phases = cfg.n_phases;
     p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
     p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
-    return launch_render(p, cfg, stream) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+    return launch_render(p, cfg, stream, guard) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
 }

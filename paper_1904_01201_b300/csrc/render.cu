@@ -123,6 +123,10 @@ __device__ __forceinline__ int meshlet_backfacing(const Params &p, const SceneDe
     if (!(hneed > 0.f)) return 1;
     const float g = fmaxf(fabsf(xc) + rx, fabsf(yc) + ry) / dlo;
     const float f = fmaxf(p.fx, p.fy), c = fmaxf(fabsf(p.cx), fabsf(p.cy));
+    // a box that may project beyond 2^20 pixels may hold triangles clipped
+    // to the guard band (from 2^22 pixels), whose sub-triangles the bound
+    // below does not cover: keep it
+    if (!(f * g + c < 1048576.f)) return 1;
     const float eps_e = 6.f * 5.9604645e-8f * (3.f * S.coord_max + 1.7320508f * cmax);
     const float eta = 0.5f + 256.f * (f * (1.f + g) * eps_e / dlo + 4.f * 5.9604645e-8f * (f * g + c));
     const float emax = 256.f * f * (1.f + g) * lmax * 2.f / dlo;
@@ -466,14 +470,15 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
 #pragma unroll
     for (int i = 0; i < 12; i++) M[i] = __ldg(p.views[view].M + i);
 
-    // K1: transform + snap this meshlet's vertices
+    // K1: transform + snap this meshlet's vertices (q = 0: near-clipped or
+    // beyond the fixed-point range, handled by the clipping path)
     for (uint32_t v = lane; v < nv; v += 32) {
         const float4 P = st.vert[v];
         EyeHot h;
         float xe, ye;
         eye_transform(M, P.x, P.y, P.z, xe, ye, h.d);
         if (h.d >= zn) {
-            project_snap(xe, ye, h.d, p.fx, p.fy, p.cx, p.cy, h.q, h.X, h.Y);
+            if (!project_snap(xe, ye, h.d, p.fx, p.fy, p.cx, p.cy, h.q, h.X, h.Y)) h.q = 0.f;
         } else {
             h.q = 0.f;
             h.X = h.Y = 0;
@@ -494,11 +499,12 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
         const bool all_far = a.d > zf && b.d > zf && cc.d > zf;
         if (!all_near && !all_far) {
             Tri2D t;
-            if (a.d >= zn && b.d >= zn && cc.d >= zn) {
+            if (a.q > 0.f && b.q > 0.f && cc.q > 0.f) {
                 if (orient_cull(a.X, a.Y, a.q, b.X, b.Y, b.q, cc.X, cc.Y, cc.q, t))
                     emit_tri(t, id, p, zbuf, bigq, bign, view, phase, &sf);
             } else {
-                // near-clipped: eye-space positions again from the staged vertices
+                // clipping path: eye-space positions again from the staged
+                // vertices, near clip, then the guard band if a snap is out of range
                 const uint32_t li[3] = {ia, ib, ic};
                 CVert<0> v[3];
 #pragma unroll
@@ -511,11 +517,29 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
                 const int np = clip_near<0>(v, zn, poly);
                 int X[4], Y[4];
                 float q[4];
+                bool in_range = true;
                 for (int k = 0; k < np; k++)
-                    project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k], Y[k]);
-                for (int f = 0; f + 2 < np; f++)
-                    if (orient_cull(X[0], Y[0], q[0], X[f + 1], Y[f + 1], q[f + 1], X[f + 2], Y[f + 2], q[f + 2], t))
-                        emit_tri(t, id, p, zbuf, bigq, bign, view, phase);
+                    in_range &= project_snap(poly[k].xe, poly[k].ye, poly[k].d, p.fx, p.fy, p.cx, p.cy, q[k], X[k],
+                                             Y[k]);
+                if (in_range) {
+                    for (int f = 0; f + 2 < np; f++) {
+                        int ix[3];
+                        if (clipped_fan_tri(X, Y, q, f, ix, t)) emit_tri(t, id, p, zbuf, bigq, bign, view, phase);
+                    }
+                } else {
+                    // guard band (out of line); a vertex still out of range
+                    // after it (not reachable within the documented input
+                    // limits) drops the triangle and raises kErrRange
+                    ClipPoly<0> cp;
+                    for (int k = 0; k < 4; k++) cp.v[k] = poly[k];
+                    cp.n = np;
+                    Tri2D gt[kMaxClipVerts - 2];
+                    const int ng = guard_fan<0>(cp, GuardCam{p.gx, p.gy, p.fx, p.fy, p.cx, p.cy}, gt, nullptr);
+                    if (ng < 0) atomicOr(&g_device_err, kErrRange);
+                    // this view's shading needs the guard-band path
+                    if (ng > 0) atomicOr(const_cast<uint32_t *>(&p.views[view].outputs), kViewGuard);
+                    for (int k = 0; k < ng; k++) emit_tri(gt[k], id, p, zbuf, bigq, bign, view, phase);
+                }
             }
         }
     }
@@ -869,7 +893,7 @@ cudaError_t launch_mip_down(const uint32_t *src, uint32_t w, uint32_t h, uint32_
 }
 
 // --------------------------------------------------------------------- shade
-template <int NA>
+template <int NA, bool G>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
                                            uint32_t frame, uint32_t agent, uint32_t outputs)
 {
@@ -913,7 +937,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
         float dep[K];
 #pragma unroll
         for (int k = 0; k < K; k++)
-            shade_pixel<NA>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k], out_rgb != nullptr);
+            shade_pixel<NA, G>(st, S, M, p, (int)(x0 + k), (int)y, key[k], rgb[k], dep[k], id[k], out_rgb != nullptr);
         if (sigma > 0.f && out_depth) {
             const uint32_t k0 = p.dyn[4], k1 = p.dyn[5];
 #pragma unroll
@@ -961,6 +985,12 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
     }
 }
 
+// Shading of one render call. G = false when the host's bound proves that no
+// view of the call can snap a vertex beyond +-2^30 sub-pixels (no guard-band
+// path compiled in: the common case); G = true otherwise. A view the
+// rasteriser flagged for the guard band in a G = false launch would mean
+// that bound failed: it is reported (kErrRange) and shaded without it.
+template <bool G>
 __global__ void __launch_bounds__(kShadeThreads, 8) shade_kernel(const Params p, uint32_t view0)
 {
     __shared__ float sM[12];
@@ -977,14 +1007,15 @@ __global__ void __launch_bounds__(kShadeThreads, 8) shade_kernel(const Params p,
     }
     __syncthreads();
     const uint32_t outputs = s_outputs;
+    if (!G && (outputs & kViewGuard) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&g_device_err, kErrRange);
     if (!(outputs & HSR_OUT_RGB))
-        shade_rows<0>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<0, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else if (sS.color_mode == kColorTexture)
-        shade_rows<2>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<2, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else if (sS.color_mode == kColorVertex)
-        shade_rows<3>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<3, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else
-        shade_rows<0>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<0, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
 }
 
 constexpr size_t kRasterSmem = kRasterWarps * (2 * sizeof(MeshletStage) + kMeshletVerts * sizeof(EyeHot)) +
@@ -1106,7 +1137,7 @@ cudaError_t prepare_kernels()
     return set_raster_smem_attr(dev);
 }
 
-cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream)
+cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1178,10 +1209,14 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         std::min<uint32_t>((quads + kShadeThreads * per_thread - 1) / (kShadeThreads * per_thread), 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
-        shade_kernel<<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+        if (guard)
+            shade_kernel<true><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+        else
+            shade_kernel<false><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+
     mark(3, stream);
     if (g_timing) g_ev_recorded = true;
     return cudaSuccess;

@@ -159,9 +159,11 @@ def test_invalid_arguments_on_device():
     assert hsr.hsr_render(h.handle, good, intr, 4097, 16, out["rgb"], out["depth"]) == hsr.HSR_ERR_INVALID_ARG
     bad_i = Intrinsics(8, 8, 8, 8, 0.0, 10.0)
     assert hsr.hsr_render(h.handle, good, bad_i, 16, 16, out["rgb"], out["depth"]) == hsr.HSR_ERR_INVALID_ARG
-    # projection could leave +-2^30 sub-pixels: tiny near plane, huge focal length
-    guard = Intrinsics(4000, 4000, 8, 8, 1e-6, 10.0)
-    assert hsr.hsr_render(h.handle, good, guard, 16, 16, out["rgb"], out["depth"]) == hsr.HSR_ERR_INVALID_ARG
+    # principal point beyond 2^16 pixels, near plane below 2^-20 m
+    assert hsr.hsr_render(h.handle, good, Intrinsics(8, 8, 70000, 8, 0.01, 10.0), 16, 16, out["rgb"],
+                          out["depth"]) == hsr.HSR_ERR_INVALID_ARG
+    assert hsr.hsr_render(h.handle, good, Intrinsics(8, 8, 8, 8, 1e-7, 10.0), 16, 16, out["rgb"],
+                          out["depth"]) == hsr.HSR_ERR_INVALID_ARG
     # a later call still works
     assert hsr.hsr_render(h.handle, good, intr, 16, 16, out["rgb"], out["depth"], out["ids"]) == hsr.HSR_OK
     torch.cuda.synchronize()

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from paper_1904_01201_b300.workloads import Scene, Intrinsics, make_room, random_poses, pinhole_90
-from tests.tiny import identity_pose, screen_intr, screen_to_world, scene_from_tris, grid_scene
+from tests.tiny import identity_pose, screen_intr, screen_to_world, scene_from_tris, grid_scene, random_tiny_scene
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 BG = 0xFFFFFFFF
@@ -507,15 +507,6 @@ def brute_force(scene, pose, intr, W, H, R=None, delta=2.0 ** -7):
             "spread": spread.reshape(H, W)}
 
 
-def _random_tiny_scene(rng, T):
-    tris = []
-    for _ in range(T):
-        c = rng.uniform([-2, -2, -5], [2, 2, 0.3])
-        tri = c + rng.normal(scale=rng.uniform(0.05, 1.5), size=(3, 3))
-        tris.append(tri)
-    return scene_from_tris(tris, front=False)
-
-
 @pytest.mark.parametrize("block", range(4))
 def test_brute_force_ray_casting(oracle_mod, block):
     rng = np.random.default_rng(100 + block)
@@ -523,7 +514,7 @@ def test_brute_force_ray_casting(oracle_mod, block):
     for trial in range(n_trials):
         W, H = int(rng.integers(8, 40)), int(rng.integers(8, 40))
         T = int(rng.integers(1, 51))
-        sc = _random_tiny_scene(rng, T)
+        sc = random_tiny_scene(rng, T)
         axis = rng.normal(size=3)
         ang = float(rng.uniform(-0.6, 0.6))
         R = _rodrigues(axis, ang)
@@ -701,7 +692,7 @@ def test_guard_band_random_scenes_vs_ray_casting(oracle_mod, block):
     for trial in range(60):
         W, H = int(rng.integers(8, 40)), int(rng.integers(8, 40))
         T = int(rng.integers(4, 40))
-        sc = _random_tiny_scene(rng, T)
+        sc = random_tiny_scene(rng, T)
         f = float(rng.uniform(0.4, 1.2)) * W
         intr = Intrinsics(f, f * float(rng.uniform(0.7, 1.4)), W / 2 + float(rng.uniform(-2, 2)),
                           H / 2 + float(rng.uniform(-2, 2)), float(10 ** rng.uniform(-6, -5)), 6.0)

@@ -67,3 +67,14 @@ def grid_scene(corners, n, m, jitter=0.0, rng=None):
     flip = np.einsum("ij,ij->i", nrm, -a) < 0
     idx[flip, 1], idx[flip, 2] = idx[flip, 2].copy(), idx[flip, 1].copy()
     return Scene(xyz=xyz.astype(np.float32), idx=idx.astype(np.uint32))
+
+
+def random_tiny_scene(rng, T):
+    """T random triangles around the origin camera (centres in a box reaching
+    behind it, sizes from 5 cm to 1.5 m), unoriented."""
+    tris = []
+    for _ in range(T):
+        c = rng.uniform([-2, -2, -5], [2, 2, 0.3])
+        tri = c + rng.normal(scale=rng.uniform(0.05, 1.5), size=(3, 3))
+        tris.append(tri)
+    return scene_from_tris(tris, front=False)
