@@ -5,8 +5,12 @@ Default workload (N=1): the 1M-triangle synthetic house with a 4096^2 RGBA8
 atlas, 64 agents at random navigable poses, 256x256 RGB + depth — one step
 renders all 64 views in one batched launch. `--mode plain` renders the same
 views one agent per launch. The batched step is one replay of a
-graph-captured persistent batch (hsr_batch_render). `--impl reference` times the CPU oracle (the
-reference arm: there is no runnable code of the paper).
+graph-captured persistent batch (hsr_batch_render). The default run (one
+GPU) adds sub-records for the rest of the metric: the 128^2 batching
+workload (8 scenes, 1,024 agents), the 2M-triangle 512^2 workload, and
+serving at 10k and 50k requests/s with p50/p99 latency (`--no-sub` skips
+them). `--impl reference` times the CPU oracle (the reference arm: there is
+no runnable code of the paper) on the view sequence cpu_baseline renders.
 
 Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the
 path has no exchange step); value is the sum of all ranks' frames over the
@@ -218,23 +222,61 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(wk, n_frames: int, min_seconds: float = 10.0, seconds_cap: float = 30.0):
-    """The oracle, as it stands, on a bounded sample of the workload's views:
-    at least n_frames views and min_seconds of CPU work, at most seconds_cap."""
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo), or the platform's."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def cpu_chunks(wk, size: int):
+    """The view sequence the CPU legs render: the workload's views in order,
+    cycling, in chunks of up to `size` consecutive views of one scene (one
+    oracle call each)."""
+    soa = wk["soa"]
+    i = 0
+    while True:
+        s = int(soa[i])
+        sel = [j for j in range(i, min(i + size, len(soa))) if soa[j] == s]
+        yield s, sel
+        i = (sel[-1] + 1) % len(soa)
+
+
+def cpu_baseline(wk, n_frames: int, min_seconds: float = 10.0, seconds_cap: float = 30.0,
+                 single_seconds: float = 3.0):
+    """The oracle, as it stands, on a bounded sample of the workload's views
+    (the sequence of cpu_chunks, as the reference arm renders it): at least
+    n_frames views and min_seconds of CPU work on every host core, at most
+    seconds_cap; then one view at a time on one thread for single_seconds."""
     import oracle
     cores = os.cpu_count() or 1
-    poses, soa = wk["poses"], wk["soa"]
+    poses = wk["poses"]
     done, t0 = 0, time.perf_counter()
-    i = 0
-    while time.perf_counter() - t0 < seconds_cap and not (done >= n_frames and time.perf_counter() - t0 >= min_seconds):
-        s = int(soa[i % len(soa)])
-        sel = [j for j in range(i, min(i + cores, len(soa))) if soa[j] == s] or [i % len(soa)]
+    for s, sel in cpu_chunks(wk, cores):
         oracle.render(wk["scenes"][s], poses[sel], wk["intr"], wk["W"], wk["H"], nthreads=cores, ids=wk["ids"])
         done += len(sel)
-        i = (sel[-1] + 1) % len(soa)
+        el = time.perf_counter() - t0
+        if el >= seconds_cap or (done >= n_frames and el >= min_seconds):
+            break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} of the workload's views rendered by the CPU oracle on {cores} threads in {dt:.1f} s"}
+    one, t1 = 0, time.perf_counter()
+    for s, sel in cpu_chunks(wk, 1):
+        oracle.render(wk["scenes"][s], poses[sel], wk["intr"], wk["W"], wk["H"], nthreads=1, ids=wk["ids"])
+        one += 1
+        if time.perf_counter() - t1 >= single_seconds:
+            break
+    dt1 = time.perf_counter() - t1
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{done} of the workload's views, in order from the first, rendered by the CPU oracle on "
+                      f"{cores} threads in {dt:.1f} s",
+            "single_thread": {"value": one / dt1, "unit": UNIT, "threads": 1,
+                              "sample": f"{one} views, in order from the first, on one thread in {dt1:.1f} s"}}
 
 
 # ----------------------------------------------------------------- arms
@@ -244,15 +286,15 @@ def run_reference(args, wk):
         return None
     import oracle
     cores = os.cpu_count() or 1
-    n = min(len(wk["soa"]), max(1, cores))
     for _ in range(args.warmup):
         oracle.render(wk["scenes"][int(wk["soa"][0])], wk["poses"][:1], wk["intr"], wk["W"], wk["H"], nthreads=1,
                       ids=wk["ids"])
+    # each step: the next chunk of the view sequence cpu_baseline renders
+    chunks = cpu_chunks(wk, cores)
     t0 = time.perf_counter()
     frames = 0
     for k in range(args.steps):
-        s = int(wk["soa"][0])
-        sel = np.nonzero(wk["soa"] == s)[0][:n]
+        s, sel = next(chunks)
         oracle.render(wk["scenes"][s], wk["poses"][sel], wk["intr"], wk["W"], wk["H"], nthreads=cores, ids=wk["ids"])
         frames += len(sel)
     dt = time.perf_counter() - t0
@@ -260,9 +302,10 @@ def run_reference(args, wk):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/int", "data": "synthetic",
-            "config": {"workload": wk["name"], "sample_views_per_step": int(n), "mode": "cpu-oracle"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{n} views per step of the workload on {cores} threads"},
+            "config": {"workload": wk["name"], "sample_views_per_step": int(cores), "mode": "cpu-oracle"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": f"{frames} of the workload's views, in order from the first (up to {cores} "
+                                       f"per step, as cpu_baseline renders them), on {cores} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -305,12 +348,26 @@ def run_gpu(args, wk):
         return 1
 
     intr_c = hsr.as_intrinsics(wk["intr"])      # converted once, as a caller looping over agents would
+    # each agent's C-ABI arguments (scene, pose, output addresses) prepared
+    # once, as a caller looping over its agents would hold them, so that the
+    # loop times the library's calls rather than the binding's conversions
+    import ctypes
+    lib = hsr.library()
+    poses_c = np.ascontiguousarray(poses, dtype=np.float32)
+    px = W * H
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    plain_args = []
+    for i in range(n):
+        ids_p = None if out.get("ids") is None else ctypes.c_void_p(out["ids"].data_ptr() + 4 * px * i)
+        plain_args.append((ctypes.c_void_p(handles[int(soa[i])].handle),
+                           ctypes.c_void_p(poses_c.ctypes.data + 28 * i), 1, ctypes.byref(intr_c), W, H,
+                           ctypes.c_void_p(out["rgb"].data_ptr() + 3 * px * i),
+                           ctypes.c_void_p(out["depth"].data_ptr() + 4 * px * i), ids_p, sptr))
+    render_c = lib.hsr_render
 
     def step_plain():
-        for i in range(n):
-            h = handles[int(soa[i])]
-            st = hsr.hsr_render(h.handle, poses[i:i + 1], intr_c, W, H, out["rgb"][i:i + 1], out["depth"][i:i + 1],
-                                None if "ids" not in out else out["ids"][i:i + 1], stream)
+        for a in plain_args:
+            st = render_c(*a)
             if st != 0:
                 raise hsr.HsrError(st, "render")
         return n
@@ -385,13 +442,30 @@ def run_gpu(args, wk):
         oms, _, _ = timed(step_oneshot, osteps, False)
         oneshot = {"value": n * osteps / (oms / 1e3), "ms_per_step": oms / osteps}
 
-    # plain one-agent-per-launch path on the same views, for comparison
+    # plain one-agent-per-launch path on the same views, for comparison: its
+    # rate (CUDA events around each step of n calls), the host's time to
+    # issue one call (wall clock over a step, unsynchronised), and one call's
+    # device time (stage timing: first kernel start to last kernel end)
     plain = None
     if args.mode == "batched" and not args.no_plain:
-        pms, _, _ = timed(step_plain, max(3, args.steps // 10), False)
         psteps = max(3, args.steps // 10)
-        plain = {"value": n * psteps / (pms / 1e3), "ms_per_step": pms / psteps,
-                 "launches_per_step": n}
+        pms, _, _ = timed(step_plain, psteps, False)
+        torch.cuda.synchronize()
+        th = time.perf_counter()
+        step_plain()
+        host_ms = (time.perf_counter() - th) * 1e3 / n
+        torch.cuda.synchronize()
+        hsr.hsr_set_stage_timing(True)
+        dev_ms = []
+        for a in plain_args[:64]:
+            st = render_c(*a)
+            if st != 0:
+                raise hsr.HsrError(st, "render")
+            dev_ms.append(hsr.hsr_get_stage_timing()["total"])
+        hsr.hsr_set_stage_timing(False)
+        plain = {"value": n * psteps / (pms / 1e3), "ms_per_step": pms / psteps, "launches_per_step": n,
+                 "host_ms_per_call": host_ms, "device_ms_per_call": statistics.mean(dev_ms),
+                 "device_bound_value": 1e3 / statistics.mean(dev_ms)}
 
     # end to end through the C-ABI with host buffers: every step renders from
     # host poses (the view descriptors go up inside the call) and copies its
@@ -500,6 +574,26 @@ def run_gpu(args, wk):
     if world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(wk, args.cpu_frames)
     return res
+
+
+def run_subrecords(args):
+    """The rest of the metric in the default run, each with its own clocks:
+    the 128^2 batching workload (8 scenes, 1,024 agents; batched vs plain),
+    the 2M-triangle 512^2 workload with ids, and serving at 10k and 50k
+    requests/s (p50 / p99 latency)."""
+    import copy
+    out = {}
+    for name in ("batching", "large"):
+        a = copy.copy(args)
+        a.workload, a.no_cpu = name, True
+        r = run_gpu(a, make_workload(name, args.seed))
+        if r is not None:
+            r.pop("cpu_baseline", None)
+            out[name] = r
+    a = copy.copy(args)
+    a.rates = "10000,50000"
+    out["serving"] = run_serving(a)
+    return out
 
 
 def run_serving(args):
@@ -707,6 +801,8 @@ def main():
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="house: skip the batching, large and serving sub-records of the default run")
     ap.add_argument("--cpu-frames", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--agents", type=int, default=0, help="render only the first N agents (profiling)")
@@ -726,6 +822,9 @@ def main():
         wk["soa"], wk["poses"] = wk["soa"][:k], wk["poses"][:k]
         wk["name"] += f"-first{k}"
     res = run_reference(args, wk) if args.impl == "reference" else run_gpu(args, wk)
+    if res is not None and args.impl != "reference" and args.workload == "house" and not args.agents \
+            and not args.no_sub and dist_env()[1] == 1:
+        res["sub"] = run_subrecords(args)
     if res is not None:
         print(json.dumps(res), flush=True)
 

@@ -123,6 +123,9 @@ float guard_g(float f)
     return num / f;
 }
 
+// Page-locked staging of one-shot calls' descriptors, per host thread: a
+// ring of kStagingSlots buffers, so that a thread may run that many calls
+// ahead of the device before it waits for the upload of an earlier one.
 struct Staging {
     void *host = nullptr;
     size_t cap = 0;
@@ -135,9 +138,74 @@ struct Staging {
         if (done) cudaEventDestroy(done);
     }
 };
-thread_local Staging g_staging;
+constexpr int kStagingSlots = 4;
+struct StagingRing {
+    Staging slot[kStagingSlots];
+    int next = 0;
+};
+thread_local StagingRing g_staging;
 
 constexpr uint64_t kMaxScratchBytes = 2ull << 30;
+
+// Device scratch of one-shot calls, kept per host thread and reused by its
+// next call instead of being allocated and freed every call (descriptors
+// and scratch of a call up to kReuseBytes; larger calls take stream-ordered
+// allocations). A call on another stream than the previous one first waits,
+// on the device, for the previous call's work (the `done` event), so two
+// calls never share the buffer at the same time.
+constexpr size_t kReuseBytes = 256ull << 20;
+struct CallScratch {
+    int device = -1;
+    unsigned char *d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    cudaStream_t last = nullptr;
+    bool used = false;
+    ~CallScratch()
+    {
+        if (used && done) cudaEventSynchronize(done);
+        if (d) cudaFree(d);
+        if (done) cudaEventDestroy(done);
+    }
+    // A buffer of at least `bytes` on the current device, ordered after the
+    // previous call's use on `stream`; nullptr if it cannot be had.
+    unsigned char *acquire(size_t bytes, cudaStream_t stream)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+        if (dev != device || cap < bytes) {
+            if (used && done && cudaEventSynchronize(done) != cudaSuccess) return nullptr;
+            if (d) cudaFree(d);
+            if (done) cudaEventDestroy(done);
+            d = nullptr;
+            done = nullptr;
+            cap = 0;
+            used = false;
+            device = dev;
+            const size_t want = std::max<size_t>(bytes, 64ull << 20);
+            if (cudaMalloc(&d, want) != cudaSuccess) {
+                d = nullptr;
+                return nullptr;
+            }
+            if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaFree(d);
+                d = nullptr;
+                return nullptr;
+            }
+            cap = want;
+        }
+        if (used && stream != last && cudaStreamWaitEvent(stream, done, 0) != cudaSuccess) return nullptr;
+        return d;
+    }
+    // The call's work is queued on `stream`.
+    bool release(cudaStream_t stream)
+    {
+        last = stream;
+        used = true;
+        return cudaEventRecord(done, stream) == cudaSuccess;
+    }
+};
+thread_local CallScratch g_call_scratch;
 
 void view_planes(const float M[12], const hsr_intrinsics &in, uint32_t W, uint32_t H, float planes[24])
 {
@@ -545,7 +613,8 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     Plan pl;
     make_plan(pl, n_scenes, n, width, height, list_entries, items, cfg);
 
-    Staging &st = g_staging;
+    Staging &st = g_staging.slot[g_staging.next];
+    g_staging.next = (g_staging.next + 1) % kStagingSlots;
     if (st.pending) {
         if (cudaEventSynchronize(st.done) != cudaSuccess) return HSR_ERR_CUDA;
         st.pending = false;
@@ -565,13 +634,26 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
                                   vr.outputs, &guard);
     if (status != HSR_OK) return status;
 
+    // descriptors and scratch: the thread's reusable buffer, or stream-ordered
+    // allocations for calls beyond its size
+    const size_t desc_al = al256(pl.desc_bytes);
     void *dbuf = nullptr, *sbuf = nullptr;
-    cudaError_t e = cudaMallocAsync(&dbuf, pl.desc_bytes, stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMallocAsync(&sbuf, pl.scratch_bytes, stream);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(dbuf, stream);
-        return cuda_status(e);
+    CallScratch &cs = g_call_scratch;
+    const bool reuse = desc_al + pl.scratch_bytes <= kReuseBytes;
+    cudaError_t e = cudaSuccess;
+    if (reuse) {
+        unsigned char *buf = cs.acquire(desc_al + pl.scratch_bytes, stream);
+        if (!buf) return HSR_ERR_OOM;
+        dbuf = buf;
+        sbuf = buf + desc_al;
+    } else {
+        e = cudaMallocAsync(&dbuf, pl.desc_bytes, stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaMallocAsync(&sbuf, pl.scratch_bytes, stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(dbuf, stream);
+            return cuda_status(e);
+        }
     }
     const Params p = make_params(pl, static_cast<unsigned char *>(dbuf), static_cast<unsigned char *>(sbuf), *intr,
                                  rgb, depth, ids);
@@ -579,6 +661,10 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
     if (e == cudaSuccess) st.pending = true;
     if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream, guard);
+    if (reuse) {
+        if (!cs.release(stream) && e == cudaSuccess) e = cudaErrorUnknown;
+        return e == cudaSuccess ? HSR_OK : cuda_status(e);
+    }
     cudaError_t e1 = cudaFreeAsync(sbuf, stream);
     cudaError_t e2 = cudaFreeAsync(dbuf, stream);
     if (e != cudaSuccess) return cuda_status(e);

@@ -1137,11 +1137,24 @@ cudaError_t prepare_kernels()
     return set_raster_smem_attr(dev);
 }
 
+// SM count of a device, queried once per device.
+static cudaError_t device_sms(int dev, int *sms)
+{
+    static int cache[64] = {};
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) {
+        *sms = cache[dev];
+        return cudaSuccess;
+    }
+    const cudaError_t e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) cache[dev] = *sms;
+    return e;
+}
+
 cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = device_sms(dev, &sms);
     if (e != cudaSuccess) return e;
     mark(0, stream);
     if (p.stats) {

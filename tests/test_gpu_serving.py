@@ -174,3 +174,53 @@ def test_action_requests_need_attached_agents(scenes):
         srv.attach_agents(ag)
     srv.close()
     ag.close()
+
+
+def test_serving_workload_settings(oracle_mod):
+    """The serving configuration as bench.py runs it: the 8 batching scenes
+    resident (0.2M-2M triangles), 1,024 device-resident agents, action
+    requests at 64/128/256/512 (weights 0.2/0.4/0.3/0.1) in bursts, micro-
+    batches of up to 64 views on 3 streams, 300 us wait, 4 GiB of
+    framebuffers. Every result equals the one-shot render of the pose its
+    action reached (the oracle's actuation in submission order), bit for bit;
+    two results per resolution against the oracle."""
+    res = (64, 128, 256, 512)
+    sc = wl.batching_scenes(0)
+    hs = [hsr.SceneHandle(s) for s in sc]
+    agents, soa = serve.make_agents(sc, hs, 1024, seed=0)
+    navs = [wl.navmap(s, 0.05) for s in sc]
+    poses0 = agents.poses()
+    srv = serve.Server(hs, res=res, weights=(0.2, 0.4, 0.3, 0.1), fb_bytes=4 << 30, max_batch=64, n_streams=3,
+                       max_wait_us=300)
+    srv.attach_agents(agents)
+    n = 800
+    req = serve.make_action_requests(n, 1024, res=res, seed=3)
+    for k in range(0, n, 100):                 # bursts: later ones arrive while earlier ones render
+        srv.submit(req[k:k + 100])
+    got = _collect(srv, n, False)
+    cur = poses0.copy()
+    reached = []
+    for i, rq in enumerate(req):
+        a = int(rq["agent"])
+        cur[a], _ = oracle_mod.actuate(cur[a], int(rq["action"]), navs[int(soa[a])])
+        reached.append(cur[a].copy())
+        st, fr = got[i]
+        assert st == 0, i
+        r = int(rq["res"])
+        ref = hsr.render(hs[int(soa[a])], cur[a][None], wl.pinhole_90(r, r), r, r, ids=False)
+        torch.cuda.synchronize()
+        assert torch.equal(fr["rgb"], ref["rgb"][0]), i
+        assert torch.equal(fr["depth"], ref["depth"][0]), i
+    assert np.array_equal(agents.poses().view(np.uint32), cur.view(np.uint32))
+    for r in res:
+        for i in [j for j, rq in enumerate(req) if int(rq["res"]) == r][:2]:
+            a = int(req[i]["agent"])
+            o = oracle_mod.render(sc[int(soa[a])], reached[i][None], wl.pinhole_90(r, r), r, r, ids=False)
+            assert np.array_equal(got[i][1]["depth"].cpu().numpy().view(np.uint32), o["depth"][0].view(np.uint32))
+            assert np.abs(got[i][1]["rgb"].cpu().numpy().astype(int) - o["rgb"][0].astype(int)).max() <= 1
+    st = srv.stats()
+    assert st["completed"] == n and st["rejected"] == 0
+    srv.close()
+    agents.close()
+    for h in hs:
+        h.close()
