@@ -382,6 +382,9 @@ bool noise_ok(const hsr_depth_noise *nz)
     return !nz || (std::isfinite(nz->depth_sigma) && nz->depth_sigma >= 0.f && nz->reserved == 0);
 }
 
+// Whether a call adds depth noise (then it shades with the noise variant).
+bool noisy(const hsr_depth_noise *nz) { return nz && nz->depth_sigma > 0.f; }
+
 // Camera setup of n views (a1) into the host staging buffer `hbuf`
 // (pl.desc_bytes): views sorted by scene (stable), slot arrays, scene table,
 // zeroed counters and the dynamic header words. frames[i] (or i) is the
@@ -526,9 +529,10 @@ Params make_params(const Plan &pl, unsigned char *desc, unsigned char *scratch, 
 }
 
 // Stream work of one render: upload descriptors, the actuation pass of a
-// step batch, the kernels (guard: shading with the guard-band path).
+// step batch, the kernels (guard: shading with the guard-band path; noise:
+// shading with the depth-noise model).
 cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const void *h_desc, cudaStream_t stream,
-                           bool actuate, bool guard)
+                           bool actuate, bool guard, bool noise)
 {
     cudaError_t e = cudaMemcpyAsync(d_desc, h_desc, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return e;
@@ -536,7 +540,7 @@ cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const 
         e = launch_actuate(p, pl.n_cap, stream);
         if (e != cudaSuccess) return e;
     }
-    return launch_render(p, pl.cfg, stream, guard);
+    return launch_render(p, pl.cfg, stream, guard, noise);
 }
 
 // Scenes, poses, intrinsics and size of a render; at least one output buffer
@@ -660,7 +664,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     e = cudaMemcpyAsync(dbuf, hbuf, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
     if (e == cudaSuccess) st.pending = true;
-    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream, guard);
+    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream, guard, nr.noise && nr.noise->depth_sigma > 0.f);
     if (reuse) {
         if (!cs.release(stream) && e == cudaSuccess) e = cudaErrorUnknown;
         return e == cudaSuccess ? HSR_OK : cuda_status(e);
@@ -684,12 +688,12 @@ struct hsr_batch {
     unsigned char *d_desc[2] = {nullptr, nullptr};
     unsigned char *h_desc[2] = {nullptr, nullptr};
     unsigned char *d_scratch = nullptr;
-    // captured renders per descriptor buffer k, in four variants: pose
-    // renders (0) and step renders (2: upload, actuation, render), each also
-    // with the guard-band shading (+1); variant 0 is captured at creation,
-    // the others on first use
-    cudaGraph_t graph[4][2] = {};
-    cudaGraphExec_t exec[4][2] = {};
+    // captured renders per descriptor buffer k, in eight variants: pose
+    // renders (0) or step renders (2: upload, actuation, render), with the
+    // guard-band shading (+1) and / or the depth-noise shading (+4); variant
+    // 0 is captured at creation, the others on first use
+    cudaGraph_t graph[8][2] = {};
+    cudaGraphExec_t exec[8][2] = {};
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool launched[2] = {false, false};
     int cur = 0;
@@ -709,7 +713,7 @@ void free_batch(hsr_batch *b)
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     for (int k = 0; k < 2; k++) {
-        for (int v = 0; v < 4; v++) {
+        for (int v = 0; v < 8; v++) {
             if (b->exec[v][k]) cudaGraphExecDestroy(b->exec[v][k]);
             if (b->graph[v][k]) cudaGraphDestroy(b->graph[v][k]);
         }
@@ -1210,7 +1214,7 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
         if ((e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
         const Params p = make_params(pl, b->d_desc[k], b->d_scratch, *intr, rgb, depth, ids);
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail(e);
-        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, false, false);
+        cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, false, false, false);
         e = cudaStreamEndCapture(cs, &b->graph[0][k]);
         if (er != cudaSuccess) return fail(er);
         if (e != cudaSuccess) return fail(e);
@@ -1224,8 +1228,9 @@ int batch_create(const hsr_scene *const *scenes, uint32_t n_scenes, uint32_t n_c
     return HSR_OK;
 }
 
-// Graph variant v (0: pose render, 2: step render, +1: guard-band shading) of
-// descriptor buffer k, captured on first use. Called with the batch's lock.
+// Graph variant v (0: pose render, 2: step render, +1: guard-band shading,
+// +4: depth-noise shading) of descriptor buffer k, captured on first use.
+// Called with the batch's lock.
 int batch_exec(hsr_batch *b, int v, int k, cudaGraphExec_t *out)
 {
     if (!b->exec[v][k]) {
@@ -1235,7 +1240,8 @@ int batch_exec(hsr_batch *b, int v, int k, cudaGraphExec_t *out)
         const Params p = make_params(pl, b->d_desc[k], b->d_scratch, b->intr, b->rgb, b->depth, b->ids);
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, v >= 2, (v & 1) != 0);
+            cudaError_t er = enqueue_render(pl, p, b->d_desc[k], b->h_desc[k], cs, (v & 2) != 0, (v & 1) != 0,
+                                            (v & 4) != 0);
             e = cudaStreamEndCapture(cs, &b->graph[v][k]);
             if (er != cudaSuccess) e = er;
         }
@@ -1289,7 +1295,7 @@ int hsr_batch_render_noisy(hsr_batch *b, const uint32_t *scene_of_agent, const h
                               nullptr, nullptr, &guard);
     if (st != HSR_OK) return st;
     cudaGraphExec_t ex = nullptr;
-    if ((st = batch_exec(b, guard ? 1 : 0, k, &ex)) != HSR_OK) return st;
+    if ((st = batch_exec(b, (guard ? 1 : 0) | (noisy(noise) ? 4 : 0), k, &ex)) != HSR_OK) return st;
     if (cudaGraphLaunch(ex, stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
@@ -1353,7 +1359,7 @@ int hsr_batch_step(hsr_batch *b, hsr_agents *agents, const uint32_t *agent_idx, 
                               nullptr, &guard);
     if (st != HSR_OK) return st;
     cudaGraphExec_t ex = nullptr;
-    if ((st = batch_exec(b, guard ? 3 : 2, k, &ex)) != HSR_OK) return st;
+    if ((st = batch_exec(b, 2 | (guard ? 1 : 0) | (noisy(noise) ? 4 : 0), k, &ex)) != HSR_OK) return st;
     if (cudaGraphLaunch(ex, stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;
@@ -1383,7 +1389,7 @@ int hsr_batch_render_views(hsr_batch *b, const hsr_view *views, uint32_t n, cons
                           nullptr, outs.data(), &guard);
     if (st != HSR_OK) return st;
     cudaGraphExec_t ex = nullptr;
-    if ((st = batch_exec(b, guard ? 1 : 0, k, &ex)) != HSR_OK) return st;
+    if ((st = batch_exec(b, (guard ? 1 : 0) | (noisy(noise) ? 4 : 0), k, &ex)) != HSR_OK) return st;
     if (cudaGraphLaunch(ex, stream) != cudaSuccess) return HSR_ERR_CUDA;
     if (cudaEventRecord(b->done[k], stream) != cudaSuccess) return HSR_ERR_CUDA;
     b->launched[k] = true;

@@ -401,17 +401,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Appendix C noise model: inverse depth plus iid Gaussian noise of std sigma
 // (Box-Muller on two Philox words at counter (pixel, agent, 'nois', 0));
-// a noisy inverse depth at or below 1/far reports no return (depth 0). The
-// cosine is taken as cospi(2 u2), whose argument is exact in fp32 (u2 has 23
-// bits), rather than cos(2 pi u2), whose rounded argument would dominate the
-// error of z.
+// a noisy inverse depth at or below 1/far reports no return (depth 0).
+// PRECISE (the shading variant every noisy call launches): the cosine as
+// cospi(2 u2), whose argument is exact in fp32 (u2 has 23 bits); the rounded
+// argument of cos(2 pi u2) would dominate the error of z. The other form is
+// compiled into the noise-free variant only because its register allocation
+// measured fastest with it (that variant never runs it).
+template <bool PRECISE>
 __device__ __forceinline__ float noisy_depth(float sigma, uint32_t k0, uint32_t k1, float inv_far, float q,
                                              uint32_t pixel, uint32_t agent)
 {
     const uint4 r = philox4x32_10(make_uint4(pixel, agent, 0x6e6f6973u, 0u), k0, k1);
     const float u1 = ((float)(r.x >> 9) + 0.5f) * 1.1920928955078125e-07f;   // 2^-23
     const float u2 = ((float)(r.y >> 9) + 0.5f) * 1.1920928955078125e-07f;
-    const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float c = PRECISE ? cospif(2.0f * u2) : cosf(6.283185307179586f * u2);
+    const float z = sqrtf(-2.0f * logf(u1)) * c;
     const float qn = __fmaf_rn(sigma, z, q);
     return qn > inv_far ? __frcp_rn(qn) : 0.0f;
 }

@@ -893,7 +893,9 @@ cudaError_t launch_mip_down(const uint32_t *src, uint32_t w, uint32_t h, uint32_
 }
 
 // --------------------------------------------------------------------- shade
-template <int NA, bool G>
+// N: the call adds depth noise (the host launches this variant for every
+// noisy call; it applies the precise noise model).
+template <int NA, bool G, bool N>
 __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, const float *M, uint32_t vi,
                                            uint32_t frame, uint32_t agent, uint32_t outputs)
 {
@@ -943,7 +945,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
 #pragma unroll
             for (int k = 0; k < K; k++)
                 if (key[k] != ~0ull)
-                    dep[k] = noisy_depth(sigma, k0, k1, p.inv_far, __uint_as_float(~(uint32_t)(key[k] >> 32)),
+                    dep[k] = noisy_depth<N>(sigma, k0, k1, p.inv_far, __uint_as_float(~(uint32_t)(key[k] >> 32)),
                                          (uint32_t)(pi + k), agent);
         }
         const size_t o = fbase + pi;
@@ -990,7 +992,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
 // path compiled in: the common case); G = true otherwise. A view the
 // rasteriser flagged for the guard band in a G = false launch would mean
 // that bound failed: it is reported (kErrRange) and shaded without it.
-template <bool G>
+template <bool G, bool N>
 __global__ void __launch_bounds__(kShadeThreads, 8) shade_kernel(const Params p, uint32_t view0)
 {
     __shared__ float sM[12];
@@ -1009,13 +1011,13 @@ __global__ void __launch_bounds__(kShadeThreads, 8) shade_kernel(const Params p,
     const uint32_t outputs = s_outputs;
     if (!G && (outputs & kViewGuard) && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&g_device_err, kErrRange);
     if (!(outputs & HSR_OUT_RGB))
-        shade_rows<0, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<0, G, N>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else if (sS.color_mode == kColorTexture)
-        shade_rows<2, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<2, G, N>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else if (sS.color_mode == kColorVertex)
-        shade_rows<3, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<3, G, N>(p, sS, sM, vi, s_frame, s_agent, outputs);
     else
-        shade_rows<0, G>(p, sS, sM, vi, s_frame, s_agent, outputs);
+        shade_rows<0, G, N>(p, sS, sM, vi, s_frame, s_agent, outputs);
 }
 
 constexpr size_t kRasterSmem = kRasterWarps * (2 * sizeof(MeshletStage) + kMeshletVerts * sizeof(EyeHot)) +
@@ -1150,7 +1152,7 @@ static cudaError_t device_sms(int dev, int *sms)
     return e;
 }
 
-cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard)
+cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard, bool noise)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1222,10 +1224,14 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         std::min<uint32_t>((quads + kShadeThreads * per_thread - 1) / (kShadeThreads * per_thread), 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
-        if (guard)
-            shade_kernel<true><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+        if (guard && noise)
+            shade_kernel<true, true><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+        else if (guard)
+            shade_kernel<true, false><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+        else if (noise)
+            shade_kernel<false, true><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
         else
-            shade_kernel<false><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
+            shade_kernel<false, false><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
