@@ -309,6 +309,27 @@ def run_reference(args, wk):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_reference_other(args):
+    """The reference arm of the serving workload: the oracle's rate over the
+    request mix (cpu_serving). The transfer and semantic workloads time GPU
+    copy paths and a GPU sensor pair that have no CPU counterpart."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    if args.workload != "serving":
+        return {"impl": "reference", "unavailable": f"the {args.workload} workload times GPU transfer paths with no "
+                                                    "CPU counterpart; the oracle arm covers house, room, batching, "
+                                                    "large and serving"}
+    from paper_1904_01201_b300 import workloads as wl
+    cpu = cpu_serving(wl.batching_scenes(args.seed), args)
+    return {"impl": "reference", "metric": "served RGB-D frames/sec with p50/p99 request latency",
+            "value": cpu["value"], "unit": UNIT, "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/int", "data": "synthetic",
+            "config": {"workload": "serving-8scenes-1024agents-mix64-512", "mode": "cpu-oracle"},
+            "cpu_baseline": cpu, "e2e": {"value": cpu["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+
+
 def run_gpu(args, wk):
     import torch
     rank, world, local = dist_env()
@@ -444,16 +465,27 @@ def run_gpu(args, wk):
 
     # plain one-agent-per-launch path on the same views, for comparison: its
     # rate (CUDA events around each step of n calls), the host's time to
-    # issue one call (wall clock over a step, unsynchronised), and one call's
-    # device time (stage timing: first kernel start to last kernel end)
+    # issue one call, and one call's device time (stage timing: first kernel
+    # start to last kernel end). The host time is wall clock over bursts of
+    # at most as many calls as the library has page-locked staging slots,
+    # each burst started on an idle device, so that no call waits for a slot
+    # (a longer unsynchronised run would time the device instead).
     plain = None
     if args.mode == "batched" and not args.no_plain:
         psteps = max(3, args.steps // 10)
         pms, _, _ = timed(step_plain, psteps, False)
-        torch.cuda.synchronize()
-        th = time.perf_counter()
-        step_plain()
-        host_ms = (time.perf_counter() - th) * 1e3 / n
+        burst = 4
+        host_s, host_calls = 0.0, 0
+        for k in range(0, min(n, 256), burst):
+            torch.cuda.synchronize()
+            th = time.perf_counter()
+            for a in plain_args[k:k + burst]:
+                st = render_c(*a)
+                if st != 0:
+                    raise hsr.HsrError(st, "render")
+            host_s += time.perf_counter() - th
+            host_calls += len(plain_args[k:k + burst])
+        host_ms = host_s * 1e3 / host_calls
         torch.cuda.synchronize()
         hsr.hsr_set_stage_timing(True)
         dev_ms = []
@@ -572,27 +604,32 @@ def run_gpu(args, wk):
         res["plain"] = plain
         res["batched_over_plain"] = value / plain["value"]
     if world == 1 and not args.no_cpu:
-        res["cpu_baseline"] = cpu_baseline(wk, args.cpu_frames)
+        res["cpu_baseline"] = cpu_baseline(wk, args.cpu_frames, min_seconds=args.cpu_seconds,
+                                           seconds_cap=3 * args.cpu_seconds,
+                                           single_seconds=max(2.0, args.cpu_seconds / 3))
     return res
 
 
 def run_subrecords(args):
     """The rest of the metric in the default run, each with its own clocks:
-    the 128^2 batching workload (8 scenes, 1,024 agents; batched vs plain),
-    the 2M-triangle 512^2 workload with ids, and serving at 10k and 50k
-    requests/s (p50 / p99 latency)."""
+    the 10k-triangle room at 128^2, the 128^2 batching workload (8 scenes,
+    1,024 agents), the 2M-triangle 512^2 workload with ids (each batched vs
+    plain, with the oracle's rate on a shorter sample of the same views),
+    serving at 10k and 50k requests/s (p50 / p99 latency; the oracle's rate
+    over the request mix), and the frame-transfer strategies at 128^2 RGB-D
+    (1 and 5 renderers, 1 and 64 agents per launch)."""
     import copy
     out = {}
-    for name in ("batching", "large"):
+    for name in ("room", "batching", "large"):
         a = copy.copy(args)
-        a.workload, a.no_cpu = name, True
+        a.workload, a.cpu_seconds = name, min(args.cpu_seconds, 5.0)
         r = run_gpu(a, make_workload(name, args.seed))
         if r is not None:
-            r.pop("cpu_baseline", None)
             out[name] = r
     a = copy.copy(args)
-    a.rates = "10000,50000"
+    a.rates, a.cpu_seconds = "10000,50000", min(args.cpu_seconds, 5.0)
     out["serving"] = run_serving(a)
+    out["transfer"] = run_transfer(args, quick=True)
     return out
 
 
@@ -634,6 +671,7 @@ def run_serving(args):
     if agents is not None:
         agents.close()
     best = max(rows, key=lambda r: r["frames_per_s"])
+    cpu = cpu_serving(scenes, args) if world == 1 and rank == 0 and not args.no_cpu else None
     return {"metric": "served RGB-D frames/sec with p50/p99 request latency", "value": best["frames_per_s"],
             "unit": UNIT, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/int", "data": "synthetic",
@@ -641,7 +679,46 @@ def run_serving(args):
                        "requests": args.serve_requests, "max_batch": args.serve_batch,
                        "streams": args.serve_streams, "max_wait_us": args.serve_wait_us, "fb_bytes": 4 << 30},
             "per_rate": [{k: v for k, v in r.items() if k != "stats"} for r in rows],
-            "clocks": clocks}
+            "clocks": clocks, **({"cpu_baseline": cpu} if cpu else {})}
+
+
+def cpu_serving(scenes, args):
+    """The oracle's rate over the serving request mix: requests of random-
+    walking agents (resolutions 64/128/256/512 at weights 0.2/0.4/0.3/0.1)
+    in arrival order, taken in windows of `window` requests whose requests of
+    one scene and resolution are rendered by one oracle call, on every host
+    core for at least cpu_seconds (at most three times that); then one
+    request at a time on one thread."""
+    import oracle
+    from paper_1904_01201_b300 import serve
+    from paper_1904_01201_b300 import workloads as wl
+    cores = os.cpu_count() or 1
+    req = serve.make_requests(scenes, 4000, seed=args.seed)
+
+    def chunks(window):
+        for i in range(0, len(req), window):
+            w = req[i:i + window]
+            for key in sorted({(int(q["scene"]), int(q["res"])) for q in w}):
+                sel = (w["scene"] == key[0]) & (w["res"] == key[1])
+                yield key[0], key[1], w["pose"][sel]
+
+    def run(window, nthreads, seconds):
+        done, t0 = 0, time.perf_counter()
+        for s, r, poses in chunks(window):
+            oracle.render(scenes[s], poses, wl.pinhole_90(r, r), r, r, nthreads=nthreads, ids=False)
+            done += len(poses)
+            if time.perf_counter() - t0 >= seconds:
+                break
+        return done, time.perf_counter() - t0
+
+    window = 8 * cores
+    done, dt = run(window, cores, args.cpu_seconds)
+    one, dt1 = run(1, 1, max(2.0, args.cpu_seconds / 3))
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{done} requests of the serving mix from its first windows of {window} (arrival order), "
+                      f"by the CPU oracle on {cores} threads in {dt:.1f} s (throughput; no arrival process)",
+            "single_thread": {"value": one / dt1, "unit": UNIT, "threads": 1,
+                              "sample": f"the first {one} requests on one thread in {dt1:.1f} s"}}
 
 
 def run_semantic(args):
@@ -695,7 +772,7 @@ def run_semantic(args):
             "rgbd_frames_per_s": fps_rgbd, "semantic_slowdown": fps_rgbd / fps_sem, "clocks": clocks}
 
 
-def run_transfer(args):
+def run_transfer(args, quick: bool = False):
     """Frame-transfer strategies (Table 2 and the resolution figure beside it):
     frames stay in device memory for a device consumer (GPU->GPU), are copied
     to pinned host memory (GPU->CPU), or copied to the host and back into a
@@ -760,14 +837,14 @@ def run_transfer(args):
     clk = ClockSampler()
     table = []
     for per_launch in (1, 64):
-        for sensor in ("rgb", "rgbd", "rgbds"):
+        for sensor in (("rgbd",) if quick else ("rgb", "rgbd", "rgbds")):
             for strategy in ("gpu-cpu-gpu", "gpu-cpu", "gpu-gpu"):
-                for n_streams in (1, 3, 5):
+                for n_streams in ((1, 5) if quick else (1, 3, 5)):
                     table.append({"res": 128, "sensors": sensor, "transfer": strategy, "renderers": n_streams,
                                   "agents_per_launch": per_launch,
                                   "frames_per_s": measure(128, sensor, strategy, n_streams, per_launch)})
     sweep = []
-    for per_launch in (1, 64):
+    for per_launch in (() if quick else (1, 64)):
         for res in (64, 128, 256, 512):
             for strategy in ("gpu-cpu-gpu", "gpu-cpu", "gpu-gpu"):
                 sweep.append({"res": res, "sensors": "rgbd", "transfer": strategy, "renderers": 1,
@@ -802,8 +879,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
-                    help="house: skip the batching, large and serving sub-records of the default run")
+                    help="house: skip the room, batching, large, serving and transfer sub-records of the default run")
     ap.add_argument("--cpu-frames", type=int, default=256)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="least CPU time of the oracle's all-core sample (at most three times that)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--agents", type=int, default=0, help="render only the first N agents (profiling)")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch configuration")
@@ -811,6 +890,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.impl == "reference" and args.workload in ("serving", "transfer", "semantic"):
+        res = run_reference_other(args)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
     if args.workload in ("serving", "transfer", "semantic"):
         res = {"serving": run_serving, "transfer": run_transfer, "semantic": run_semantic}[args.workload](args)
         if res is not None:

@@ -93,3 +93,43 @@ def test_render_host_matches_device_outputs():
     for b in bs + [nod]:
         b.close()
     h.close()
+
+
+@pytest.mark.parametrize("depth,ids", [(False, False), (True, False), (True, True)])
+def test_transfer_strategies_deliver_the_same_frames(oracle_mod, depth, ids):
+    """The frame hand-offs of the transfer experiment (Table 2): frames left in
+    device memory (GPU->GPU), copied to page-locked host memory (GPU->CPU),
+    and copied on to a separate device buffer (GPU->CPU->GPU), for the colour,
+    colour + depth and colour + depth + semantic sensor sets, queued on a side
+    stream after the render as the benchmark does. Every leg equals the
+    device frames bit for bit; two views against the oracle."""
+    sc = wl.make_house(24, 60_000, 256, semantic=True)
+    h = hsr.SceneHandle(sc)
+    W = H = 96
+    n = 6
+    intr = wl.pinhole_90(W, H)
+    poses = wl.random_poses(sc, n, 41)
+    b = hsr.Batch([h], n, intr, W, H, ids=ids, depth=depth)
+    s = torch.cuda.Stream()
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in b.out.items() if v is not None}
+    back = {k: torch.empty_like(v) for k, v in b.out.items() if v is not None}
+    b.render(poses, stream=s)
+    with torch.cuda.stream(s):
+        for k, dst in host.items():
+            dst.copy_(b.out[k], non_blocking=True)
+        for k, dst in back.items():
+            dst.copy_(host[k], non_blocking=True)
+    s.synchronize()
+    for k in host:
+        dev = b.out[k].cpu()
+        assert torch.equal(host[k], dev), ("gpu-cpu", k)
+        assert torch.equal(back[k].cpu(), dev), ("gpu-cpu-gpu", k)
+    for i in (0, n - 1):
+        o = oracle_mod.render(sc, poses[i:i + 1], intr, W, H, ids=True)
+        assert np.abs(back["rgb"][i].cpu().numpy().astype(int) - o["rgb"][0].astype(int)).max() <= 1
+        if depth:
+            assert np.array_equal(back["depth"][i].cpu().numpy().view(np.uint32), o["depth"][0].view(np.uint32))
+        if ids:
+            assert np.array_equal(back["ids"][i].cpu().numpy().view(np.uint32), o["ids"][0])
+    b.close()
+    h.close()
