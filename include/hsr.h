@@ -486,8 +486,8 @@ HSR_API int hsr_get_stage_stats(uint32_t *counts);
  *   - All calls share the array and it keeps the last call's contents (each
  *     call re-initialises what it needs). Calls whose work overlaps on the
  *     GPU race and corrupt each other's images: order them on one stream.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture on that device.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it for the process.
  */
 HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose *poses, uint32_t n,
                        const hsr_intrinsics *intr, uint32_t width, uint32_t height,

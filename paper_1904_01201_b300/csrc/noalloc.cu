@@ -28,8 +28,7 @@
 //    (different streams, or different host threads without ordering) race
 //    and give wrong images. Serialise them on one stream.
 //  * the first call on each device looks up the array's device address with
-//    cudaGetSymbolAddress (with that device current); make that first call
-//    before any stream capture on that device.
+//    cudaGetSymbolAddress (with that device current) and caches it.
 #include <cstring>
 #include <mutex>
 
