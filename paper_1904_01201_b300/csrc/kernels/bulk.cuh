@@ -83,4 +83,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it on the stream is still
+// running; grid_dependency_wait blocks until that kernel has completed and
+// its memory operations are visible (immediately when there is none), and
+// must precede every access to memory the earlier kernels touch.
+// allow_dependent_launch lets the next such kernel be scheduled once every
+// CTA of this grid has called it or exited.
+__device__ __forceinline__ void grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace hsr

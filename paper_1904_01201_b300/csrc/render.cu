@@ -40,7 +40,7 @@ namespace hsr {
 
 constexpr int kRasterWarps = 8;
 constexpr int kRasterThreads = kRasterWarps * 32;
-constexpr int kBigCap = 2 * kMeshletTris;        // a lane emits at most two sub-triangles
+constexpr int kBigCap = 2 * kMeshletTris;        // two per lane (guard-band ones in rounds)
 // Shading is bound by the latency of its dependent loads (key -> triangle ->
 // vertices -> texels): small CTAs, two pixels per thread and a 64-register
 // bound (8 CTAs, 32 warps per SM) keep the most of them in flight; measured
@@ -137,6 +137,7 @@ __device__ __forceinline__ int meshlet_backfacing(const Params &p, const SceneDe
 
 __global__ void __launch_bounds__(256) cull_kernel_vg(const Params p)
 {
+    allow_dependent_launch();
     // the active views' z-buffers set to empty (~0), 16 bytes per store (the
     // z-buffer starts on a 256-byte boundary); done here, before the raster,
     // so the clear overlaps the culling's record loads and the keys are still
@@ -251,6 +252,7 @@ static_assert(kCullViews <= 32, "one lane per view of a culling item");
 // at most kCullSlots scene slots (cull_kernel_vg otherwise).
 __global__ void __launch_bounds__(256) cull_kernel(const Params p)
 {
+    allow_dependent_launch();
     {
         const size_t n = (size_t)p.dyn[0] * p.width * p.height;
         ulonglong2 *z2 = reinterpret_cast<ulonglong2 *>(p.zbuf);
@@ -441,6 +443,8 @@ __device__ __forceinline__ void emit_tri(const Tri2D &t, uint32_t id, const Para
 // bits; images are at most 4096 rows), grid-stride.
 __global__ void __launch_bounds__(256) big_raster_kernel(const Params p, uint32_t phase)
 {
+    allow_dependent_launch();
+    grid_dependency_wait();
     const int lane = threadIdx.x & 31;
     const uint32_t count = min(p.big_inst_count[phase], p.big_inst_cap);
     const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -487,14 +491,20 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
     }
     __syncwarp();
 
-    // K2 + K4: one triangle per lane
+    // K2 + K4: one triangle per lane. A lane queues at most two large
+    // (sub-)triangles here, so the warp's queue (kBigCap) holds them all; a
+    // guard-band clip can yield up to six, so those are kept and emitted one
+    // per lane per round below, the queue drained after each round.
     SmallFrag sf;
     sf.mask = 0u;
+    uint32_t id = 0;
+    Tri2D gq[kMaxClipVerts - 2];
+    int gn = 0;
     if ((uint32_t)lane < nt) {
         const uint2 mt = st.tri[toff + lane];
         const uint32_t ia = mt.x & 255u, ib = (mt.x >> 8) & 255u, ic = (mt.x >> 16) & 255u;
         const EyeHot a = vh[ia], b = vh[ib], cc = vh[ic];
-        const uint32_t id = mt.y;
+        id = mt.y;
         const bool all_near = a.d < zn && b.d < zn && cc.d < zn;
         const bool all_far = a.d > zf && b.d > zf && cc.d > zf;
         if (!all_near && !all_far) {
@@ -533,12 +543,11 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
                     ClipPoly<0> cp;
                     for (int k = 0; k < 4; k++) cp.v[k] = poly[k];
                     cp.n = np;
-                    Tri2D gt[kMaxClipVerts - 2];
-                    const int ng = guard_fan<0>(cp, GuardCam{p.gx, p.gy, p.fx, p.fy, p.cx, p.cy}, gt, nullptr);
+                    const int ng = guard_fan<0>(cp, GuardCam{p.gx, p.gy, p.fx, p.fy, p.cx, p.cy}, gq, nullptr);
                     if (ng < 0) atomicOr(&g_device_err, kErrRange);
                     // this view's shading needs the guard-band path
                     if (ng > 0) atomicOr(const_cast<uint32_t *>(&p.views[view].outputs), kViewGuard);
-                    for (int k = 0; k < ng; k++) emit_tri(gt[k], id, p, zbuf, bigq, bign, view, phase);
+                    gn = max(ng, 0);
                 }
             }
         }
@@ -556,6 +565,18 @@ __device__ __forceinline__ void process_meshlet(const MeshletStage &st, const Pa
     __syncwarp();
     if (lane == 0) *bign = 0;
     __syncwarp();
+    // guard-band sub-triangles, one per lane per round
+    if (__any_sync(0xFFFFFFFFu, gn > 0)) {
+        for (int gk = 0; __any_sync(0xFFFFFFFFu, gk < gn); gk++) {
+            if (gk < gn) emit_tri(gq[gk], id, p, zbuf, bigq, bign, view, phase);
+            __syncwarp();
+            const uint32_t ng = *bign;
+            for (uint32_t r = 0; r < ng; r++) raster_big_warp(bigq[r], lane, p.q_far, zbuf, (int)p.width);
+            __syncwarp();
+            if (lane == 0) *bign = 0;
+            __syncwarp();
+        }
+    }
 }
 
 // Conservative occlusion test of a meshlet box against the tile-z pyramid of
@@ -616,6 +637,8 @@ __device__ __forceinline__ bool box_occluded(const float *bmin, const float *bma
 // cover 512 contiguous bytes of a row; the four are combined with shuffles.
 __global__ void __launch_bounds__(256) hiz_kernel(const Params p)
 {
+    allow_dependent_launch();
+    grid_dependency_wait();
     const uint32_t per_view = p.hiz_w * p.hiz_h;
     const uint32_t total = p.dyn[0] * per_view * 4u;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ((total + 31) & ~31u);
@@ -648,6 +671,8 @@ __global__ void __launch_bounds__(256) hiz_kernel(const Params p)
 // Coarser pyramid levels of each active view (one block per view).
 __global__ void __launch_bounds__(256) hiz_pyramid_kernel(const Params p)
 {
+    allow_dependent_launch();
+    grid_dependency_wait();
     const uint32_t v = blockIdx.x;
     if (v >= p.dyn[0]) return;
     uint32_t *pyr = p.hiz + (size_t)v * p.hiz_total;
@@ -671,6 +696,8 @@ __global__ void __launch_bounds__(256) hiz_pyramid_kernel(const Params p)
 // pair); the pairs not proven hidden are compacted into the survivor list.
 __global__ void __launch_bounds__(256) occl_kernel(const Params p, uint32_t phase)
 {
+    allow_dependent_launch();
+    grid_dependency_wait();
     const uint32_t count = min(p.vis_count[phase], p.vis_cap);
     const int lane = threadIdx.x & 31;
     const uint32_t rounded = (count + 31u) & ~31u;
@@ -726,6 +753,8 @@ __device__ __forceinline__ void stage_meshlet(MeshletStage &st, uint64_t *bar, c
 // latency sits on the warp's path.
 __global__ void __launch_bounds__(kRasterThreads, 3) raster_kernel(const Params p, uint32_t phase)
 {
+    allow_dependent_launch();
+    grid_dependency_wait();
     // dynamic shared memory per warp: two meshlet stages, the vertex cache and
     // the big-triangle queue (kRasterSmem)
     extern __shared__ __align__(128) unsigned char smem[];
@@ -995,6 +1024,7 @@ __device__ __forceinline__ void shade_rows(const Params &p, const SceneDev &S, c
 template <bool G, bool N>
 __global__ void __launch_bounds__(kShadeThreads, 8) shade_kernel(const Params p, uint32_t view0)
 {
+    grid_dependency_wait();
     __shared__ float sM[12];
     __shared__ SceneDev sS;
     __shared__ uint32_t s_frame, s_agent, s_outputs;
@@ -1139,6 +1169,28 @@ cudaError_t prepare_kernels()
     return set_raster_smem_attr(dev);
 }
 
+// Launch of a kernel that may start while the kernel before it on the stream
+// is finishing (programmatic dependent launch): its CTAs are scheduled once
+// every CTA of that kernel has allowed it, and wait for its completion
+// (grid_dependency_wait) before touching memory, so only the launch latency
+// and CTA start-up overlap.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t stream, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // SM count of a device, queried once per device.
 static cudaError_t device_sms(int dev, int *sms)
 {
@@ -1189,23 +1241,19 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         const uint32_t hiz_blocks = std::min<uint32_t>((hiz_threads + 255) / 256, (uint32_t)sms * 16);
         for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
             if (ph > 0) {
-                hiz_kernel<<<hiz_blocks, 256, 0, stream>>>(p);
-                e = cudaGetLastError();
+                e = launch_dependent(hiz_kernel, dim3(hiz_blocks), dim3(256), 0, stream, p);
                 if (e != cudaSuccess) return e;
-                hiz_pyramid_kernel<<<p.n_views, 256, 0, stream>>>(p);
-                e = cudaGetLastError();
+                e = launch_dependent(hiz_pyramid_kernel, dim3(p.n_views), dim3(256), 0, stream, p);
                 if (e != cudaSuccess) return e;
                 const uint32_t occl_blocks = std::min<uint32_t>((p.vis_cap + 255) / 256, (uint32_t)sms * 16);
-                occl_kernel<<<std::max(occl_blocks, 1u), 256, 0, stream>>>(p, ph);
-                e = cudaGetLastError();
+                e = launch_dependent(occl_kernel, dim3(std::max(occl_blocks, 1u)), dim3(256), 0, stream, p, ph);
                 if (e != cudaSuccess) return e;
             }
-            raster_kernel<<<(uint32_t)sms * cfg.raster_ctas_per_sm, kRasterThreads, kRasterSmem, stream>>>(p, ph);
-            e = cudaGetLastError();
+            e = launch_dependent(raster_kernel, dim3((uint32_t)sms * cfg.raster_ctas_per_sm), dim3(kRasterThreads),
+                                 kRasterSmem, stream, p, ph);
             if (e != cudaSuccess) return e;
             if (p.big_rec) {
-                big_raster_kernel<<<(uint32_t)sms * 8, 256, 0, stream>>>(p, ph);
-                e = cudaGetLastError();
+                e = launch_dependent(big_raster_kernel, dim3((uint32_t)sms * 8), dim3(256), 0, stream, p, ph);
                 if (e != cudaSuccess) return e;
             }
         }
@@ -1224,15 +1272,9 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         std::min<uint32_t>((quads + kShadeThreads * per_thread - 1) / (kShadeThreads * per_thread), 1024);
     for (uint32_t v0 = 0; v0 < p.n_views; v0 += 65535) {
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
-        if (guard && noise)
-            shade_kernel<true, true><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
-        else if (guard)
-            shade_kernel<true, false><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
-        else if (noise)
-            shade_kernel<false, true><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
-        else
-            shade_kernel<false, false><<<dim3(bx, nv), kShadeThreads, 0, stream>>>(p, v0);
-        e = cudaGetLastError();
+        void (*shade)(Params, uint32_t) = guard ? (noise ? shade_kernel<true, true> : shade_kernel<true, false>)
+                                                : (noise ? shade_kernel<false, true> : shade_kernel<false, false>);
+        e = launch_dependent(shade, dim3(bx, nv), dim3(kShadeThreads), 0, stream, p, v0);
         if (e != cudaSuccess) return e;
     }
 

@@ -156,6 +156,79 @@ def test_wide_room_tiny_near_every_path(oracle_mod, small, bin_):
     h.close()
 
 
+def _floor_fan(n=32, half=3.0, y=-1.5, zb=0.5, za=-4.0, spread=2.0):
+    """n floor triangles sharing one base edge behind the camera (x = -half
+    .. half at z = zb) with apexes spread ahead (z = za): n + 2 vertices, so
+    the scene is one meshlet. Every triangle crosses the near plane, and its
+    clip points project far outside the fixed-point range on three sides."""
+    base = [np.array([-half, y, zb]), np.array([half, y, zb])]
+    apex = [np.array([-spread + 2 * spread * i / max(n - 1, 1), y, za]) for i in range(n)]
+    xyz = np.array(base + apex, np.float32)
+    idx = []
+    for i in range(n):
+        t = [0, 1, 2 + i]
+        a, b, c = (xyz[k].astype(np.float64) for k in t)
+        if np.dot(np.cross(b - a, c - a), -a) < 0:         # counter-clockwise seen from the camera
+            t = [0, 2 + i, 1]
+        idx.append(t)
+    sc = Scene(xyz=xyz, idx=np.array(idx, np.uint32))
+    sc.vrgb = (np.arange(3 * (n + 2)) * 37 % 256).astype(np.uint8).reshape(-1, 3)
+    return sc
+
+
+def _guard_subtriangles(sc, intr, oracle_mod):
+    """Sub-triangles the guard band cuts the identity view's triangles into
+    (near clip in float64, then the oracle's guard clip)."""
+    fx, fy, cx, cy, near, _ = [float(v) for v in intr.as_array()]
+    total = 0
+    for t in sc.xyz[sc.idx].astype(np.float64):
+        P = [(v[0], v[1], -v[2]) for v in t]
+        poly = []
+        for k in range(3):
+            a, b = P[k], P[(k + 1) % 3]
+            if a[2] >= near:
+                poly.append(a)
+            if (a[2] >= near) != (b[2] >= near):
+                s = (near - a[2]) / (b[2] - a[2])
+                poly.append(tuple(a[j] + s * (b[j] - a[j]) for j in range(3)))
+        if len(poly) < 3:
+            continue
+        snap = max(max(abs(256 * (fx * x / d + cx)), abs(256 * (-fy * y / d + cy))) for x, y, d in poly)
+        if snap >= 2.0 ** 30:
+            total += max(len(oracle_mod.guard_clip(np.array(poly, np.float32), 2.0 ** 21 / fx, 2.0 ** 21 / fy)) - 2, 0)
+    return total
+
+
+def test_guard_fans_beyond_one_warp_queue(oracle_mod):
+    """One meshlet whose 32 triangles are all cut by the guard band into
+    three sub-triangles each, 96 large ones for one warp: more than the
+    warp's queue holds at once, so they go through it in rounds. Through the
+    per-warp queue (no bins), the bins, and the allocation-free entry point."""
+    sc = _floor_fan()
+    W = H = 1024
+    intr = Intrinsics(512.0, 512.0, 512.0, 512.0, 2e-6, 60.0)
+    assert _guard_subtriangles(sc, intr, oracle_mod) > 64
+    poses = identity_pose()[None]
+    o = oracle_mod.render(sc, poses, intr, W, H)
+    assert (o["ids"] != BG).mean() > 0.25 and len(np.unique(o["ids"])) == 33
+    h = hsr.SceneHandle(sc)
+    for small, bin_ in ((8, 1 << 20), (8, 8)):
+        cfg = hsr.hsr_config(small, bin_, 4, 3, 1, (4.0, 10.0))
+        hsr.hsr_set_tuned_config([h.handle], 1, W, H, True, cfg)
+        _parity(_np(hsr.render(h, poses, intr, W, H, ids=True)), o, f"one-shot {small}/{bin_}")
+        b = hsr.Batch([h], 1, intr, W, H, ids=True)
+        b.render(poses)
+        _parity(_np(b.out), o, f"batch {small}/{bin_}")
+        b.close()
+    hsr.hsr_set_tuned_config([h.handle], 1, W, H, True, None)
+    out = hsr.alloc_outputs(1, W, H)
+    st = hsr.hsr_render_noalloc(h.handle, poses, intr, W, H, out["rgb"], out["depth"], out["ids"])
+    assert st == hsr.HSR_OK, hsr.hsr_status_string(st)
+    _parity(_np(out), o, "noalloc")
+    assert hsr.hsr_device_status(1) == hsr.HSR_OK
+    h.close()
+
+
 def test_huge_fronto_parallel_quad(oracle_mod):
     """A quad at depth D reaching 10^6 m to every side: every pixel covered,
     depth exactly D, as the oracle."""
