@@ -209,9 +209,9 @@ struct Params {
     uint32_t fault_tx;         // test hook: extra bytes each meshlet staging waits for (0 in normal operation)
     uint32_t cull_views;       // views a culling warp item covers (1..16, from the amount of work)
     uint32_t *stats;           // diagnostic counters or null: [0..2] pairs per phase, [3..5] skipped per phase
-    // Tile bins of large triangles: a triangle with more than small_px
-    // candidate pixels is stored once in `big_rec` and binned to every 8x8
-    // tile its pixel range touches (`big_inst`, one list of big_inst_cap
+    // Bins of large triangles: a triangle with more than bin_px candidate
+    // pixels is stored once in `big_rec` and binned as runs of up to 32 rows
+    // of its candidate rectangle (`big_inst`, one list of big_inst_cap
     // entries per phase); big_raster_kernel rasterises the bins after each
     // phase. Null / full bins fall back to the per-warp queue.
     struct BigTri *big_rec;
