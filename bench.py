@@ -172,30 +172,44 @@ def load_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def load_peaks_field(key: str):
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            v = json.load(f).get(key)
+        return None if v is None else float(v)
+    return None
+
+
 def raster_bytes_per_view(scene) -> float:
     """Algorithmic bytes of the raster stage per view: the mesh read once
     (a 12-byte index triple per triangle, 12 bytes of xyz per vertex)."""
     return 12.0 * scene.n_tris + 12.0 * scene.n_verts
 
 
-def recorded_traffic(workload_name: str):
-    """dram bytes per raster launch from a committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def recorded_profile(workload_name: str, key: str):
+    """A per-launch figure (dram_bytes_per_launch, warp_instructions_per_launch)
+    of the raster stage from a committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"raster_kernel_{workload_name}.txt")
     if not os.path.exists(path):
         return None
     vals = {}
     with open(path) as f:
         for line in f:
-            if ":" in line:
+            if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("source_sha256") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def recorded_traffic(workload_name: str):
+    return recorded_profile(workload_name, "dram_bytes_per_launch")
 
 
 def max_over_ranks(ms: float, world: int, device) -> float:
@@ -574,6 +588,19 @@ def run_gpu(args, wk):
     raster_views = n if args.mode == "batched" else 1
     raster_achieved = rview * raster_views / (stages["raster"] / 1e3) / 1e9
     traffic = recorded_traffic(wk["name"]) if args.mode == "batched" else None
+    # the same stage against the instruction-issue roofline: its kernels' warp
+    # instructions per call (ncu, committed summary) over its live time,
+    # against one warp instruction per clock on each SM sub-partition
+    winst = recorded_profile(wk["name"], "warp_instructions_per_launch") if args.mode == "batched" else None
+    issue = None
+    if winst:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or load_peaks_field("sm_max_mhz") or 2032.0
+        ipeak = sms * 4 * mhz * 1e6 / 1e9
+        iach = winst / (stages["raster"] / 1e3) / 1e9
+        issue = {"bound": "alu", "achieved": iach, "peak": ipeak, "unit": "G warp instructions/s", "frac": iach / ipeak,
+                 "warp_instructions_per_launch": winst, "sms": sms, "sm_mhz": mhz,
+                 "what": "raster stage (all its kernels, one render call) over its live time"}
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -584,8 +611,12 @@ def run_gpu(args, wk):
                    "parallelism": f"replicas x{world}", "launch_config": tuned or "default"},
         "roofline": {"bound": "hbm", "achieved": raster_achieved, "peak": peak, "unit": "GB/s",
                      "frac": raster_achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "hsr::raster_kernel", "kernel_ms_per_launch": stages["raster"],
-                     "algorithmic_bytes_per_view": rview, "views_per_launch": raster_views},
+                     "kernel": "raster stage (raster_kernel and big_raster_kernel per phase, tile z, pyramid, "
+                               "occlusion)", "kernel_ms_per_launch": stages["raster"],
+                     "algorithmic_bytes_per_view": rview, "views_per_launch": raster_views,
+                     "dram_gbs": None if traffic is None else traffic / (stages["raster"] / 1e3) / 1e9,
+                     "dram_frac": None if traffic is None else traffic / (stages["raster"] / 1e3) / 1e9 / peak},
+        "roofline_issue": issue,
         "roofline_path": {"bound": "hbm", "achieved": path_achieved, "peak": peak, "unit": "GB/s",
                           "frac": path_achieved / peak, "peak_kind": peak_kind,
                           "what": "whole render call (cull + raster + shade) per step",
