@@ -1100,11 +1100,12 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
             d.atlas_w = atlas_w;
             d.atlas_h = atlas_h;
             d.color_mode = kColorTexture;
-            // the same texels in a texture (the driver's 2D-local layout): the
-            // bilinear footprint comes back from one gather per channel; a
-            // scene whose atlas does not fit a texture samples the linear copy
+            // the same texels in a texture (the driver's 2D-local layout), one
+            // 32-bit channel per texel: the bilinear footprint's four packed
+            // texels come back from one gather; a scene whose atlas does not
+            // fit a texture samples the linear copy
             d.atlas_tex = 0;
-            const cudaChannelFormatDesc cd = cudaCreateChannelDesc<uchar4>();
+            const cudaChannelFormatDesc cd = cudaCreateChannelDesc<unsigned int>();
             if (cudaMallocArray(&s->atlas_array, &cd, atlas_w, atlas_h) == cudaSuccess) {
                 cudaResourceDesc rd{};
                 rd.resType = cudaResourceTypeArray;

@@ -40,16 +40,17 @@ __device__ __forceinline__ uint32_t sample_bilinear(const SceneDev &S, float u, 
     const float gx = __fsub_rn(1.0f, ax), gy = __fsub_rn(1.0f, ay);
     uint32_t out = 0;
     if (S.atlas_tex) {
-        // one gather per channel returns that channel of the footprint
-        // (ix, iy) .. (ix + 1, iy + 1), clamped to the edge: at unnormalised
-        // (ix + 1, iy + 1) the footprint's corner is floor(ix + 1/2) = ix,
-        // half a texel from any rounding boundary; the components come as
-        // x (ix, iy + 1), y (ix + 1, iy + 1), z (ix + 1, iy), w (ix, iy)
-        const float u = (float)(ix + 1), w = (float)(iy + 1);
+        // one gather returns the footprint (ix, iy) .. (ix + 1, iy + 1),
+        // clamped to the edge, as four packed texels (the texture has one
+        // 32-bit channel): at unnormalised (ix + 1, iy + 1) the footprint's
+        // corner is floor(ix + 1/2) = ix, half a texel from any rounding
+        // boundary; the texels come as x (ix, iy + 1), y (ix + 1, iy + 1),
+        // z (ix + 1, iy), w (ix, iy)
+        const uint4 g = tex2Dgather<uint4>((cudaTextureObject_t)S.atlas_tex, (float)(ix + 1), (float)(iy + 1), 0);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            const uchar4 g = tex2Dgather<uchar4>((cudaTextureObject_t)S.atlas_tex, u, w, c);
-            const float v00 = (float)g.w, v10 = (float)g.z, v01 = (float)g.x, v11 = (float)g.y;
+            const float v00 = texel_channel(g.w, c), v10 = texel_channel(g.z, c);
+            const float v01 = texel_channel(g.x, c), v11 = texel_channel(g.y, c);
             const float top = __fmaf_rn(ax, v10, __fmul_rn(gx, v00));
             const float bot = __fmaf_rn(ax, v11, __fmul_rn(gx, v01));
             out |= round_channel(__fmaf_rn(ay, bot, __fmul_rn(gy, top))) << (8 * c);
