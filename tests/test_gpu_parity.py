@@ -164,10 +164,34 @@ def test_invalid_arguments_on_device():
                           out["depth"]) == hsr.HSR_ERR_INVALID_ARG
     assert hsr.hsr_render(h.handle, good, Intrinsics(8, 8, 8, 8, 1e-7, 10.0), 16, 16, out["rgb"],
                           out["depth"]) == hsr.HSR_ERR_INVALID_ARG
+    # zero views, no output buffer, null handle
+    assert hsr.hsr_render(h.handle, good[:0], intr, 16, 16, out["rgb"], out["depth"]) == hsr.HSR_ERR_INVALID_ARG
+    assert hsr.hsr_render(h.handle, good, intr, 16, 16, None, None, None) == hsr.HSR_ERR_INVALID_ARG
+    assert hsr.hsr_render_noalloc(h.handle, good[:0], intr, 16, 16, out["rgb"], out["depth"]) == \
+        hsr.HSR_ERR_INVALID_ARG
+    assert hsr.hsr_render(0, good, intr, 16, 16, out["rgb"], out["depth"]) == hsr.HSR_ERR_INVALID_ARG
     # a later call still works
     assert hsr.hsr_render(h.handle, good, intr, 16, 16, out["rgb"], out["depth"], out["ids"]) == hsr.HSR_OK
     torch.cuda.synchronize()
     h.close()
+
+
+def test_empty_and_invalid_scenes_refused():
+    """A scene with no triangles or no vertices, an index beyond the vertex
+    count, or a non-finite position is refused at load (zero counts and bad
+    indices are invalid arguments by the ABI's contract)."""
+    xyz = np.array([[0, 0, -5], [1, 0, -5], [0, 1, -5]], np.float32)
+    idx = np.array([[0, 1, 2]], np.uint32)
+    for x, i in ((xyz, idx[:0]), (xyz[:0], idx), (xyz, np.array([[0, 1, 3]], np.uint32)),
+                 (np.array([[0, 0, -5], [np.nan, 0, -5], [0, 1, -5]], np.float32), idx)):
+        with pytest.raises(hsr.HsrError) as e:
+            hsr.hsr_scene_load(x, i)
+        assert e.value.status == hsr.HSR_ERR_INVALID_ARG
+    h = hsr.hsr_scene_load(xyz, idx)          # the valid one loads, renders and frees
+    out = hsr.alloc_outputs(1, 8, 8)
+    assert hsr.hsr_render(h, identity_pose()[None], screen_intr(8, 8), 8, 8, out["rgb"], out["depth"]) == hsr.HSR_OK
+    torch.cuda.synchronize()
+    hsr.hsr_scene_free(h)
 
 
 def test_determinism_and_order_independence():
