@@ -540,7 +540,7 @@ cudaError_t enqueue_render(const Plan &pl, const Params &p, void *d_desc, const 
         e = launch_actuate(p, pl.n_cap, stream);
         if (e != cudaSuccess) return e;
     }
-    return launch_render(p, pl.cfg, stream, guard, noise);
+    return launch_render(p, pl.cfg, stream, guard, noise, false);
 }
 
 // Scenes, poses, intrinsics and size of a render; at least one output buffer
@@ -664,7 +664,7 @@ int render_views(const hsr_scene *const *scenes, uint32_t n_scenes, const uint32
     e = cudaMemcpyAsync(dbuf, hbuf, pl.desc_bytes, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaEventRecord(st.done, stream);
     if (e == cudaSuccess) st.pending = true;
-    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream, guard, nr.noise && nr.noise->depth_sigma > 0.f);
+    if (e == cudaSuccess) e = launch_render(p, pl.cfg, stream, guard, nr.noise && nr.noise->depth_sigma > 0.f, true);
     if (reuse) {
         if (!cs.release(stream) && e == cudaSuccess) e = cudaErrorUnknown;
         return e == cudaSuccess ? HSR_OK : cuda_status(e);

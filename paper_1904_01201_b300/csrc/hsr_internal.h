@@ -250,8 +250,13 @@ cudaError_t prepare_kernels();
 // Launches the cull, raster and shade kernels on `stream`; `guard`: some view
 // may snap a vertex beyond +-2^30 sub-pixels (guard_free failed for it), so
 // shading compiles in the guard-band path; `noise`: the call adds depth noise
-// (the shading variant with the noise model).
-cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard, bool noise);
+// (the shading variant with the noise model); `pdl`: kernels after the cull
+// use programmatic dependent launch (direct calls; graph-captured batches,
+// whose launch gaps are already small and which serve concurrent streams,
+// launch them plainly: early-scheduled waiting CTAs would hold SM slots the
+// other streams' work could use).
+cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard, bool noise,
+                          bool pdl);
 // Device error flags (kErrWaitTimeout, ...) raised by kernels on the current
 // device since the last clear; waits for the device.
 cudaError_t read_device_errors(uint32_t *flags, bool clear);

@@ -186,5 +186,5 @@ extern "C" HSR_API int hsr_render_noalloc(const hsr_scene *scene, const hsr_pose
     p.n_phases = cfg.n_phases;
     p.phase_r2[0] = cfg.phase_r[0] * cfg.phase_r[0];
     p.phase_r2[1] = cfg.phase_r[1] * cfg.phase_r[1];
-    return launch_render(p, cfg, stream, guard, false) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
+    return launch_render(p, cfg, stream, guard, false, true) == cudaSuccess ? HSR_OK : HSR_ERR_CUDA;
 }

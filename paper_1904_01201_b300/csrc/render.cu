@@ -1169,13 +1169,14 @@ cudaError_t prepare_kernels()
     return set_raster_smem_attr(dev);
 }
 
-// Launch of a kernel that may start while the kernel before it on the stream
-// is finishing (programmatic dependent launch): its CTAs are scheduled once
-// every CTA of that kernel has allowed it, and wait for its completion
-// (grid_dependency_wait) before touching memory, so only the launch latency
-// and CTA start-up overlap.
+// Launch of a kernel that, with `pdl`, may start while the kernel before it
+// on the stream is finishing (programmatic dependent launch): its CTAs are
+// scheduled once every CTA of that kernel has allowed it, and wait for its
+// completion (grid_dependency_wait) before touching memory, so only the
+// launch latency and CTA start-up overlap. Without `pdl` it is an ordinary
+// launch (the wait then returns at once).
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+static cudaError_t launch_dependent(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                                     cudaStream_t stream, Args... args)
 {
     cudaLaunchAttribute attr[1];
@@ -1187,7 +1188,7 @@ static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 bl
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -1204,7 +1205,8 @@ static cudaError_t device_sms(int dev, int *sms)
     return e;
 }
 
-cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard, bool noise)
+cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t stream, bool guard, bool noise,
+                          bool pdl)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1241,19 +1243,19 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         const uint32_t hiz_blocks = std::min<uint32_t>((hiz_threads + 255) / 256, (uint32_t)sms * 16);
         for (uint32_t ph = 0; ph < std::max<uint32_t>(p.n_phases, 1u); ph++) {
             if (ph > 0) {
-                e = launch_dependent(hiz_kernel, dim3(hiz_blocks), dim3(256), 0, stream, p);
+                e = launch_dependent(pdl, hiz_kernel, dim3(hiz_blocks), dim3(256), 0, stream, p);
                 if (e != cudaSuccess) return e;
-                e = launch_dependent(hiz_pyramid_kernel, dim3(p.n_views), dim3(256), 0, stream, p);
+                e = launch_dependent(pdl, hiz_pyramid_kernel, dim3(p.n_views), dim3(256), 0, stream, p);
                 if (e != cudaSuccess) return e;
                 const uint32_t occl_blocks = std::min<uint32_t>((p.vis_cap + 255) / 256, (uint32_t)sms * 16);
-                e = launch_dependent(occl_kernel, dim3(std::max(occl_blocks, 1u)), dim3(256), 0, stream, p, ph);
+                e = launch_dependent(pdl, occl_kernel, dim3(std::max(occl_blocks, 1u)), dim3(256), 0, stream, p, ph);
                 if (e != cudaSuccess) return e;
             }
-            e = launch_dependent(raster_kernel, dim3((uint32_t)sms * cfg.raster_ctas_per_sm), dim3(kRasterThreads),
+            e = launch_dependent(pdl, raster_kernel, dim3((uint32_t)sms * cfg.raster_ctas_per_sm), dim3(kRasterThreads),
                                  kRasterSmem, stream, p, ph);
             if (e != cudaSuccess) return e;
             if (p.big_rec) {
-                e = launch_dependent(big_raster_kernel, dim3((uint32_t)sms * 8), dim3(256), 0, stream, p, ph);
+                e = launch_dependent(pdl, big_raster_kernel, dim3((uint32_t)sms * 8), dim3(256), 0, stream, p, ph);
                 if (e != cudaSuccess) return e;
             }
         }
@@ -1274,7 +1276,7 @@ cudaError_t launch_render(const Params &p, const LaunchCfg &cfg, cudaStream_t st
         const uint32_t nv = std::min<uint32_t>(65535, p.n_views - v0);
         void (*shade)(Params, uint32_t) = guard ? (noise ? shade_kernel<true, true> : shade_kernel<true, false>)
                                                 : (noise ? shade_kernel<false, true> : shade_kernel<false, false>);
-        e = launch_dependent(shade, dim3(bx, nv), dim3(kShadeThreads), 0, stream, p, v0);
+        e = launch_dependent(pdl, shade, dim3(bx, nv), dim3(kShadeThreads), 0, stream, p, v0);
         if (e != cudaSuccess) return e;
     }
 
