@@ -4,7 +4,8 @@
 // workers submit such requests concurrently and a scheduler thread packs them
 // into graph-replayed micro-batches per resolution, admitted against a fixed
 // framebuffer budget, with several micro-batches in flight on separate
-// streams.
+// streams; a completion thread polls each stream's event and hands finished
+// results back.
 #include "../../include/hsr.h"
 
 #include <algorithm>
@@ -70,6 +71,12 @@ struct hsr_server {
     std::deque<Pending> incoming;
     std::deque<hsr_result> done;
     std::thread worker;
+    // completion: each stream's batch records done_ev[st]; the completion
+    // thread polls the streams whose batch is in flight (flight[st])
+    std::vector<cudaEvent_t> done_ev;
+    std::vector<InFlight *> flight;
+    std::condition_variable flight_cv;
+    std::thread completer;
     bool stop = false;
     uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0;
     uint32_t in_flight = 0, queued = 0;
@@ -112,25 +119,57 @@ void eligible_actions(const hsr_server *s, const std::deque<Pending> &q, size_t 
 
 uint64_t frame_bytes(uint32_t res, bool ids) { return (uint64_t)res * res * (ids ? 11u : 7u); }
 
-void CUDART_CB on_done(void *arg)
+// A batch has finished on its stream (s->mu held): its results become
+// available, its stream and agents free; `status` is HSR_OK unless the
+// stream reported an error.
+void finish_batch(hsr_server *s, InFlight *f, double t, int status)
 {
-    InFlight *f = static_cast<InFlight *>(arg);
-    hsr_server *s = f->srv;
-    const double t = now_s();
-    {
-        std::lock_guard<std::mutex> lock(s->mu);
-        for (hsr_result &r : f->results) {
-            r.t_done = t;
-            s->done.push_back(r);
-        }
-        s->completed += f->results.size();
-        s->in_flight -= (uint32_t)f->results.size();
-        s->busy[f->stream] = false;
-        for (uint32_t a : f->agents) s->agent_busy[a] = false;
+    for (hsr_result &r : f->results) {
+        r.t_done = t;
+        if (status != HSR_OK) r.status = status;
+        s->done.push_back(r);
     }
-    s->cv.notify_all();
-    s->done_cv.notify_all();
-    delete f;
+    s->completed += f->results.size();
+    s->in_flight -= (uint32_t)f->results.size();
+    s->busy[f->stream] = false;
+    for (uint32_t a : f->agents) s->agent_busy[a] = false;
+}
+
+// Completion thread: polls the event of every stream with a batch in flight
+// (yielding between rounds, so a finished batch is seen within a few
+// microseconds), sleeps while none is; after stop, finishes what is in flight.
+void complete_loop(hsr_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    for (;;) {
+        bool any = false, finished = false;
+        for (size_t st = 0; st < s->flight.size(); st++) {
+            InFlight *f = s->flight[st];
+            if (!f) continue;
+            const cudaError_t q = cudaEventQuery(s->done_ev[st]);
+            if (q == cudaErrorNotReady) {
+                any = true;
+                continue;
+            }
+            finish_batch(s, f, now_s(), q == cudaSuccess ? HSR_OK : HSR_ERR_CUDA);
+            s->flight[st] = nullptr;
+            delete f;
+            finished = true;
+        }
+        if (finished) {
+            s->cv.notify_all();
+            s->done_cv.notify_all();
+        }
+        if (!any) {
+            if (s->stop) break;
+            s->flight_cv.wait(lock);
+            continue;
+        }
+        lock.unlock();
+        std::this_thread::yield();
+        lock.lock();
+    }
 }
 
 void fail_request(hsr_server *s, const Pending &p, int status)
@@ -280,8 +319,12 @@ void run(hsr_server *s)
             int rc = best_kind ? hsr_batch_step(b, ag, agent_idx.data(), actions.data(), n, frames.data(), nullptr,
                                                 stream)
                                : hsr_batch_render(b, soa.data(), poses.data(), n, frames.data(), stream);
-            if (rc == HSR_OK && cudaLaunchHostFunc(stream, on_done, f) != cudaSuccess) rc = HSR_ERR_CUDA;
+            if (rc == HSR_OK && cudaEventRecord(s->done_ev[st], stream) != cudaSuccess) rc = HSR_ERR_CUDA;
             lock.lock();
+            if (rc == HSR_OK) {
+                s->flight[st] = f;
+                s->flight_cv.notify_one();
+            }
             if (rc != HSR_OK) {
                 // the views could not be rendered: report the error, return the slots
                 for (hsr_result &r : f->results) {
@@ -310,16 +353,18 @@ void run(hsr_server *s)
 void destroy_server(hsr_server *s)
 {
     if (!s) return;
-    if (s->worker.joinable()) {
-        {
-            std::lock_guard<std::mutex> lock(s->mu);
-            s->stop = true;
-        }
-        s->cv.notify_all();
-        s->worker.join();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
     }
+    s->cv.notify_all();
+    s->flight_cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    if (s->completer.joinable()) s->completer.join();
     cudaSetDevice(s->device);
     for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
+    for (cudaEvent_t e : s->done_ev)
+        if (e) cudaEventDestroy(e);
     for (ResPool &P : s->pools) {
         for (hsr_batch *b : P.batch) hsr_batch_destroy(b);
         if (P.rgb) cudaFree(P.rgb);
@@ -364,6 +409,10 @@ int hsr_server_create(const hsr_scene *const *scenes, uint32_t n_scenes, const h
         if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) rc = HSR_ERR_CUDA;
         s->streams.push_back(stream);
         s->busy.push_back(false);
+        cudaEvent_t ev = nullptr;
+        if (rc == HSR_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = HSR_ERR_CUDA;
+        s->done_ev.push_back(ev);
+        s->flight.push_back(nullptr);
     }
     s->pools.resize(cfg->n_res);
     for (uint32_t k = 0; k < cfg->n_res && rc == HSR_OK; k++) {
@@ -395,6 +444,7 @@ int hsr_server_create(const hsr_scene *const *scenes, uint32_t n_scenes, const h
         destroy_server(s);
         return rc;
     }
+    s->completer = std::thread(complete_loop, s);
     s->worker = std::thread(run, s);
     *out = s;
     return HSR_OK;
