@@ -903,7 +903,7 @@ def main():
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving: request rates (1/s)")
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-streams", type=int, default=4)
-    ap.add_argument("--serve-wait-us", type=int, default=150)
+    ap.add_argument("--serve-wait-us", type=int, default=50)
     ap.add_argument("--serve-requests", default="action", choices=["action", "pose"],
                     help="serving: requests carry an action of a device-resident agent, or a host pose")
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])

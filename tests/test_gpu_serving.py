@@ -180,7 +180,7 @@ def test_serving_workload_settings(oracle_mod):
     """The serving configuration as bench.py runs it: the 8 batching scenes
     resident (0.2M-2M triangles), 1,024 device-resident agents, action
     requests at 64/128/256/512 (weights 0.2/0.4/0.3/0.1) in bursts, micro-
-    batches of up to 64 views on 4 streams, 150 us wait, 4 GiB of
+    batches of up to 64 views on 4 streams, 50 us wait, 4 GiB of
     framebuffers. Every result equals the one-shot render of the pose its
     action reached (the oracle's actuation in submission order), bit for bit;
     two results per resolution against the oracle."""
@@ -191,7 +191,7 @@ def test_serving_workload_settings(oracle_mod):
     navs = [wl.navmap(s, 0.05) for s in sc]
     poses0 = agents.poses()
     srv = serve.Server(hs, res=res, weights=(0.2, 0.4, 0.3, 0.1), fb_bytes=4 << 30, max_batch=64, n_streams=4,
-                       max_wait_us=150)
+                       max_wait_us=50)
     srv.attach_agents(agents)
     n = 800
     req = serve.make_action_requests(n, 1024, res=res, seed=3)
