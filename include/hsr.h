@@ -220,8 +220,10 @@ HSR_API int hsr_render_views(const hsr_scene *const *scenes, uint32_t n_scenes, 
  * resolution is free; admitted requests of one resolution are packed into a
  * micro-batch (<= max_batch views, waiting at most max_wait_us for more) and
  * rendered by replaying that resolution's captured graph on one of n_streams
- * streams, so micro-batches overlap on the device. Each request yields one
- * result (polled), which points at its device frame until released.
+ * streams, so micro-batches overlap on the device. A completion thread polls
+ * each stream's event while a micro-batch is in flight (it keeps one host
+ * core busy then, and sleeps otherwise). Each request yields one result
+ * (polled), which points at its device frame until released.
  * Results are identical to a one-shot hsr_render of the same view.
  *
  * Action requests (agent >= 0; needs hsr_server_attach_agents) carry an
