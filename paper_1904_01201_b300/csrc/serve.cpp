@@ -363,6 +363,8 @@ void destroy_server(hsr_server *s)
     if (s->completer.joinable()) s->completer.join();
     cudaSetDevice(s->device);
     for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
+    // a batch launched while the server stopped may not have been collected
+    for (InFlight *f : s->flight) delete f;
     for (cudaEvent_t e : s->done_ev)
         if (e) cudaEventDestroy(e);
     for (ResPool &P : s->pools) {
