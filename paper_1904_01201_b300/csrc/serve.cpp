@@ -138,37 +138,47 @@ void finish_batch(hsr_server *s, InFlight *f, double t, int status)
 // Completion thread: polls the event of every stream with a batch in flight
 // (yielding between rounds, so a finished batch is seen within a few
 // microseconds), sleeps while none is; after stop, finishes what is in flight.
+// The events are queried without the server's lock (a stream's entry changes
+// only after its batch is finished here), so the scheduler thread is not
+// kept waiting for the lock.
 void complete_loop(hsr_server *s)
 {
     cudaSetDevice(s->device);
+    std::vector<InFlight *> snap;
+    std::vector<cudaError_t> state;
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
-        bool any = false, finished = false;
-        for (size_t st = 0; st < s->flight.size(); st++) {
-            InFlight *f = s->flight[st];
-            if (!f) continue;
-            const cudaError_t q = cudaEventQuery(s->done_ev[st]);
-            if (q == cudaErrorNotReady) {
-                any = true;
-                continue;
-            }
-            finish_batch(s, f, now_s(), q == cudaSuccess ? HSR_OK : HSR_ERR_CUDA);
-            s->flight[st] = nullptr;
-            delete f;
-            finished = true;
-        }
-        if (finished) {
-            s->cv.notify_all();
-            s->done_cv.notify_all();
-        }
+        snap = s->flight;
+        bool any = false;
+        for (InFlight *f : snap) any |= f != nullptr;
         if (!any) {
             if (s->stop) break;
             s->flight_cv.wait(lock);
             continue;
         }
         lock.unlock();
-        std::this_thread::yield();
+        state.assign(snap.size(), cudaErrorNotReady);
+        bool ready = false;
+        for (size_t st = 0; st < snap.size(); st++)
+            if (snap[st]) {
+                state[st] = cudaEventQuery(s->done_ev[st]);
+                ready |= state[st] != cudaErrorNotReady;
+            }
+        if (!ready) {
+            std::this_thread::yield();
+            lock.lock();
+            continue;
+        }
+        const double t = now_s();
         lock.lock();
+        for (size_t st = 0; st < snap.size(); st++) {
+            if (!snap[st] || state[st] == cudaErrorNotReady) continue;
+            finish_batch(s, snap[st], t, state[st] == cudaSuccess ? HSR_OK : HSR_ERR_CUDA);
+            s->flight[st] = nullptr;
+            delete snap[st];
+        }
+        s->cv.notify_all();
+        s->done_cv.notify_all();
     }
 }
 
