@@ -647,8 +647,8 @@ def run_subrecords(args):
     1,024 agents), the 2M-triangle 512^2 workload with ids (each batched vs
     plain, with the oracle's rate on a shorter sample of the same views),
     serving at 10k and 50k requests/s (p50 / p99 latency; the oracle's rate
-    over the request mix), and the frame-transfer strategies at 128^2 RGB-D
-    (1 and 5 renderers, 1 and 64 agents per launch)."""
+    over the request mix), and the frame-transfer strategies (the whole
+    table and resolution sweep, on shorter measurement windows)."""
     import copy
     out = {}
     for name in ("room", "batching", "large"):
@@ -813,7 +813,8 @@ def run_transfer(args, quick: bool = False):
     simulator processes, each rendering 1 agent per launch (as a simulator
     process does) or 64. Copies are queued on each renderer's stream after
     its render; frames/s over all renderers, wall clock, synchronised on both
-    sides."""
+    sides. `quick` measures every cell over a shorter window (0.1 s instead
+    of 0.25 s)."""
     import torch
     from paper_1904_01201_b300 import hsr
     from paper_1904_01201_b300 import workloads as wl
@@ -854,7 +855,7 @@ def run_transfer(args, quick: bool = False):
         t0 = time.perf_counter()
         step(3)
         torch.cuda.synchronize()
-        steps = int(min(400, max(5, 0.25 / max(1e-6, time.perf_counter() - t0))))
+        steps = int(min(400, max(5, window / max(1e-6, time.perf_counter() - t0))))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(steps):
@@ -865,17 +866,18 @@ def run_transfer(args, quick: bool = False):
             b.close()
         return n_streams * per_launch * steps / dt
 
+    window = 0.1 if quick else 0.25
     clk = ClockSampler()
     table = []
     for per_launch in (1, 64):
-        for sensor in (("rgbd",) if quick else ("rgb", "rgbd", "rgbds")):
+        for sensor in ("rgb", "rgbd", "rgbds"):
             for strategy in ("gpu-cpu-gpu", "gpu-cpu", "gpu-gpu"):
-                for n_streams in ((1, 5) if quick else (1, 3, 5)):
+                for n_streams in (1, 3, 5):
                     table.append({"res": 128, "sensors": sensor, "transfer": strategy, "renderers": n_streams,
                                   "agents_per_launch": per_launch,
                                   "frames_per_s": measure(128, sensor, strategy, n_streams, per_launch)})
     sweep = []
-    for per_launch in (() if quick else (1, 64)):
+    for per_launch in (1, 64):
         for res in (64, 128, 256, 512):
             for strategy in ("gpu-cpu-gpu", "gpu-cpu", "gpu-gpu"):
                 sweep.append({"res": res, "sensors": "rgbd", "transfer": strategy, "renderers": 1,
@@ -888,7 +890,8 @@ def run_transfer(args, quick: bool = False):
             "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/int",
             "data": "synthetic",
             "config": {"workload": "transfer-house-1M-atlas4096-sem", "tris": int(sc.n_tris),
-                       "value_is": "gpu-gpu, rgbd, 128x128, 1 renderer, 64 agents per launch"},
+                       "value_is": "gpu-gpu, rgbd, 128x128, 1 renderer, 64 agents per launch",
+                       "window_s": window},
             "table": table, "resolution_sweep": sweep, "clocks": clocks}
 
 
