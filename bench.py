@@ -647,8 +647,9 @@ def run_subrecords(args):
     1,024 agents), the 2M-triangle 512^2 workload with ids (each batched vs
     plain, with the oracle's rate on a shorter sample of the same views),
     serving at 10k and 50k requests/s (p50 / p99 latency; the oracle's rate
-    over the request mix), and the frame-transfer strategies (the whole
-    table and resolution sweep, on shorter measurement windows)."""
+    over the request mix), the frame-transfer strategies (the whole table
+    and resolution sweep, on shorter measurement windows), and the semantic
+    sensor from the separate 3M-triangle mesh."""
     import copy
     out = {}
     for name in ("room", "batching", "large"):
@@ -661,6 +662,7 @@ def run_subrecords(args):
     a.rates, a.cpu_seconds = "10000,50000", min(args.cpu_seconds, 5.0)
     out["serving"] = run_serving(a)
     out["transfer"] = run_transfer(args, quick=True)
+    out["semantic"] = run_semantic(args)
     return out
 
 
@@ -913,7 +915,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
-                    help="house: skip the room, batching, large, serving and transfer sub-records of the default run")
+                    help="house: skip the room, batching, large, serving, transfer and semantic sub-records of the "
+                         "default run")
     ap.add_argument("--cpu-frames", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="least CPU time of the oracle's all-core sample (at most three times that)")
