@@ -1,4 +1,4 @@
-"""Serving driver: a thin wrapper of the hsr_server_* C-ABI and a Poisson
+"""Serving front end: a thin wrapper of the hsr_server_* C-ABI and a Poisson
 load generator (the core — admission, micro-batching, streams, completion —
 is C++ in csrc/serve.cpp).
 

@@ -85,7 +85,7 @@ def test_committed_profiles_parse():
 
 
 def test_algorithmic_bytes_per_view(room):
-    """SURVEY's per-view formula on the vertex-coloured room (no atlas):
+    """The per-view algorithmic-byte formula on the vertex-coloured room (no atlas):
     12 B per triangle, 15 B per vertex, 7 B per pixel."""
     sc = room["scenes"][0]
     assert bench.algorithmic_bytes_per_view(sc, 128, 128, False) == 12.0 * sc.n_tris + 15.0 * sc.n_verts + 7.0 * 128 * 128
