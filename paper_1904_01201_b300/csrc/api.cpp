@@ -995,7 +995,8 @@ int hsr_scene_load(const float *xyz, uint32_t n_verts, const uint32_t *idx, uint
         // may run one entry past a meshlet's last triangle
         mtri.push_back(make_uint2(0u, 0u));
         mtri.push_back(make_uint2(0u, 0u));
-        // groups of 32 meshlets
+        // groups of 32 meshlets: group g is meshlets [32 g, min(32 g + 32, n)),
+        // which the culling kernel computes without reading the group record
         std::vector<Group> groups;
         for (uint32_t m0 = 0; m0 < n_meshlets; m0 += kGroupMeshlets) {
             Group g{};

@@ -10,7 +10,8 @@
 namespace hsr {
 
 // Meshlets: up to 32 triangles and 64 distinct vertices, spatially coherent
-// (Morton order of triangle centroids). Groups: 32 consecutive meshlets.
+// (Morton order of triangle centroids). Groups: 32 consecutive meshlets,
+// group g holding meshlets [32 g, 32 g + 32) (the last one fewer).
 constexpr int kMeshletTris = 32;
 constexpr int kMeshletVerts = 64;
 constexpr int kGroupMeshlets = 32;

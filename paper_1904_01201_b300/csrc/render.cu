@@ -135,6 +135,34 @@ __device__ __forceinline__ int meshlet_backfacing(const Params &p, const SceneDe
     return sub_area > 2.f * change ? 2 : 1;
 }
 
+// The warps' remaining staged pairs of each phase, appended with one global
+// reservation per phase for the whole CTA (each warp's share is taken in
+// shared memory), instead of one per warp and phase: at the end of the
+// culling every warp flushes at about the same time, and the reservations
+// of all of them fall on the same three counters. Every thread of the CTA
+// calls it.
+__device__ __forceinline__ void flush_rest_cta(const Params &p, uint4 (*s_buf)[3][2 * 32], const uint32_t (&nbuf)[3],
+                                               int lane, int warp)
+{
+    __shared__ uint32_t s_cnt[3], s_base[3];
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    uint32_t off[3];
+#pragma unroll
+    for (int ph = 0; ph < 3; ph++) {
+        uint32_t o = 0u;
+        if (lane == 0 && nbuf[ph]) o = atomicAdd(&s_cnt[ph], nbuf[ph]);
+        off[ph] = __shfl_sync(0xFFFFFFFFu, o, 0);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && s_cnt[threadIdx.x])
+        s_base[threadIdx.x] = atomicAdd(p.vis_count + threadIdx.x, s_cnt[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (int ph = 0; ph < 3; ph++)
+        if ((uint32_t)lane < nbuf[ph]) p.vis[vis_index(p, ph, s_base[ph] + off[ph] + lane)] = s_buf[warp][ph][lane];
+}
+
 __global__ void __launch_bounds__(256) cull_kernel_vg(const Params p)
 {
     allow_dependent_launch();
@@ -231,9 +259,7 @@ __global__ void __launch_bounds__(256) cull_kernel_vg(const Params p)
             }
         }
     }
-#pragma unroll
-    for (uint32_t ph = 0; ph < 3; ph++)
-        if (nbuf[ph]) flush(ph, nbuf[ph]);
+    flush_rest_cta(p, s_buf, nbuf, lane, warp);
 }
 
 // Most views of one group tested per warp item (the group's and its
@@ -300,11 +326,18 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
         const uint32_t va = s_v0[k] + ch * p.cull_views;
         const uint32_t vb = min(va + p.cull_views, s_v0[k] + s_nv[k]);
         const SceneDev &S = p.scenes[s_scene[k]];
-        const Group grp = S.groups[g];
-        const uint32_t m = grp.m0 + lane;
-        const bool valid = m < grp.m1;
+        // group g is the run of kGroupMeshlets consecutive meshlets from
+        // g * kGroupMeshlets, so the meshlet loads need not wait for its
+        // record; the back-face test's plane records are requested into L1
+        // at the same time (no register held until the test reads them)
+        const uint32_t m = g * kGroupMeshlets + lane;
+        const bool valid = m < S.n_meshlets;
         Meshlet ml{};
-        if (valid) ml = S.meshlets[m];
+        if (valid) {
+            ml = S.meshlets[m];
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(S.mplane + 2 * (size_t)m));
+        }
+        const Group grp = S.groups[g];
         uint32_t nvb = __shfl_down_sync(0xFFFFFFFFu, ml.vbase, 1);
         uint32_t ntb = __shfl_down_sync(0xFFFFFFFFu, ml.tbase, 1);
         if (valid && (m + 1 == grp.m1 || lane == 31)) {
@@ -368,9 +401,7 @@ __global__ void __launch_bounds__(256) cull_kernel(const Params p)
             }
         }
     }
-#pragma unroll
-    for (uint32_t ph = 0; ph < 3; ph++)
-        if (nbuf[ph]) flush(ph, nbuf[ph]);
+    flush_rest_cta(p, s_buf, nbuf, lane, warp);
 }
 
 // --------------------------------------------------------------------- raster
