@@ -290,3 +290,26 @@ def test_intrinsics_limits():
     torch.cuda.synchronize()
     assert hsr.hsr_device_status(1) == hsr.HSR_OK
     h.close()
+
+
+def test_wide_room_guard_band_with_noisy_depth(oracle_mod):
+    """The shading variant with both the guard-band path and depth noise
+    (Appendix C): the wide room at 1024^2 and near 2e-6 m with sigma 0.4.
+    Ids and RGB equal the noise-free guard-band render, and depth meets the
+    noise tests' derived fp32/fp64 bound against the oracle."""
+    from tests.test_gpu_noise import assert_noisy_parity
+    sc = _wide_room(1)
+    poses = _room_poses()
+    W = H = 1024
+    intr = Intrinsics(W / 2, W / 2 * 1.2, W / 2, H / 2, 2e-6, 60.0)
+    assert _max_snap(sc, poses, intr, oracle_mod) > 2.0 ** 36
+    h = hsr.SceneHandle(sc)
+    sigma, seed = 0.4, 0x5EED
+    g = _np(hsr.render(h, poses, intr, W, H, ids=True, noise_sigma=sigma, noise_seed=seed))
+    assert hsr.hsr_device_status(1) == hsr.HSR_OK
+    o = oracle_mod.render(sc, poses, intr, W, H, noise_sigma=sigma, noise_seed=seed)
+    n_both, _ = assert_noisy_parity(g, o, intr, sigma, "guard band + noise")
+    assert n_both > 0.3 * g["depth"].size
+    clean = _np(hsr.render(h, poses, intr, W, H, ids=True))
+    assert np.array_equal(clean["ids"], g["ids"]) and np.array_equal(clean["rgb"], g["rgb"])
+    h.close()
