@@ -313,3 +313,25 @@ def test_wide_room_guard_band_with_noisy_depth(oracle_mod):
     clean = _np(hsr.render(h, poses, intr, W, H, ids=True))
     assert np.array_equal(clean["ids"], g["ids"]) and np.array_equal(clean["rgb"], g["rgb"])
     h.close()
+
+
+def test_wide_room_guard_band_trilinear(oracle_mod):
+    """Trilinear sampling on guard-clipped triangles (the level of detail
+    comes from each guard sub-triangle's own derivatives): the wide room with
+    a 2048^2 atlas at 1024^2 and near 2e-6 m, so that its floor is magnified
+    near the camera and minified by several levels far away."""
+    sc = _wide_room(1)
+    sc.atlas = np.random.default_rng(9).integers(0, 256, (2048, 2048, 4), dtype=np.uint8)
+    poses = _room_poses()
+    W = H = 1024
+    intr = Intrinsics(W / 2, W / 2 * 1.2, W / 2, H / 2, 2e-6, 60.0)
+    assert _max_snap(sc, poses, intr, oracle_mod) > 2.0 ** 36
+    h = hsr.SceneHandle(sc)
+    h.set_sampling(hsr.HSR_SAMPLE_TRILINEAR)
+    g = _np(hsr.render(h, poses, intr, W, H, ids=True))
+    assert hsr.hsr_device_status(1) == hsr.HSR_OK
+    o = oracle_mod.render(sc, poses, intr, W, H, trilinear=True, lod=True)
+    hit = np.isfinite(o["lod"])
+    assert (o["lod"][hit] > 1).mean() > 0.02 and (o["lod"][hit] <= 0).mean() > 0.02
+    _parity(g, o, "guard band, trilinear")
+    h.close()
