@@ -331,7 +331,7 @@ def run_reference_other(args):
     if rank != 0:
         return None
     if args.workload != "serving":
-        return {"impl": "reference", "unavailable": f"the {args.workload} workload times GPU transfer paths with no "
+        return {"impl": "reference", "unavailable": f"the {args.workload} workload times GPU-side paths with no "
                                                     "CPU counterpart; the oracle arm covers house, room, batching, "
                                                     "large and serving"}
     from paper_1904_01201_b300 import workloads as wl
@@ -648,8 +648,9 @@ def run_subrecords(args):
     plain, with the oracle's rate on a shorter sample of the same views),
     serving at 10k and 50k requests/s (p50 / p99 latency; the oracle's rate
     over the request mix), the frame-transfer strategies (the whole table
-    and resolution sweep, on shorter measurement windows), and the semantic
-    sensor from the separate 3M-triangle mesh."""
+    and resolution sweep, on shorter measurement windows), the semantic
+    sensor from the separate 3M-triangle mesh, and agents stepped on the
+    device with and without depth noise."""
     import copy
     out = {}
     for name in ("room", "batching", "large"):
@@ -663,6 +664,7 @@ def run_subrecords(args):
     out["serving"] = run_serving(a)
     out["transfer"] = run_transfer(args, quick=True)
     out["semantic"] = run_semantic(args)
+    out["steps"] = run_steps(args)
     return out
 
 
@@ -805,6 +807,73 @@ def run_semantic(args):
             "rgbd_frames_per_s": fps_rgbd, "semantic_slowdown": fps_rgbd / fps_sem, "clocks": clocks}
 
 
+def run_steps(args):
+    """Agents stepped on the device (Sec. 4 action space: move forward 0.25 m,
+    turn 10 degrees, no sliding) and rendered in one batched call per step:
+    the 1M-triangle house at 256x256, 64 agents on its navigability grid taking
+    uniform random actions, RGB-D; with and without the Appendix C depth noise
+    (sigma 0.4 in inverse depth). Beside them the same batch rendering the
+    agents' current poses from the host. Frames/s from the median of CUDA
+    events around each call, L2 flushed before each."""
+    import torch
+    from paper_1904_01201_b300 import hsr
+    from paper_1904_01201_b300 import workloads as wl
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    sc = wl.make_house(args.seed, 1_000_000, 4096)
+    nav = wl.navmap(sc, 0.05)
+    n, W = 64, 256
+    intr = wl.pinhole_90(W, W)
+    h = hsr.SceneHandle(sc)
+    ag = hsr.Agents([h], [nav], wl.navigable_poses(sc, nav, n, args.seed + 3))
+    b = hsr.Batch([h], n, intr, W, W, ids=False)
+    idx = np.arange(n, dtype=np.uint32)
+    rng = np.random.default_rng(args.seed + 11)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(call):
+        for i in range(max(3, args.warmup)):
+            call(i)
+        ts = []
+        for i in range(max(5, min(args.steps, 50))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(i)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        return n / (ms * 1e-3), ms
+
+    def step(sigma):
+        def call(i):
+            b.step(ag, idx, rng.integers(hsr.HSR_ACTION_MOVE_FORWARD, hsr.HSR_ACTION_TURN_RIGHT + 1, n).astype(np.uint8),
+                   stream=stream, noise_sigma=sigma, noise_seed=7 + i)
+        return call
+
+    clk = ClockSampler()
+    fps, ms = timed(step(None))
+    fps_noise, ms_noise = timed(step(0.4))
+    now = ag.poses(stream)
+    fps_pose, ms_pose = timed(lambda i: b.render(now, stream=stream))
+    clocks = clk.stop()
+    b.close()
+    ag.close()
+    h.close()
+    return {"metric": "RGB-D frames/sec of agents stepped on the device", "value": fps, "unit": UNIT,
+            "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/int",
+            "data": "synthetic",
+            "config": {"workload": "steps-house-1M-atlas4096-64x256", "tris": int(sc.n_tris), "agents": n, "res": W,
+                       "actions": "uniform move_forward / turn_left / turn_right", "l2": "flushed between steps",
+                       "timing": "median of per-call CUDA events"},
+            "ms_per_step": ms, "noisy_depth": {"sigma": 0.4, "value": fps_noise, "ms_per_step": ms_noise},
+            "pose_render": {"value": fps_pose, "ms_per_step": ms_pose,
+                            "what": "the same batch rendering the agents' current poses sent from the host"},
+            "clocks": clocks}
+
+
 def run_transfer(args, quick: bool = False):
     """Frame-transfer strategies (Table 2 and the resolution figure beside it):
     frames stay in device memory for a device consumer (GPU->GPU), are copied
@@ -904,7 +973,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hsr", choices=["hsr", "reference"])
     ap.add_argument("--workload", default="house",
-                    choices=["house", "room", "batching", "large", "serving", "transfer", "semantic"])
+                    choices=["house", "room", "batching", "large", "serving", "transfer", "semantic", "steps"])
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving: request rates (1/s)")
     ap.add_argument("--serve-batch", type=int, default=64)
     ap.add_argument("--serve-streams", type=int, default=4)
@@ -915,8 +984,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
-                    help="house: skip the room, batching, large, serving, transfer and semantic sub-records of the "
-                         "default run")
+                    help="house: skip the room, batching, large, serving, transfer, semantic and steps sub-records of "
+                         "the default run")
     ap.add_argument("--cpu-frames", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="least CPU time of the oracle's all-core sample (at most three times that)")
@@ -927,13 +996,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference" and args.workload in ("serving", "transfer", "semantic"):
+    if args.impl == "reference" and args.workload in ("serving", "transfer", "semantic", "steps"):
         res = run_reference_other(args)
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.workload in ("serving", "transfer", "semantic"):
-        res = {"serving": run_serving, "transfer": run_transfer, "semantic": run_semantic}[args.workload](args)
+    if args.workload in ("serving", "transfer", "semantic", "steps"):
+        res = {"serving": run_serving, "transfer": run_transfer, "semantic": run_semantic,
+               "steps": run_steps}[args.workload](args)
         if res is not None:
             print(json.dumps(res), flush=True)
         return
